@@ -1,0 +1,381 @@
+/*
+ * qext_oracle.c -- plain, slow, obviously correct CPU oracle for the block-wise
+ * two-source extractor Ext_bs^eq (Algorithm 1) of Li & Zhou, "Real-Time
+ * Seedless Post-Processing for Quantum Random Number Generators"
+ * (arXiv 2402.14607).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the reference the CUDA path is
+ * checked against.  Only the tests, the smoke check and the benchmark's CPU
+ * baseline may load it.  It shares no code, header, table or constant with the
+ * CUDA library: it has its own polynomial arithmetic, its own irreducibility
+ * test and its own bit addressing, written for clarity, not speed.
+ *
+ * Conventions (the paper fixes none of these; they are the readings this
+ * project adopts, and every function below follows them):
+ *   - A stream is a little-endian array of uint32 words; stream bit t is bit
+ *     (t mod 32) of word floor(t/32).  An ADC sample s of b bits occupies
+ *     stream bits [s*b, (s+1)*b), least significant bit first.
+ *   - Block l (0-based) of a source is stream bits [l*n, (l+1)*n), n = q*n_p.
+ *     Element i (0-based) of the block is bits [l*n + i*q, l*n + (i+1)*q);
+ *     element bit j is the coefficient of alpha^j (polynomial basis).
+ *   - GF(2^q) = F_2[alpha] / P(alpha).  P is given to every routine as a full
+ *     coefficient vector (bit d of the vector = coefficient of x^d, degree q).
+ *   - Output: Z^(l) truncated to its first m coefficients (alpha^0..alpha^m-1)
+ *     occupies output bits [l*m, (l+1)*m); unused bits of the last word are 0.
+ *
+ * Field elements and polynomials are arrays of uint64 words, least
+ * significant word first, holding up to ORC_MAXQ coefficients.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_MAXQ 256                      /* largest field degree supported   */
+#define ORC_W ((ORC_MAXQ + 64) / 64 + 1)  /* words of a degree <= MAXQ poly   */
+#define ORC_W2 (2 * ORC_W)                /* words of a product before mod    */
+
+/* ------------------------------------------------------------------------ */
+/* Bit helpers on word arrays (uint64 polynomial coefficient vectors).       */
+/* ------------------------------------------------------------------------ */
+static int pbit(const uint64_t *a, int d) { return (int)((a[d >> 6] >> (d & 63)) & 1u); }
+static void pset(uint64_t *a, int d) { a[d >> 6] |= (uint64_t)1 << (d & 63); }
+static void pflip(uint64_t *a, int d) { a[d >> 6] ^= (uint64_t)1 << (d & 63); }
+
+/* degree of a polynomial stored in nw words; -1 for the zero polynomial */
+static int pdeg(const uint64_t *a, int nw)
+{
+    for (int w = nw - 1; w >= 0; --w)
+        if (a[w]) {
+            int d = 63;
+            while (!((a[w] >> d) & 1u)) --d;
+            return w * 64 + d;
+        }
+    return -1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* GF(2^q) multiplication, bit-serial (Sec. 3.2, the field F_{2^q} with      */
+/* addition = bitwise parity).  Right-to-left shift-and-add: for each bit j  */
+/* of b, add alpha^j * a when that bit is set, where alpha^j * a is kept     */
+/* reduced mod P after every single shift by alpha.                          */
+/* ------------------------------------------------------------------------ */
+void orc_gf_mul(int q, const uint64_t *poly, const uint64_t *a, const uint64_t *b, uint64_t *out)
+{
+    uint64_t sh[ORC_W], acc[ORC_W];
+    int nw = q / 64 + 1;
+    memset(sh, 0, sizeof sh);
+    memset(acc, 0, sizeof acc);
+    for (int d = 0; d < q; ++d)
+        if (pbit(a, d)) pset(sh, d);                  /* sh = a (reduced input) */
+    for (int j = 0; j < q; ++j) {
+        if (pbit(b, j))
+            for (int w = 0; w < nw; ++w) acc[w] ^= sh[w];   /* acc += alpha^j a  */
+        /* sh = sh * alpha mod P: shift by one, subtract P if degree reached q */
+        for (int w = nw - 1; w > 0; --w) sh[w] = (sh[w] << 1) | (sh[w - 1] >> 63);
+        sh[0] <<= 1;
+        if (pbit(sh, q))
+            for (int d = 0; d <= q; ++d)
+                if (pbit(poly, d)) pflip(sh, d);
+    }
+    int ow = (q + 63) / 64;
+    for (int w = 0; w < ow; ++w) out[w] = acc[w];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Polynomial arithmetic over F_2 used only by the irreducibility test.      */
+/* ------------------------------------------------------------------------ */
+
+/* r = a mod m (m nonzero); all arrays ORC_W2 words */
+static void pmod(const uint64_t *a, const uint64_t *m, uint64_t *r)
+{
+    int dm = pdeg(m, ORC_W2);
+    memcpy(r, a, sizeof(uint64_t) * ORC_W2);
+    for (int d = pdeg(r, ORC_W2); d >= dm; --d)
+        if (pbit(r, d))
+            for (int e = 0; e <= dm; ++e)
+                if (pbit(m, e)) pflip(r, d - dm + e);
+}
+
+/* r = a*b mod m, schoolbook product then remainder */
+static void pmulmod(const uint64_t *a, const uint64_t *b, const uint64_t *m, uint64_t *r)
+{
+    uint64_t prod[ORC_W2];
+    memset(prod, 0, sizeof prod);
+    int da = pdeg(a, ORC_W2), db = pdeg(b, ORC_W2);
+    for (int i = 0; i <= da; ++i)
+        if (pbit(a, i))
+            for (int j = 0; j <= db; ++j)
+                if (pbit(b, j)) pflip(prod, i + j);
+    pmod(prod, m, r);
+}
+
+/* g = gcd(a, b), Euclid */
+static void pgcd(const uint64_t *a, const uint64_t *b, uint64_t *g)
+{
+    uint64_t u[ORC_W2], v[ORC_W2], t[ORC_W2];
+    memcpy(u, a, sizeof u);
+    memcpy(v, b, sizeof v);
+    while (pdeg(v, ORC_W2) >= 0) {
+        pmod(u, v, t);
+        memcpy(u, v, sizeof u);
+        memcpy(v, t, sizeof v);
+    }
+    memcpy(g, u, sizeof u);
+}
+
+/* r = x^(2^e) mod m by e repeated squarings of x */
+static void x_pow_2e(int e, const uint64_t *m, uint64_t *r)
+{
+    uint64_t x[ORC_W2], t[ORC_W2];
+    memset(x, 0, sizeof x);
+    pset(x, 1);
+    pmod(x, m, r);
+    for (int i = 0; i < e; ++i) {
+        pmulmod(r, r, m, t);
+        memcpy(r, t, sizeof t);
+    }
+}
+
+/*
+ * Rabin's irreducibility test for a degree-q polynomial over F_2:
+ * P is irreducible iff x^(2^q) = x (mod P) and, for every prime r dividing q,
+ * gcd(x^(2^(q/r)) - x mod P, P) = 1.
+ * Returns 1 if irreducible, 0 otherwise.
+ */
+int orc_is_irreducible(int q, const uint64_t *poly)
+{
+    uint64_t m[ORC_W2], r[ORC_W2], g[ORC_W2];
+    if (q < 1 || q > ORC_MAXQ) return 0;
+    memset(m, 0, sizeof m);
+    for (int d = 0; d <= q; ++d)
+        if (pbit(poly, d)) pset(m, d);
+    if (pdeg(m, ORC_W2) != q) return 0;
+    if (q == 1) return 1;
+    x_pow_2e(q, m, r);
+    pflip(r, 1);                                   /* r = x^(2^q) - x mod P */
+    if (pdeg(r, ORC_W2) >= 0) return 0;
+    int rem = q;
+    for (int p = 2; p <= rem; ++p) {
+        if (rem % p) continue;
+        while (rem % p == 0) rem /= p;
+        x_pow_2e(q / p, m, r);
+        pflip(r, 1);
+        pgcd(m, r, g);
+        if (pdeg(g, ORC_W2) != 0) return 0;
+    }
+    return 1;
+}
+
+/*
+ * Field polynomial choice (the paper leaves P_q open, Sec. 3.2): the
+ * lexicographically first irreducible polynomial of minimum weight.
+ *   q = 1: F_2 itself, P = x (multiplication is AND).
+ *   else a trinomial x^q + x^a + 1 with the smallest a, if one exists;
+ *   else a pentanomial x^q + x^c + x^b + x^a + 1, q > c > b > a >= 1,
+ *   minimising c, then b, then a.
+ * Writes the coefficient vector to poly (q/64+1 words) and the taps below q
+ * (descending, the constant term excluded) to taps[0..2] (unused = 0).
+ * Returns the weight (2, 3 or 5), or 0 if none was found.
+ */
+int orc_select_poly(int q, uint64_t *poly, int *taps)
+{
+    uint64_t p[ORC_W];
+    int nw = q / 64 + 1;
+    taps[0] = taps[1] = taps[2] = 0;
+    if (q == 1) {
+        memset(poly, 0, sizeof(uint64_t) * nw);
+        pset(poly, 1);
+        return 2;
+    }
+    for (int a = 1; a < q; ++a) {
+        memset(p, 0, sizeof p);
+        pset(p, q); pset(p, a); pset(p, 0);
+        if (orc_is_irreducible(q, p)) {
+            memcpy(poly, p, sizeof(uint64_t) * nw);
+            taps[0] = a;
+            return 3;
+        }
+    }
+    for (int c = 3; c < q; ++c)
+        for (int b = 2; b < c; ++b)
+            for (int a = 1; a < b; ++a) {
+                memset(p, 0, sizeof p);
+                pset(p, q); pset(p, c); pset(p, b); pset(p, a); pset(p, 0);
+                if (orc_is_irreducible(q, p)) {
+                    memcpy(poly, p, sizeof(uint64_t) * nw);
+                    taps[0] = c; taps[1] = b; taps[2] = a;
+                    return 5;
+                }
+            }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Inner-product extractor, Definition 3.2:                                  */
+/*   Ext_IP^{n,q}(x, y) = sum_{i=1..n} x_i * y_i   in GF(2^q).               */
+/* xs, ys: n_p elements, each (q+63)/64 words; out: (q+63)/64 words.         */
+/* ------------------------------------------------------------------------ */
+void orc_ext_ip(int q, int n_p, const uint64_t *poly, const uint64_t *xs, const uint64_t *ys, uint64_t *out)
+{
+    int ew = (q + 63) / 64;
+    uint64_t prod[ORC_W];
+    memset(out, 0, sizeof(uint64_t) * ew);
+    for (int i = 0; i < n_p; ++i) {
+        orc_gf_mul(q, poly, xs + (size_t)i * ew, ys + (size_t)i * ew, prod);
+        for (int w = 0; w < ew; ++w) out[w] ^= prod[w];   /* +_q is bitwise parity */
+    }
+}
+
+/* stream bit t of a word array */
+static int sbit(const uint32_t *s, uint64_t t) { return (int)((s[t >> 5] >> (t & 31)) & 1u); }
+
+/*
+ * Algorithm 1 (Ext_bs^eq) over nblocks whole blocks of two packed streams.
+ * For l = 1..nblocks: I_l is the next q*n_p stream bits of each source
+ * (consecutive, non-overlapping windows: the cursor advances by one block),
+ * Z^(l) = Ext_IP^{n_p,q}(X_{I_l}, Y_{I_l}), and Z^(l) is output in order,
+ * truncated to its first m bits.  out must hold ceil(nblocks*m/32) words and
+ * is fully overwritten.  threads <= 0 means "all available" (OpenMP builds).
+ * Returns 0, or -1 on bad arguments.
+ */
+int orc_extract(int q, int n_p, int m, const uint64_t *poly, const uint32_t *x, const uint32_t *y,
+                uint64_t nblocks, uint32_t *out, int threads)
+{
+    if (q < 1 || q > ORC_MAXQ || n_p < 1 || m < 1 || m > q) return -1;
+    uint64_t n = (uint64_t)q * (uint64_t)n_p;
+    uint64_t outw = (nblocks * (uint64_t)m + 31) / 32;
+    memset(out, 0, sizeof(uint32_t) * outw);
+    int ew = (q + 63) / 64;
+    (void)threads;
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+#pragma omp parallel
+#endif
+    {
+        uint64_t *xs = (uint64_t *)calloc((size_t)n_p * ew, sizeof(uint64_t));
+        uint64_t *ys = (uint64_t *)calloc((size_t)n_p * ew, sizeof(uint64_t));
+        uint64_t z[ORC_W];
+#ifdef _OPENMP
+#pragma omp for schedule(static)
+#endif
+        for (int64_t l = 0; l < (int64_t)nblocks; ++l) {
+            uint64_t base = (uint64_t)l * n;                     /* I_l starts here */
+            memset(xs, 0, sizeof(uint64_t) * (size_t)n_p * ew);
+            memset(ys, 0, sizeof(uint64_t) * (size_t)n_p * ew);
+            for (int i = 0; i < n_p; ++i)
+                for (int j = 0; j < q; ++j) {
+                    uint64_t t = base + (uint64_t)i * q + j;
+                    if (sbit(x, t)) pset(xs + (size_t)i * ew, j);
+                    if (sbit(y, t)) pset(ys + (size_t)i * ew, j);
+                }
+            orc_ext_ip(q, n_p, poly, xs, ys, z);                   /* Z^(l) */
+            for (int j = 0; j < m; ++j)                              /* first m bits */
+                if (pbit(z, j)) {
+                    uint64_t o = (uint64_t)l * m + j;
+                    /* blocks write disjoint bit ranges; word sharing is guarded */
+#ifdef _OPENMP
+#pragma omp atomic
+#endif
+                    out[o >> 5] |= (uint32_t)1 << (o & 31);
+                }
+        }
+        free(xs);
+        free(ys);
+    }
+    return 0;
+}
+
+/*
+ * log2 of the per-block error of Theorem 3.1 for an n-bit block (n = q*n_p)
+ * of min-entropy k bits (k = delta*q*n_p):
+ *   eps_blk = sqrt(3) * 2^(-1/4 - (delta/4 - 1/8) q n_p + 2q)
+ *   log2 eps_blk = log2(sqrt 3) - 1/4 - (k/4 - n/8) + 2q.
+ */
+double orc_log2_eps_block(uint32_t n, double k, uint32_t q)
+{
+    return 0.5 * log2(3.0) - 0.25 - (k / 4.0 - (double)n / 8.0) + 2.0 * (double)q;
+}
+
+/*
+ * Per-block plan from Definition 2.3's (t, m, k, eps) with t = n:
+ *   delta = k/n must exceed 1/2 (the construction needs rate > 1/2);
+ *   n_min = ceil(24 / (2 delta - 1)) (Algorithm 1's n), evaluated exactly as
+ *           the least integer d with d*(2k - n) >= 24n;
+ *   candidates: divisors d of n with d >= n_min, increasing, q = n/d;
+ *   pick the first with log2 eps_blk(q) <= log2 eps and (m == 0 or m <= q).
+ * m == 0 selects m = q (the whole field element, Theorem 3.4's output length).
+ * Returns 0 on success, -2 if delta <= 1/2, -3 if no candidate meets eps,
+ * -1 on bad arguments.
+ */
+int orc_plan(uint32_t n, uint32_t m, double k, double eps, uint32_t *n_p, uint32_t *q, uint32_t *m_out,
+             double *log2_eps)
+{
+    if (n == 0 || !(eps > 0.0) || !(eps < 1.0) || !(k > 0.0) || k > (double)n) return -1;
+    double gap = 2.0 * k - (double)n;
+    if (!(gap > 0.0)) return -2;
+    uint64_t dmin = 1;
+    while ((double)dmin * gap < 24.0 * (double)n) ++dmin;
+    double le = log2(eps);
+    for (uint64_t d = dmin; d <= n; ++d) {
+        if (n % d) continue;
+        uint32_t qq = (uint32_t)(n / d);
+        double l2 = orc_log2_eps_block(n, k, qq);
+        if (l2 <= le && (m == 0 || m <= qq)) {
+            *n_p = (uint32_t)d;
+            *q = qq;
+            *m_out = m ? m : qq;
+            *log2_eps = l2;
+            return 0;
+        }
+    }
+    return -3;
+}
+
+/*
+ * Algorithm 1's own parameter line: n = ceil(24/(2 delta - 1)),
+ * q = b * ceil(log2(N / (eps n)) / b), for N samples of b bits.
+ * Returns 0, or -2 if delta <= 1/2, -1 on bad arguments.
+ */
+int orc_alg1_params(double N, uint32_t b, double delta, double eps, uint32_t *n_p, uint32_t *q)
+{
+    if (!(N > 0) || b == 0 || !(eps > 0) || !(eps < 1)) return -1;
+    if (!(delta > 0.5)) return -2;
+    double nn = ceil(24.0 / (2.0 * delta - 1.0));
+    double qq = (double)b * ceil(log2(N / (eps * nn)) / (double)b);
+    *n_p = (uint32_t)nn;
+    *q = (uint32_t)qq;
+    return 0;
+}
+
+/*
+ * Ingest: pack nsamples samples of b bits (b <= 16, taken from the low bits of
+ * each uint16) into a stream, sample s at stream bits [s*b, (s+1)*b), LSB
+ * first (the raw data X = X_1 ... X_N in ({0,1}^b)^N of Sec. 3).
+ * out must hold ceil(nsamples*b/32) words and is fully overwritten.
+ */
+void orc_pack_samples(uint32_t b, const uint16_t *samples, uint64_t nsamples, uint32_t *out)
+{
+    uint64_t nbits = nsamples * b;
+    memset(out, 0, sizeof(uint32_t) * ((nbits + 31) / 32));
+    for (uint64_t s = 0; s < nsamples; ++s)
+        for (uint32_t j = 0; j < b; ++j)
+            if ((samples[s] >> j) & 1u) {
+                uint64_t t = s * b + j;
+                out[t >> 5] |= (uint32_t)1 << (t & 31);
+            }
+}
+
+int orc_max_q(void) { return ORC_MAXQ; }
+
+int orc_has_openmp(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 0;
+#endif
+}
