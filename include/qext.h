@@ -1,0 +1,162 @@
+/*
+ * qext.h -- C ABI of the GB300 (sm_103a) implementation of the block-wise
+ * seedless two-source extractor Ext_bs^eq of Li & Zhou, "Real-Time Seedless
+ * Post-Processing for Quantum Random Number Generators" (arXiv 2402.14607).
+ *
+ * What is computed (Algorithm 1 with the inner-product gadget, Def. 3.2):
+ *   two raw bit streams x, y are cut into consecutive, non-overlapping
+ *   n-bit blocks; block l of each stream is read as n_p elements of GF(2^q)
+ *   (n = q * n_p); the block pair maps to
+ *       Z^(l) = Ext_IP^{n_p,q}(x_l, y_l) = sum_{i<n_p} x_{l,i} * y_{l,i}
+ *   in GF(2^q); Z^(l) is truncated to its first m coefficients and the
+ *   outputs are concatenated in block order.  All arithmetic is exact GF(2).
+ *
+ * Bit conventions (the paper fixes none; these are this library's):
+ *   - streams are arrays of uint32 words, little-endian; stream bit t is bit
+ *     (t mod 32) of word t/32;
+ *   - block l is stream bits [l*n, (l+1)*n); element i of a block is bits
+ *     [i*q, (i+1)*q) of the block; element bit j is the coefficient of
+ *     alpha^j;
+ *   - GF(2^q) = F_2[alpha]/P(alpha) with P the minimum-weight irreducible
+ *     polynomial of degree q that comes first in the order x^q + x^a + 1
+ *     (smallest a), then x^q + x^c + x^b + x^a + 1 (smallest c, then b,
+ *     then a); q = 1 is F_2 itself;
+ *   - output: Z^(l)'s coefficients alpha^0..alpha^(m-1) occupy output bits
+ *     [l*m, (l+1)*m); bits of the last output word past nblocks*m are 0.
+ *
+ * Errors: every call returns QEXT_OK (0) or a negative QEXT_E_* code; no call
+ * aborts or prints.  Calls that enqueue GPU work are asynchronous on the given
+ * stream and report launch errors only; a kernel that gives up a bounded wait
+ * records QEXT_E_TIMEOUT in a device status word read by qext_device_status.
+ *
+ * Threading: a plan is immutable after creation and may be used from several
+ * host threads and streams at once.  A qext_stream is not thread-safe.
+ */
+#ifndef QEXT_H
+#define QEXT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as the CUDA runtime's cudaStream_t; NULL = the legacy default
+ * stream. */
+typedef struct CUstream_st *qext_cuda_stream;
+
+#define QEXT_OK 0
+#define QEXT_E_INVAL (-1)       /* null / misaligned pointer, bad size or argument   */
+#define QEXT_E_ENTROPY (-2)     /* min-entropy rate k/n <= 1/2: no guarantee (Sec. 5) */
+#define QEXT_E_PARAM (-3)       /* no block factorisation meets eps (Thm 3.1)         */
+#define QEXT_E_UNSUPPORTED (-4) /* field size q has no GPU kernel in this build       */
+#define QEXT_E_CUDA (-5)        /* a CUDA runtime call failed                         */
+#define QEXT_E_TIMEOUT (-6)     /* a kernel gave up a bounded wait                    */
+#define QEXT_E_BUDGET (-7)      /* device-memory budget exhausted (admission)         */
+#define QEXT_E_STATE (-8)       /* object used in a state that forbids the call       */
+#define QEXT_E_NOSPACE (-9)     /* caller's output buffer too small                   */
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char *qext_status_string(int status);
+
+/* ------------------------------------------------------------------------
+ * Plans.
+ * ------------------------------------------------------------------------ */
+typedef struct qext_plan qext_plan; /* opaque, host-owned */
+
+/*
+ * qext_plan_create -- parameters of one block application of the extractor,
+ * from Definition 2.3's (t, m, k, epsilon) with t = n.
+ *   n    bits per block per source (the paper's q*n).  The GPU kernels need
+ *        n to be a multiple of 32 (whole words per block).
+ *   m    output bits per block, 1 <= m <= q; 0 selects m = q (Theorem 3.4's
+ *        output length m = N b / n_p over a stream).
+ *   k    min-entropy of one n-bit block of either source, in bits (the
+ *        forward-block-source rate of Def. 3.1 gives k = delta * n).
+ *   eps  per-block error target, 0 < eps < 1.
+ * Choice (Algorithm 1 and Theorem 3.1): delta = k/n must exceed 1/2;
+ * n_min = ceil(24/(2 delta - 1)); the divisors d of n with d >= n_min are
+ * tried in increasing order with q = n/d and the first one with
+ *   log2 eps_blk = log2 sqrt(3) - 1/4 - (k/4 - n/8) + 2q  <=  log2 eps
+ * and m <= q is taken (n_p = d).  The field polynomial is generated and
+ * checked for irreducibility here.
+ * Host-only: touches no GPU.  *out receives a plan to free with qext_destroy.
+ * Errors: INVAL (null out, n = 0, k outside (0, n], eps outside (0, 1)),
+ * ENTROPY (k/n <= 1/2), PARAM (no divisor meets eps and m).  A plan with no
+ * GPU kernel (q outside the built set, or n not a multiple of 32) is still
+ * created; qext_extract then returns UNSUPPORTED (qext_plan_info reports it).
+ */
+int qext_plan_create(uint32_t n, uint32_t m, double k, double eps, qext_plan **out);
+
+/* Frees a plan (NULL is accepted).  The plan must not be in use by queued
+ * GPU work: synchronise the streams that used it first. */
+int qext_destroy(qext_plan *p);
+
+/*
+ * qext_plan_info -- the chosen parameters.  Any output pointer may be NULL.
+ *   q, n_p, m          as chosen (n = q * n_p);
+ *   log2_eps_block     Theorem 3.1's per-block error, log2;
+ *   poly_taps[4]       exponents of P below q, descending, then zeros
+ *                      (the constant term 1 and x^q are implied);
+ *   gpu_supported      1 if qext_extract has a kernel for this plan
+ *                      (q in {1,2,4,8,16,32,64} and n a multiple of 32).
+ * The error of a stream of L blocks is at most L * 2^log2_eps_block
+ * (Theorem 3.3's sum with equal q).
+ */
+int qext_plan_info(const qext_plan *p, uint32_t *q, uint32_t *n_p, uint32_t *m, double *log2_eps_block,
+                   uint64_t poly_taps[4], int *gpu_supported);
+
+/*
+ * qext_alg1_params -- Algorithm 1's own parameter line for N samples of b
+ * bits, rate delta, whole-stream error eps:
+ *   n_p = ceil(24 / (2 delta - 1)),  q = b * ceil(log2(N / (eps n_p)) / b).
+ * Host-only.  Errors: INVAL (bad N, b, eps or null outputs), ENTROPY
+ * (delta <= 1/2).
+ */
+int qext_alg1_params(double N_samples, uint32_t b, double delta, double eps, uint32_t *n_p, uint32_t *q);
+
+/* ------------------------------------------------------------------------
+ * Stateless extraction over whole blocks (Algorithm 1's loop body).
+ * ------------------------------------------------------------------------ */
+
+/*
+ * qext_extract -- Z^(l) for l = 0 .. nblocks-1 (Algorithm 1, Def. 3.2).
+ *   x, y   DEVICE pointers to nblocks*n bits each (nblocks*n/32 words),
+ *          4-byte aligned; 16-byte alignment selects the vectorised path.
+ *   out    DEVICE pointer to ceil(nblocks*m/32) words; fully written (the
+ *          unused high bits of the last word are zero).  Must not overlap x
+ *          or y.
+ *   stream CUDA stream the kernel is enqueued on (asynchronous).
+ * The caller owns all three buffers.  nblocks = 0 enqueues nothing.
+ * Errors: INVAL (null plan or pointer, misalignment), UNSUPPORTED (q has no
+ * kernel: this build covers q in {1, 2, 4, 8, 16, 32, 64}), CUDA (launch).
+ */
+int qext_extract(const qext_plan *p, const uint32_t *x, const uint32_t *y, uint64_t nblocks, uint32_t *out,
+                 qext_cuda_stream stream);
+
+/*
+ * qext_pack_samples -- ingest: raw ADC samples to a packed stream.  Sample s
+ * (b bits, the low bits of samples[s]) occupies stream bits [s*b, (s+1)*b)
+ * (Sec. 3: X = X_1 ... X_N in ({0,1}^b)^N).
+ *   samples DEVICE pointer to nsamples uint16 values, 2-byte aligned; bits
+ *           above b are ignored.
+ *   out     DEVICE pointer to ceil(nsamples*b/32) words, fully written.
+ *   1 <= b <= 16.  Asynchronous on stream.
+ * Errors: INVAL, CUDA.
+ */
+int qext_pack_samples(uint32_t b, const uint16_t *samples, uint64_t nsamples, uint32_t *out,
+                      qext_cuda_stream stream);
+
+/*
+ * qext_device_status -- reads and clears the device status word of the
+ * current device (QEXT_OK or QEXT_E_TIMEOUT from a kernel that gave up a
+ * bounded wait).  Synchronises the device.  Errors: CUDA.
+ */
+int qext_device_status(int *status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QEXT_H */

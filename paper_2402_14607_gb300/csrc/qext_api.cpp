@@ -1,0 +1,37 @@
+// C ABI entry points that enqueue GPU work: argument checks, then the
+// launchers of the .cu translation units.  Declarations and contracts are in
+// include/qext.h.
+#include <cstdint>
+
+#include "qext_internal.h"
+
+namespace {
+bool aligned(const void *p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+}  // namespace
+
+extern "C" {
+
+int qext_extract(const qext_plan *p, const uint32_t *x, const uint32_t *y, uint64_t nblocks, uint32_t *out,
+                 qext_cuda_stream stream) {
+    if (!p) return QEXT_E_INVAL;
+    if (!p->gpu_supported) return QEXT_E_UNSUPPORTED;
+    if (nblocks == 0) return QEXT_OK;
+    if (!x || !y || !out || !aligned(x, 4) || !aligned(y, 4) || !aligned(out, 4)) return QEXT_E_INVAL;
+    if (nblocks > (UINT64_MAX / p->n)) return QEXT_E_INVAL;
+    return qext::launch_extract(p, x, y, nblocks, out, stream);
+}
+
+int qext_pack_samples(uint32_t b, const uint16_t *samples, uint64_t nsamples, uint32_t *out,
+                      qext_cuda_stream stream) {
+    if (b < 1 || b > 16) return QEXT_E_INVAL;
+    if (nsamples == 0) return QEXT_OK;
+    if (!samples || !out || !aligned(samples, 2) || !aligned(out, 4)) return QEXT_E_INVAL;
+    return qext::launch_pack(b, samples, nsamples, out, stream);
+}
+
+int qext_device_status(int *status) {
+    if (!status) return QEXT_E_INVAL;
+    return qext::read_device_status(status);
+}
+
+}  // extern "C"

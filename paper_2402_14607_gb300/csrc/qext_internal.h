@@ -1,0 +1,34 @@
+// Internal declarations shared by the translation units of libqext.
+#pragma once
+
+#include <cstdint>
+
+#include "../../include/qext.h"
+
+// An immutable extraction plan (Definition 2.3's (t, m, k, eps) resolved to a
+// block factorisation n = q * n_p and a field polynomial).
+struct qext_plan {
+    uint32_t n;          // block bits per source
+    uint32_t n_p;        // field elements per block
+    uint32_t q;          // field degree
+    uint32_t m;          // output bits per block
+    double k;            // min-entropy per block (bits)
+    double eps;          // per-block error target
+    double log2_eps;     // Theorem 3.1's per-block error, log2
+    uint32_t ntaps;      // number of entries of taps[] used
+    uint32_t taps[4];    // exponents of P(x) - x^q, descending, ending with 0
+    int gpu_supported;   // a kernel exists for this q
+};
+
+namespace qext {
+
+// Field degrees with a GPU kernel.
+bool gpu_q_supported(uint32_t q);
+
+// Ingest and extraction launchers (defined in the .cu files).
+int launch_extract(const qext_plan *p, const uint32_t *x, const uint32_t *y, uint64_t nblocks, uint32_t *out,
+                   qext_cuda_stream stream);
+int launch_pack(uint32_t b, const uint16_t *samples, uint64_t nsamples, uint32_t *out, qext_cuda_stream stream);
+int read_device_status(int *status);
+
+}  // namespace qext

@@ -1,0 +1,151 @@
+"""Thin Python binding of libqext (include/qext.h): the same names, argument
+marshalling only.  Every computation runs in the CUDA library; if the library
+is not built this module raises instead of computing anything itself.
+
+Pointers may be given as integers or as torch tensors (their data_ptr());
+streams as None (torch's current stream), a torch.cuda.Stream, or an int
+handle.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libqext.so")
+
+QEXT_OK = 0
+QEXT_E_INVAL = -1
+QEXT_E_ENTROPY = -2
+QEXT_E_PARAM = -3
+QEXT_E_UNSUPPORTED = -4
+QEXT_E_CUDA = -5
+QEXT_E_TIMEOUT = -6
+QEXT_E_BUDGET = -7
+QEXT_E_STATE = -8
+QEXT_E_NOSPACE = -9
+
+_lib = None
+
+
+class QextError(RuntimeError):
+    def __init__(self, code: int, where: str = ""):
+        self.code = code
+        super().__init__("%s%s" % (where + ": " if where else "", qext_status_string(code)))
+
+
+def lib():
+    """The loaded libqext (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libqext.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+    L = ctypes.CDLL(LIB_PATH)
+    vp, u32, u64, dbl, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double, ctypes.c_int
+    P = ctypes.POINTER
+    L.qext_status_string.argtypes = [i32]
+    L.qext_status_string.restype = ctypes.c_char_p
+    L.qext_plan_create.argtypes = [u32, u32, dbl, dbl, P(vp)]
+    L.qext_destroy.argtypes = [vp]
+    L.qext_plan_info.argtypes = [vp, P(u32), P(u32), P(u32), P(dbl), P(u64), P(i32)]
+    L.qext_alg1_params.argtypes = [dbl, u32, dbl, dbl, P(u32), P(u32)]
+    L.qext_extract.argtypes = [vp, vp, vp, u64, vp, vp]
+    L.qext_pack_samples.argtypes = [u32, vp, u64, vp, vp]
+    L.qext_device_status.argtypes = [P(i32)]
+    for name in ["qext_plan_create", "qext_destroy", "qext_plan_info", "qext_alg1_params", "qext_extract",
+                 "qext_pack_samples", "qext_device_status"]:
+        getattr(L, name).restype = i32
+    _lib = L
+    return L
+
+
+def _check(rc: int, where: str):
+    if rc != QEXT_OK:
+        raise QextError(rc, where)
+
+
+def _ptr(p):
+    if p is None:
+        return None
+    if isinstance(p, int):
+        return p
+    return int(p.data_ptr())
+
+
+def _stream(s):
+    if s is None:
+        import torch
+        return int(torch.cuda.current_stream().cuda_stream)
+    if isinstance(s, int):
+        return s
+    return int(s.cuda_stream)
+
+
+def qext_status_string(code: int) -> str:
+    return lib().qext_status_string(code).decode()
+
+
+class Plan:
+    """Owns a qext_plan handle (freed on close / garbage collection)."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+
+    def close(self):
+        if self.handle:
+            lib().qext_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def info(self):
+        return qext_plan_info(self)
+
+
+def qext_plan_create(n: int, m: int, k: float, eps: float) -> Plan:
+    h = ctypes.c_void_p()
+    _check(lib().qext_plan_create(n, m, k, eps, ctypes.byref(h)), "qext_plan_create")
+    return Plan(h.value)
+
+
+def qext_destroy(plan: Plan) -> None:
+    plan.close()
+
+
+def qext_plan_info(plan: Plan) -> dict:
+    q, n_p, m = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+    le = ctypes.c_double()
+    taps = (ctypes.c_uint64 * 4)()
+    sup = ctypes.c_int()
+    _check(lib().qext_plan_info(plan.handle, ctypes.byref(q), ctypes.byref(n_p), ctypes.byref(m),
+                                ctypes.byref(le), taps, ctypes.byref(sup)), "qext_plan_info")
+    return dict(q=q.value, n_p=n_p.value, n=q.value * n_p.value, m=m.value, log2_eps_block=le.value,
+                taps=tuple(int(t) for t in taps if t), gpu_supported=bool(sup.value))
+
+
+def qext_alg1_params(N_samples: float, b: int, delta: float, eps: float):
+    n_p, q = ctypes.c_uint32(), ctypes.c_uint32()
+    _check(lib().qext_alg1_params(N_samples, b, delta, eps, ctypes.byref(n_p), ctypes.byref(q)),
+           "qext_alg1_params")
+    return n_p.value, q.value
+
+
+def qext_extract(plan: Plan, x, y, nblocks: int, out, stream=None) -> None:
+    _check(lib().qext_extract(plan.handle, _ptr(x), _ptr(y), nblocks, _ptr(out), _stream(stream)),
+           "qext_extract")
+
+
+def qext_pack_samples(b: int, samples, nsamples: int, out, stream=None) -> None:
+    _check(lib().qext_pack_samples(b, _ptr(samples), nsamples, _ptr(out), _stream(stream)), "qext_pack_samples")
+
+
+def qext_device_status() -> int:
+    st = ctypes.c_int()
+    _check(lib().qext_device_status(ctypes.byref(st)), "qext_device_status")
+    return st.value

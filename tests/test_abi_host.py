@@ -1,0 +1,126 @@
+"""Host-side checks of libqext: it loads without a GPU, exports every symbol
+declared in include/qext.h, and its plan logic (block factorisation, error
+bound, field polynomial) agrees with the oracle.  No GPU work is issued."""
+import math
+import os
+import re
+
+import pytest
+
+import oracle
+from paper_2402_14607_gb300 import build as qbuild
+from paper_2402_14607_gb300 import qext
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    qbuild.build()
+    yield
+
+
+def declared_functions():
+    names = set()
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(qext_\w+)\s*\(", text))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol():
+    names = declared_functions()
+    assert "qext_extract" in names and "qext_plan_create" in names
+    L = qext.lib()
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_status_strings():
+    for code in range(-9, 1):
+        s = qext.qext_status_string(code)
+        assert s.startswith("QEXT_")
+    assert "UNKNOWN" in qext.qext_status_string(-1234)
+
+
+PLAN_CASES = [
+    (256, 0, 202, 2.0 ** -9), (1024, 0, 867, 2.0 ** -50), (1024, 0, 867, 2.0 ** -60),
+    (4096, 0, 3485, 2.0 ** -52), (4096, 0, 3510, 2.0 ** -52), (1024, 0, 809, 2.0 ** -50),
+    (5680, 80, 0.67125 * 5680, 2.0 ** -30), (2048, 40, 1800, 2.0 ** -60), (2048, 0, 1800, 2.0 ** -100),
+    (384, 0, 240, 0.5), (512, 7, 450, 2.0 ** -10), (96, 0, 90, 0.25), (2240, 0, 2000, 2.0 ** -70),
+]
+
+
+@pytest.mark.parametrize("n,m,k,eps", PLAN_CASES)
+def test_plan_matches_oracle(n, m, k, eps):
+    want = oracle.plan(n, m, k, eps)
+    p = qext.qext_plan_create(n, m, k, eps)
+    got = p.info
+    assert (got["n_p"], got["q"], got["m"]) == (want["n_p"], want["q"], want["m"])
+    assert abs(got["log2_eps_block"] - want["log2_eps"]) < 1e-9
+    assert got["taps"] == want["taps"]
+    assert got["gpu_supported"] == (got["q"] in (1, 2, 4, 8, 16, 32, 64) and n % 32 == 0)
+
+
+@pytest.mark.parametrize("n,m,k,eps,code", [
+    (1024, 0, 512, 0.5, qext.QEXT_E_ENTROPY),
+    (256, 0, 202, 2.0 ** -40, qext.QEXT_E_PARAM),
+    (0, 0, 900, 0.5, qext.QEXT_E_INVAL),           # n = 0
+    (1024, 0, 2000, 0.5, qext.QEXT_E_INVAL),       # k > n
+    (1024, 0, 900, 1.5, qext.QEXT_E_INVAL),
+    (1024, 0, 900, 0.0, qext.QEXT_E_INVAL),
+    (1024, 32, 867, 2.0 ** -50, qext.QEXT_E_PARAM),  # m larger than any feasible q
+])
+def test_plan_rejections(n, m, k, eps, code):
+    with pytest.raises(qext.QextError) as e:
+        qext.qext_plan_create(n, m, k, eps)
+    assert e.value.code == code
+    if code != qext.QEXT_E_INVAL:
+        with pytest.raises(oracle.PlanError):
+            oracle.plan(n, m, k, eps)
+
+
+@pytest.mark.parametrize("q", [2, 3, 4, 5, 8, 16, 24, 32, 48, 64, 80, 96, 128])
+def test_field_polynomial_matches_oracle(q):
+    # a plan whose only feasible factorisation has this q: n_p = 32 and a
+    # rate close to 1
+    n = 32 * q
+    p = qext.qext_plan_create(n, 0, n - 0.5, 0.5)
+    info = p.info
+    if info["q"] != q:
+        pytest.skip("plan chose q=%d" % info["q"])
+    assert info["taps"] == oracle.select_poly(q)[1]
+
+
+def test_alg1_params_worked_example():
+    assert qext.qext_alg1_params(2.0 ** 51, 16, 10.74 / 16, 2.0 ** -30) == (71, 80)
+    assert qext.qext_alg1_params(2.0 ** 51, 16, 10.74 / 16, 2.0 ** -30) == oracle.alg1_params(
+        2.0 ** 51, 16, 10.74 / 16, 2.0 ** -30)
+    with pytest.raises(qext.QextError) as e:
+        qext.qext_alg1_params(1e6, 8, 0.5, 1e-3)
+    assert e.value.code == qext.QEXT_E_ENTROPY
+
+
+def test_paper_q80_plan_is_created_but_has_no_kernel():
+    p = qext.qext_plan_create(5680, 80, 0.67125 * 5680, 2.0 ** -30)
+    info = p.info
+    assert (info["n_p"], info["q"]) == (71, 80) and not info["gpu_supported"]
+    assert info["log2_eps_block"] < math.log2(2.0 ** -30)
+    # qext_extract refuses before touching any pointer or device
+    with pytest.raises(qext.QextError) as e:
+        qext.qext_extract(p, 0, 0, 1, 0, 0)
+    assert e.value.code == qext.QEXT_E_UNSUPPORTED
+
+
+def test_extract_argument_checks_without_gpu():
+    p = qext.qext_plan_create(1024, 0, 867, 2.0 ** -50)
+    for args in [(0, 16, 1, 16), (16, 0, 1, 16), (16, 16, 1, 0), (18, 16, 1, 16), (16, 16, 1, 2)]:
+        with pytest.raises(qext.QextError) as e:
+            qext.qext_extract(p, *args, stream=0)
+        assert e.value.code == qext.QEXT_E_INVAL
+    qext.qext_extract(p, 0, 0, 0, 0, stream=0)    # nblocks = 0: nothing to do
+    with pytest.raises(qext.QextError) as e:
+        qext.qext_pack_samples(17, 16, 4, 16, stream=0)
+    assert e.value.code == qext.QEXT_E_INVAL

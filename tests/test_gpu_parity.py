@@ -1,0 +1,141 @@
+"""GPU parity: libqext's kernels against the CPU oracle, bit for bit, through
+the C ABI.  Sizes span several CTAs and warps with ragged tails; block
+layouts cover partial element groups and 4-byte-aligned pointers."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2402_14607_gb300 import build as qbuild
+from paper_2402_14607_gb300 import qext, workloads
+from tests.gpu_util import bits_at, dev_words, gpu_extract, host_words, oracle_extract, plan_for
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    qbuild.build()
+    oracle.build()
+
+
+CASES = [
+    # q, n_p, m, nblocks, pointer offset in words
+    (1, 64, 1, 1000, 0), (1, 96, 1, 77, 1),
+    (2, 64, 2, 1000, 0), (2, 48, 1, 333, 1),
+    (4, 64, 4, 4099, 0), (4, 64, 3, 1001, 0), (4, 72, 4, 257, 1), (4, 40, 2, 65, 0),
+    (8, 64, 8, 1000, 0), (8, 68, 5, 130, 0), (8, 32, 8, 95, 3),
+    (16, 64, 16, 4133, 0), (16, 64, 13, 1000, 0), (16, 70, 16, 97, 1), (16, 26, 9, 200, 0), (16, 64, 1, 31, 2),
+    (32, 64, 32, 500, 0), (32, 33, 17, 65, 1), (32, 25, 32, 40, 0),
+    (64, 64, 64, 300, 0), (64, 71, 41, 70, 1), (64, 64, 1, 100, 0), (64, 25, 64, 33, 0), (64, 64, 63, 257, 2),
+]
+
+
+@pytest.mark.parametrize("q,n_p,m,nblocks,off", CASES)
+def test_extract_matches_oracle(q, n_p, m, nblocks, off):
+    plan = plan_for(q, n_p, m)
+    n = q * n_p
+    rng = np.random.Generator(np.random.PCG64(q * 1000 + n_p + m))
+    words = nblocks * n // 32
+    x = workloads.random_words(int(rng.integers(1 << 30)), words)
+    y = workloads.random_words(int(rng.integers(1 << 30)), words)
+    got = gpu_extract(plan, x, y, nblocks, offset_words=off)
+    want = oracle_extract(plan, x, y, nblocks)
+    assert got.shape == want.shape
+    bad = np.nonzero(got != want)[0]
+    assert bad.size == 0, "first mismatching output word %d" % bad[0]
+
+
+@pytest.mark.parametrize("q", [4, 16, 64])
+def test_degenerate_inputs(q):
+    """All-zero sources give Z = 0; a zero block on one side zeroes its Z;
+    one block and nblocks = 0 work."""
+    plan = plan_for(q, 64)
+    words = 64 * q // 32
+    nb = 70
+    x = workloads.random_words(7, nb * words)
+    y = workloads.random_words(8, nb * words)
+    y[: words] = 0
+    z = np.zeros_like(x)
+    assert (gpu_extract(plan, z, y, nb) == 0).all()
+    got = gpu_extract(plan, x, y, nb)
+    assert bits_at(got, 0, q) == 0
+    assert (got == oracle_extract(plan, x, y, nb)).all()
+    one = gpu_extract(plan, x[:words], y[:words], 1)
+    assert (one == oracle_extract(plan, x[:words], y[:words], 1)).all()
+    qext.qext_extract(plan, dev_words(x), dev_words(y), 0, dev_words(np.zeros(1, np.uint32)))
+    # all-ones sources
+    ones = np.full(nb * words, 0xFFFFFFFF, np.uint32)
+    assert (gpu_extract(plan, ones, ones, nb) == oracle_extract(plan, ones, ones, nb)).all()
+
+
+@pytest.mark.parametrize("b,ns", [(8, 4096), (12, 1001), (12, 8), (16, 33), (1, 999), (5, 77), (3, 1), (11, 640)])
+def test_pack_matches_oracle(b, ns):
+    s = workloads.adc_samples(b * 7 + ns, ns, b)
+    s = s | np.uint16(0xFFFF ^ ((1 << b) - 1)) if b < 16 else s   # garbage above b must be ignored
+    ts = torch.from_numpy(s.view(np.int16)).cuda()
+    nw = -(-ns * b // 32)
+    out = torch.full((nw + 4,), -1, dtype=torch.int32, device="cuda")
+    qext.qext_pack_samples(b, ts, ns, out)
+    torch.cuda.synchronize()
+    got = host_words(out)
+    assert (got[nw:] == 0xFFFFFFFF).all()
+    want = oracle.pack_samples(b, s & np.uint16((1 << b) - 1))
+    assert (got[:nw] == want).all()
+
+
+def test_config_plain_small_end_to_end():
+    """4096 blocks x 256 bits, 8-bit ADC, seeds 0/1: GPU ingest + extraction
+    against the oracle's ingest + extraction, every output bit."""
+    spec = workloads.config_plain_small()
+    plan = qext.qext_plan_create(spec.n, 0, spec.k, spec.eps)
+    info = plan.info
+    assert (info["q"], info["n_p"]) == (4, 64)
+    sx, sy = spec.samples("x"), spec.samples("y")
+    words = spec.nbits // 32
+    px = torch.empty(words, dtype=torch.int32, device="cuda")
+    py = torch.empty(words, dtype=torch.int32, device="cuda")
+    qext.qext_pack_samples(spec.b, torch.from_numpy(sx.view(np.int16)).cuda(), sx.size, px)
+    qext.qext_pack_samples(spec.b, torch.from_numpy(sy.view(np.int16)).cuda(), sy.size, py)
+    out = torch.empty(spec.nblocks * info["m"] // 32, dtype=torch.int32, device="cuda")
+    qext.qext_extract(plan, px, py, spec.nblocks, out)
+    torch.cuda.synchronize()
+    poly, _ = oracle.select_poly(info["q"])
+    ox, oy = oracle.pack_samples(spec.b, sx), oracle.pack_samples(spec.b, sy)
+    want = oracle.extract(info["q"], info["n_p"], info["m"], poly, ox, oy, spec.nblocks)
+    assert want.size * 32 == spec.nblocks * info["q"] == spec.nbits // info["n_p"]   # Theorem 3.4
+    assert (host_words(out) == want).all()
+
+
+def test_config_large_single_stream_sampled():
+    """2^20 blocks x 1024 bits (12-bit ADC, bias offset): the full-size launch,
+    checked on sampled blocks (each recomputed by the oracle alone) and on the
+    output length."""
+    spec = workloads.config_large_single()
+    plan = qext.qext_plan_create(spec.n, 0, spec.k, spec.eps)
+    info = plan.info
+    assert (info["q"], info["n_p"], info["m"]) == (16, 64, 16)
+    words = spec.nbits // 32
+    out_words = spec.nblocks * info["m"] // 32
+    sx, sy = spec.samples("x"), spec.samples("y")
+    px = torch.empty(-(-sx.size * 12 // 32), dtype=torch.int32, device="cuda")
+    py = torch.empty_like(px)
+    qext.qext_pack_samples(12, torch.from_numpy(sx.view(np.int16)).cuda(), sx.size, px)
+    qext.qext_pack_samples(12, torch.from_numpy(sy.view(np.int16)).cuda(), sy.size, py)
+    out = torch.full((out_words + 4,), -1, dtype=torch.int32, device="cuda")
+    qext.qext_extract(plan, px, py, spec.nblocks, out)
+    torch.cuda.synchronize()
+    got = host_words(out)
+    assert (got[out_words:] == 0xFFFFFFFF).all()
+    ox = oracle.pack_samples(12, sx)[:words]
+    oy = oracle.pack_samples(12, sy)[:words]
+    assert (host_words(px)[:words] == ox).all() and (host_words(py)[:words] == oy).all()
+    rng = np.random.Generator(np.random.PCG64(99))
+    sample = np.unique(np.concatenate([rng.integers(0, spec.nblocks, 3000), np.arange(40),
+                                       np.arange(spec.nblocks - 40, spec.nblocks)]))
+    poly, _ = oracle.select_poly(16)
+    wpb = spec.n // 32
+    for l in sample:
+        l = int(l)
+        z = oracle.extract(16, 64, 16, poly, ox[l * wpb:(l + 1) * wpb], oy[l * wpb:(l + 1) * wpb], 1)
+        assert bits_at(got, l * 16, 16) == int(z[0]), "block %d" % l
