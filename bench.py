@@ -1,0 +1,329 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the block-wise two-source extraction hot path.
+
+A step is one pass of the path over one batch of synthetic raw data: ingest
+(pack the 12-bit ADC samples of both sources into bit streams) and per-block
+extraction Ext_IP^{64,16} over 2^20 block pairs of 1024 bits (1 Gbit per
+source), output truncated to m = q = 16 bits per block.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl qext|reference]
+
+Prints one JSON line (rank 0).  ``value`` is extracted Gbps over all ranks
+with inputs resident in HBM; ``e2e`` is the same metric with the raw samples
+copied host->device (pinned) and the output copied back inside each step.
+``--impl reference`` times the CPU oracle on bounded samples of the same
+workload (host cores).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "extracted Gbps on 1 GB300 (bit-exact), %HBM roofline; serving p50/p99 ms"
+UNIT = "Gbps"
+L2_BYTES = 126 << 20
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def max_over_ranks(value: float, world: int) -> float:
+    """Max of a per-rank float over all ranks (identity when world == 1)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def workload_spec(rank: int, nblocks: int):
+    from paper_2402_14607_gb300 import workloads
+    spec = workloads.config_large_single(nblocks)
+    # independent raw streams per rank (weak scaling: fixed work per GPU)
+    spec.seed_x += 1000 * rank
+    spec.seed_y += 1000 * rank
+    return spec
+
+
+def workload_config(spec, info, world):
+    return {
+        "workload": "large single stream: %d block pairs x %d bits (%.2f Gbit/source), %d-bit ADC samples "
+                    "(uint16) with bias offset U(-0.05,0.05) sigma, packed then extracted" %
+                    (spec.nblocks, spec.n, spec.nbits / 2 ** 30, spec.b),
+        "n": spec.n, "nblocks": spec.nblocks, "b": spec.b, "k": spec.k, "eps_block": spec.eps,
+        "q": info["q"], "n_p": info["n_p"], "m": info["m"], "log2_eps_block": round(info["log2_eps_block"], 2),
+        "step": "qext_pack_samples(x), qext_pack_samples(y), qext_extract",
+        "l2": "inputs larger than L2 (%.0f MB of samples per step)" % (2 * spec.nsamples * 2 / 1e6),
+        "parallelism": "blocks sharded per rank, no collective" if world > 1 else "single GPU",
+    }
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg (the only part of this file that runs oracle code)
+# ---------------------------------------------------------------------------
+def run_oracle_sample(spec, sx, sy, nblocks, threads):
+    import oracle
+    info_q = None
+    p = oracle.plan(spec.n, 0, spec.k, spec.eps)
+    info_q = (p["q"], p["n_p"], p["m"], p["poly"])
+    ns = -(-nblocks * spec.n // spec.b)
+    t0 = time.perf_counter()
+    ox = oracle.pack_samples(spec.b, sx[:ns])
+    oy = oracle.pack_samples(spec.b, sy[:ns])
+    out = oracle.extract(info_q[0], info_q[1], info_q[2], info_q[3], ox, oy, nblocks, threads=threads)
+    dt = time.perf_counter() - t0
+    return out, dt, info_q[2]
+
+
+def cpu_baseline(spec, sx, sy, gpu_out_words, sample_blocks):
+    threads = os.cpu_count() or 1
+    out, dt, m = run_oracle_sample(spec, sx, sy, sample_blocks, threads)
+    match = None
+    if gpu_out_words is not None:
+        nw = out.size
+        match = bool((gpu_out_words[:nw] == out).all()) if sample_blocks * m % 32 == 0 else None
+    return {
+        "value": round(sample_blocks * m / dt / 1e9, 6), "unit": UNIT, "cores": threads, "kind": "oracle",
+        "sample": "first %d block pairs of the same workload (ingest + extraction), %.1f s" % (sample_blocks, dt),
+        "matches_gpu_output": match,
+    }
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2402_14607_gb300 import workloads
+    nb = args.nblocks
+    spec = workload_spec(0, nb)
+    sample = args.ref_sample_blocks
+    ns = -(-sample * spec.n // spec.b)
+    sx = workloads.adc_samples(spec.seed_x, ns, spec.b, offset_amp=spec.offset_amp)   # prefix of the stream
+    sy = workloads.adc_samples(spec.seed_y, ns, spec.b, offset_amp=spec.offset_amp)
+    threads = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        run_oracle_sample(spec, sx, sy, 1, threads)
+    times = []
+    m = None
+    for _ in range(args.steps):
+        _, dt, m = run_oracle_sample(spec, sx, sy, sample, threads)
+        times.append(dt)
+    total = sum(times)
+    value = args.steps * sample * m / total / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic (seeded quantised-Gaussian ADC samples)",
+        "config": {"workload": "large single stream (n=1024, 12-bit ADC), each step a bounded sample of "
+                               "%d block pairs" % sample, "n": spec.n, "nblocks_per_step": sample, "b": spec.b},
+        "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": "%d block pairs per step (ingest + extraction)" % sample},
+        "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU leg
+# ---------------------------------------------------------------------------
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2402_14607_gb300 import build as qbuild
+    from paper_2402_14607_gb300 import qext
+    from paper_2402_14607_gb300.clocks import ClockSampler
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    qbuild.build()
+    qext.lib()
+
+    spec = workload_spec(rank, args.nblocks)
+    plan = qext.qext_plan_create(spec.n, 0, spec.k, spec.eps)
+    info = plan.info
+    m = info["m"]
+    sx = spec.samples("x")
+    sy = spec.samples("y")
+    ns = sx.size
+    nwords_packed = -(-ns * spec.b // 32)
+    out_words = -(-spec.nblocks * m // 32)
+
+    stream = torch.cuda.Stream(device=dev)
+    sh = int(stream.cuda_stream)
+    # device-resident inputs
+    d_sx = torch.from_numpy(sx.view(np.int16)).to(dev)
+    d_sy = torch.from_numpy(sy.view(np.int16)).to(dev)
+    d_px = torch.empty(nwords_packed, dtype=torch.int32, device=dev)
+    d_py = torch.empty(nwords_packed, dtype=torch.int32, device=dev)
+    d_out = torch.empty(out_words, dtype=torch.int32, device=dev)
+    torch.cuda.synchronize()
+
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def step(timing=None):
+        if timing is not None:
+            timing[0].record(stream)
+        qext.qext_pack_samples(spec.b, d_sx, ns, d_px, sh)
+        qext.qext_pack_samples(spec.b, d_sy, ns, d_py, sh)
+        if timing is not None:
+            timing[1].record(stream)
+        qext.qext_extract(plan, d_px, d_py, spec.nblocks, d_out, sh)
+        if timing is not None:
+            timing[2].record(stream)
+
+    launches_per_step = 3
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    kev = [(ev(), ev(), ev()) for _ in range(args.steps)]
+    e_start, e_stop = ev(), ev()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e_start.record(stream)
+    for i in range(args.steps):
+        step(kev[i])
+    e_stop.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    t_local = e_start.elapsed_time(e_stop) * 1e-3
+    t = max_over_ranks(t_local, world)
+    pack_ms = [a.elapsed_time(b) for a, b, _ in kev]
+    ext_ms = [b.elapsed_time(c) for _, b, c in kev]
+    bits_per_step = spec.nblocks * m
+    value = world * args.steps * bits_per_step / t / 1e9
+    input_gbps = world * args.steps * 2 * spec.nbits / t / 1e9
+
+    # dominant kernel and its roofline (algorithmic bytes / average launch time)
+    peak, peak_src = measured_peaks()
+    ext_bytes = spec.nblocks * (2 * spec.n // 8) + out_words * 4
+    pack_bytes = ns * 2 + nwords_packed * 4
+    ext_s = statistics.mean(ext_ms) * 1e-3
+    pack_s = statistics.mean(pack_ms) * 1e-3 / 2
+    if ext_s >= 2 * pack_s:
+        dom = {"kernel": "extract_kernel<16>", "bytes": ext_bytes, "t": ext_s}
+    else:
+        dom = {"kernel": "pack_kernel (b=12)", "bytes": pack_bytes, "t": pack_s}
+    achieved = dom["bytes"] / dom["t"] / 1e9
+    roofline = {"bound": "hbm", "kernel": dom["kernel"], "achieved": round(achieved, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": args.traffic,
+                "peak_source": peak_src + " hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured" else peak_src,
+                "per_kernel_ms": {"pack_x_plus_y": round(statistics.mean(pack_ms), 4),
+                                  "extract": round(statistics.mean(ext_ms), 4)},
+                "extract_frac": round(ext_bytes / ext_s / 1e9 / peak, 4),
+                "pack_frac": round(pack_bytes / pack_s / 1e9 / peak, 4)}
+
+    # end to end through the C ABI: pinned host samples in, output back out
+    h_sx = torch.from_numpy(sx.view(np.int16)).pin_memory()
+    h_sy = torch.from_numpy(sy.view(np.int16)).pin_memory()
+    h_out = torch.empty(out_words, dtype=torch.int32).pin_memory()
+
+    def e2e_step():
+        with torch.cuda.stream(stream):
+            d_sx.copy_(h_sx, non_blocking=True)
+            d_sy.copy_(h_sy, non_blocking=True)
+        step()
+        with torch.cuda.stream(stream):
+            h_out.copy_(d_out, non_blocking=True)
+
+    for _ in range(max(1, min(args.warmup, 3))):
+        e2e_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e0, e1 = ev(), ev()
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    te = max_over_ranks(e0.elapsed_time(e1) * 1e-3, world)
+    e2e = {"value": round(world * args.steps * bits_per_step / te / 1e9, 3), "unit": UNIT,
+           "h2d_bytes_per_step": 2 * ns * 2, "d2h_bytes_per_step": out_words * 4,
+           "path": "pinned host samples -> cudaMemcpyAsync -> qext_pack_samples x2 -> qext_extract -> host"}
+    gpu_out = d_out.cpu().numpy().view(np.uint32)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(spec, sx, sy, gpu_out, args.cpu_sample_blocks)
+
+    if world > 1:
+        dist.barrier()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(t / args.steps * 1e3, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic (seeded quantised-Gaussian 12-bit ADC samples, numpy PCG64)",
+            "config": workload_config(spec, info, world),
+            "input_gbps": round(input_gbps, 2),
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "clocks": {k: clk.get(k) for k in ("sm_mhz", "sm_max_mhz", "reasons", "samples", "source")},
+            "gpu_launches": launches_per_step * args.steps,
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["qext", "reference"], default="qext")
+    ap.add_argument("--nblocks", type=int, default=1 << 20, help="block pairs per step per GPU")
+    ap.add_argument("--cpu-sample-blocks", type=int, default=4096)
+    ap.add_argument("--ref-sample-blocks", type=int, default=1024)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="ncu dram bytes per launch of the dominant kernel, if captured for this build")
+    args = ap.parse_args(argv)
+    args.warmup = max(args.warmup, 3)   # at least 3 untimed warm-up steps
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

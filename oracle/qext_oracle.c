@@ -239,7 +239,7 @@ static int sbit(const uint32_t *s, uint64_t t) { return (int)((s[t >> 5] >> (t &
  * (consecutive, non-overlapping windows: the cursor advances by one block),
  * Z^(l) = Ext_IP^{n_p,q}(X_{I_l}, Y_{I_l}), and Z^(l) is output in order,
  * truncated to its first m bits.  out must hold ceil(nblocks*m/32) words and
- * is fully overwritten.  threads <= 0 means "all available" (OpenMP builds).
+ * is fully overwritten.  threads <= 0 means all processors (OpenMP builds).
  * Returns 0, or -1 on bad arguments.
  */
 int orc_extract(int q, int n_p, int m, const uint64_t *poly, const uint32_t *x, const uint32_t *y,
@@ -252,8 +252,8 @@ int orc_extract(int q, int n_p, int m, const uint64_t *poly, const uint32_t *x, 
     int ew = (q + 63) / 64;
     (void)threads;
 #ifdef _OPENMP
-    if (threads > 0) omp_set_num_threads(threads);
-#pragma omp parallel
+    int nthreads = threads > 0 ? threads : omp_get_num_procs();
+#pragma omp parallel num_threads(nthreads)
 #endif
     {
         uint64_t *xs = (uint64_t *)calloc((size_t)n_p * ew, sizeof(uint64_t));

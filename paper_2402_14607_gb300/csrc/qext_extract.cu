@@ -21,6 +21,14 @@
 
 namespace {
 
+// 2^G and 2^(32-G) for G = 1, 2, 4 (index log2 G).  Passed at run time so the
+// shifts of the transpose stages issue as IMAD / IMAD.HI on the FMA pipe
+// instead of SHF on the ALU pipe, which the AND/XOR work already saturates.
+struct ShiftMuls {
+    uint32_t lo[3];  // 2^G
+    uint32_t hi[3];  // 2^(32-G): umulhi(a, 2^(32-G)) = a >> G
+};
+
 struct ExtractArgs {
     const uint32_t *x;
     const uint32_t *y;
@@ -32,6 +40,7 @@ struct ExtractArgs {
     uint32_t taps[4];  // descending, last is 0 (the constant term)
     int vec16;         // x, y 16-byte aligned and wpb % 4 == 0
     int vec8;          // x, y 8-byte aligned and wpb % 2 == 0
+    ShiftMuls mu;
 };
 
 // ---------------------------------------------------------------------------
@@ -46,7 +55,12 @@ __device__ __forceinline__ constexpr uint32_t low_mask() {
 // in every 2G-bit lane, a keeps its low G bits and receives b's low G bits
 // on top; b receives a's high G bits below its own high G bits.
 template <int G>
-__device__ __forceinline__ void exchange(uint32_t &a, uint32_t &b) {
+__device__ __forceinline__ constexpr int log2_of() {
+    return G == 1 ? 0 : G == 2 ? 1 : 2;
+}
+
+template <int G>
+__device__ __forceinline__ void exchange(uint32_t &a, uint32_t &b, const ShiftMuls &mu) {
     if constexpr (G == 16) {
         const uint32_t na = __byte_perm(a, b, 0x5410), nb = __byte_perm(a, b, 0x7632);
         a = na;
@@ -57,8 +71,10 @@ __device__ __forceinline__ void exchange(uint32_t &a, uint32_t &b) {
         b = nb;
     } else {
         constexpr uint32_t M = low_mask<G>();
-        const uint32_t na = (a & M) | ((b << G) & ~M);
-        const uint32_t nb = ((a >> G) & M) | (b & ~M);
+        const uint32_t up = b * mu.lo[log2_of<G>()];             // b << G   (IMAD)
+        const uint32_t dn = __umulhi(a, mu.hi[log2_of<G>()]);    // a >> G   (IMAD.HI)
+        const uint32_t na = (a & M) | (up & ~M);
+        const uint32_t nb = (dn & M) | (b & ~M);
         a = na;
         b = nb;
     }
@@ -67,18 +83,18 @@ __device__ __forceinline__ void exchange(uint32_t &a, uint32_t &b) {
 // Transpose stages G = Q/2 .. 1 over Q words: afterwards w[j] holds bit j of
 // every element (Q-bit elements packed 32/Q per word).
 template <int Q, int G>
-__device__ __forceinline__ void slice_stages(uint32_t (&w)[Q]) {
+__device__ __forceinline__ void slice_stages(uint32_t (&w)[Q], const ShiftMuls &mu) {
     if constexpr (G >= 1) {
 #pragma unroll
         for (int i = 0; i < Q; ++i)
-            if ((i & G) == 0) exchange<G>(w[i], w[i + G]);
-        slice_stages<Q, G / 2>(w);
+            if ((i & G) == 0) exchange<G>(w[i], w[i + G], mu);
+        slice_stages<Q, G / 2>(w, mu);
     }
 }
 
 template <int Q>
-__device__ __forceinline__ void slice(uint32_t (&w)[Q]) {
-    slice_stages<Q, Q / 2>(w);
+__device__ __forceinline__ void slice(uint32_t (&w)[Q], const ShiftMuls &mu) {
+    slice_stages<Q, Q / 2>(w, mu);
 }
 
 // acc[j + l] ^= X[j] & Y[l] for all j, l < Q (schoolbook Gram diagonals).
@@ -94,24 +110,24 @@ __device__ __forceinline__ void gram_diagonals(const uint32_t (&X)[Q], const uin
 // exchange followed by XOR of the pair), bit p of the result is the parity
 // of a[p].
 template <int G>
-__device__ __forceinline__ void parity_fold(uint32_t (&a)[32]) {
+__device__ __forceinline__ void parity_fold(uint32_t (&a)[32], const ShiftMuls &mu) {
     if constexpr (G >= 1) {
 #pragma unroll
         for (int i = 0; i < G; ++i) {
             uint32_t u = a[i], v = a[i + G];
-            exchange<G>(u, v);
+            exchange<G>(u, v, mu);
             a[i] = u ^ v;
         }
-        parity_fold<G / 2>(a);
+        parity_fold<G / 2>(a, mu);
     }
 }
 
 template <int K>
-__device__ __forceinline__ uint32_t parity_bits32(const uint32_t *acc) {
+__device__ __forceinline__ uint32_t parity_bits32(const uint32_t *acc, const ShiftMuls &mu) {
     uint32_t a[32];
 #pragma unroll
     for (int i = 0; i < 32; ++i) a[i] = i < K ? acc[i] : 0u;
-    parity_fold<16>(a);
+    parity_fold<16>(a, mu);
     return a[0];
 }
 
@@ -198,15 +214,15 @@ __device__ __forceinline__ uint64_t block_value(const uint32_t *xb, const uint32
         uint32_t X[Q], Y[Q];
         load_group<Q>(xb, g0, a.wpb, a.vec16, X);
         load_group<Q>(yb, g0, a.wpb, a.vec16, Y);
-        slice<Q>(X);
-        slice<Q>(Y);
+        slice<Q>(X, a.mu);
+        slice<Q>(Y, a.mu);
         gram_diagonals<Q>(X, Y, acc);
     }
     uint64_t z;
     if constexpr (2 * Q - 1 <= 32) {
-        z = parity_bits32<2 * Q - 1>(acc);
+        z = parity_bits32<2 * Q - 1>(acc, a.mu);
     } else {
-        z = uint64_t(parity_bits32<32>(acc)) | (uint64_t(parity_bits32<2 * Q - 1 - 32>(acc + 32)) << 32);
+        z = uint64_t(parity_bits32<32>(acc, a.mu)) | (uint64_t(parity_bits32<2 * Q - 1 - 32>(acc + 32, a.mu)) << 32);
     }
     return reduce_small<Q>(z, a);
 }
@@ -247,11 +263,11 @@ __device__ __forceinline__ uint64_t half_product64(const uint32_t *xb, const uin
         uint32_t X[32], Y[32];
         load_half64<PART>(xb, g0, a.wpb, a.vec8, X);
         load_half64<PART>(yb, g0, a.wpb, a.vec8, Y);
-        slice<32>(X);
-        slice<32>(Y);
+        slice<32>(X, a.mu);
+        slice<32>(Y, a.mu);
         gram_diagonals<32>(X, Y, acc);
     }
-    return uint64_t(parity_bits32<32>(acc)) | (uint64_t(parity_bits32<31>(acc + 32)) << 32);
+    return uint64_t(parity_bits32<32>(acc, a.mu)) | (uint64_t(parity_bits32<31>(acc + 32, a.mu)) << 32);
 }
 
 template <>
@@ -345,6 +361,10 @@ int launch_extract(const qext_plan *p, const uint32_t *x, const uint32_t *y, uin
     const uintptr_t al = reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y);
     a.vec16 = (al % 16 == 0) && (a.wpb % 4 == 0);
     a.vec8 = (al % 8 == 0) && (a.wpb % 2 == 0);
+    for (int i = 0; i < 3; ++i) {
+        a.mu.lo[i] = 1u << (1 << i);
+        a.mu.hi[i] = 1u << (32 - (1 << i));
+    }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     switch (p->q) {
         case 1: return launch_q<1>(a, s);

@@ -39,6 +39,68 @@ __global__ void __launch_bounds__(256) pack_kernel(const uint16_t *__restrict__ 
     }
 }
 
+// b = 12: one thread per period of 8 samples (one 16-byte load) -> 3 words.
+// b = 8: 16 samples (two 16-byte loads) -> 4 words (one 16-byte store).
+// b = 16: 8 samples -> 4 words (a masked copy).
+// Requires a 16-byte aligned sample pointer; a period that runs past
+// nsamples is read sample by sample (missing samples are 0).
+template <int B>
+__global__ void __launch_bounds__(256) pack_kernel_vec(const uint16_t *__restrict__ s, uint64_t nsamples,
+                                                       uint32_t *__restrict__ out, uint64_t nwords,
+                                                       uint64_t nperiods) {
+    constexpr uint32_t S = B == 8 ? 16 : 8;                 // samples per thread
+    constexpr uint32_t L = B == 12 ? 3 : 4;                  // words per thread
+    constexpr uint32_t MASK2 = B == 16 ? 0xFFFFFFFFu : B == 12 ? 0x0FFF0FFFu : 0x00FF00FFu;
+    for (uint64_t c = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; c < nperiods;
+         c += uint64_t(gridDim.x) * blockDim.x) {
+        const uint64_t s0 = c * S;
+        uint32_t p[S / 2];  // sample pairs, low sample in the low half
+        if (s0 + S <= nsamples) {
+#pragma unroll
+            for (uint32_t v = 0; v < S / 8; ++v) {
+                const uint4 q = __ldg(reinterpret_cast<const uint4 *>(s + s0) + v);
+                p[4 * v] = q.x;
+                p[4 * v + 1] = q.y;
+                p[4 * v + 2] = q.z;
+                p[4 * v + 3] = q.w;
+            }
+        } else {
+#pragma unroll
+            for (uint32_t j = 0; j < S / 2; ++j) {
+                const uint32_t lo = s0 + 2 * j < nsamples ? __ldg(s + s0 + 2 * j) : 0u;
+                const uint32_t hi = s0 + 2 * j + 1 < nsamples ? __ldg(s + s0 + 2 * j + 1) : 0u;
+                p[j] = lo | (hi << 16);
+            }
+        }
+#pragma unroll
+        for (uint32_t j = 0; j < S / 2; ++j) p[j] &= MASK2;
+        uint32_t w[L];
+        if constexpr (B == 12) {
+            const uint32_t a0 = p[0] & 0xFFFu, a1 = p[0] >> 16, a2 = p[1] & 0xFFFu, a3 = p[1] >> 16;
+            const uint32_t a4 = p[2] & 0xFFFu, a5 = p[2] >> 16, a6 = p[3] & 0xFFFu, a7 = p[3] >> 16;
+            w[0] = a0 | (a1 << 12) | (a2 << 24);
+            w[1] = (a2 >> 8) | (a3 << 4) | (a4 << 16) | (a5 << 28);
+            w[2] = (a5 >> 4) | (a6 << 8) | (a7 << 20);
+        } else if constexpr (B == 8) {
+#pragma unroll
+            for (uint32_t j = 0; j < 4; ++j) w[j] = __byte_perm(p[2 * j], p[2 * j + 1], 0x6420);
+        } else {
+#pragma unroll
+            for (uint32_t j = 0; j < 4; ++j) w[j] = p[j];
+        }
+        const uint64_t w0 = c * L;
+        if constexpr (L == 4) {
+            if (w0 + 4 <= nwords) {
+                *reinterpret_cast<uint4 *>(out + w0) = make_uint4(w[0], w[1], w[2], w[3]);
+                continue;
+            }
+        }
+#pragma unroll
+        for (uint32_t j = 0; j < L; ++j)
+            if (w0 + j < nwords) out[w0 + j] = w[j];
+    }
+}
+
 uint32_t gcd32(uint32_t a, uint32_t b) {
     while (b) {
         const uint32_t t = a % b;
@@ -64,10 +126,25 @@ int launch_pack(uint32_t b, const uint16_t *samples, uint64_t nsamples, uint32_t
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return QEXT_E_CUDA;
         grid_cap = sms * 8;
     }
-    const uint64_t ctas = (nperiods + 255) / 256;
-    const int grid = int(ctas < uint64_t(grid_cap) ? ctas : uint64_t(grid_cap));
-    pack_kernel<<<grid, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(samples, nsamples, b, S, L, out, nwords,
-                                                                          nperiods);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const bool a16 = reinterpret_cast<uintptr_t>(samples) % 16 == 0;
+    const bool o16 = reinterpret_cast<uintptr_t>(out) % 16 == 0;
+    auto grid_for = [&](uint64_t periods) {
+        const uint64_t ctas = (periods + 255) / 256;
+        return int(ctas < uint64_t(grid_cap) ? ctas : uint64_t(grid_cap));
+    };
+    if (a16 && b == 12) {
+        const uint64_t np = (nsamples + 7) / 8;
+        pack_kernel_vec<12><<<grid_for(np), 256, 0, st>>>(samples, nsamples, out, nwords, np);
+    } else if (a16 && o16 && b == 8) {
+        const uint64_t np = (nsamples + 15) / 16;
+        pack_kernel_vec<8><<<grid_for(np), 256, 0, st>>>(samples, nsamples, out, nwords, np);
+    } else if (a16 && o16 && b == 16) {
+        const uint64_t np = (nsamples + 7) / 8;
+        pack_kernel_vec<16><<<grid_for(np), 256, 0, st>>>(samples, nsamples, out, nwords, np);
+    } else {
+        pack_kernel<<<grid_for(nperiods), 256, 0, st>>>(samples, nsamples, b, S, L, out, nwords, nperiods);
+    }
     return cudaGetLastError() == cudaSuccess ? QEXT_OK : QEXT_E_CUDA;
 }
 

@@ -32,7 +32,8 @@ def adc_samples(seed: int, nsamples: int, b: int, sigma: float = 1.0, offset_amp
     rng = np.random.Generator(np.random.PCG64(seed))
     g = rng.standard_normal(nsamples)
     if offset_amp:
-        g = g + rng.uniform(-offset_amp, offset_amp, nsamples)
+        # offsets from their own stream so any prefix of a stream is reproducible alone
+        g = g + np.random.Generator(np.random.PCG64([seed, 1])).uniform(-offset_amp, offset_amp, nsamples)
     if drift_amp:
         period = float(drift_period or nsamples)
         t = np.arange(start, start + nsamples, dtype=np.float64)

@@ -69,11 +69,17 @@ def test_degenerate_inputs(q):
     assert (gpu_extract(plan, ones, ones, nb) == oracle_extract(plan, ones, ones, nb)).all()
 
 
-@pytest.mark.parametrize("b,ns", [(8, 4096), (12, 1001), (12, 8), (16, 33), (1, 999), (5, 77), (3, 1), (11, 640)])
-def test_pack_matches_oracle(b, ns):
+@pytest.mark.parametrize("b,ns,off", [(8, 4096, 0), (8, 4099, 0), (12, 1001, 0), (12, 8, 0), (12, 100003, 0),
+                                      (16, 33, 0), (1, 999, 0), (5, 77, 0), (3, 1, 0), (11, 640, 0),
+                                      (12, 1001, 1), (8, 333, 3), (16, 65, 1)])
+def test_pack_matches_oracle(b, ns, off):
+    """Vectorised paths (b = 8, 12, 16 on 16-byte aligned samples), their
+    ragged tails, and the generic path (other b, or unaligned samples)."""
     s = workloads.adc_samples(b * 7 + ns, ns, b)
     s = s | np.uint16(0xFFFF ^ ((1 << b) - 1)) if b < 16 else s   # garbage above b must be ignored
-    ts = torch.from_numpy(s.view(np.int16)).cuda()
+    buf = torch.zeros(ns + off, dtype=torch.int16, device="cuda")
+    buf[off:] = torch.from_numpy(s.view(np.int16)).cuda()
+    ts = buf[off:]
     nw = -(-ns * b // 32)
     out = torch.full((nw + 4,), -1, dtype=torch.int32, device="cuda")
     qext.qext_pack_samples(b, ts, ns, out)
