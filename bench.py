@@ -79,7 +79,7 @@ def workload_config(spec, info, world):
                     (spec.nblocks, spec.n, spec.nbits / 2 ** 30, spec.b),
         "n": spec.n, "nblocks": spec.nblocks, "b": spec.b, "k": spec.k, "eps_block": spec.eps,
         "q": info["q"], "n_p": info["n_p"], "m": info["m"], "log2_eps_block": round(info["log2_eps_block"], 2),
-        "step": "qext_pack_samples(x), qext_pack_samples(y), qext_extract",
+        "step": None,
         "l2": "inputs larger than L2 (%.0f MB of samples per step)" % (2 * spec.nsamples * 2 / 1e6),
         "parallelism": "blocks sharded per rank, no collective" if world > 1 else "single GPU",
     }
@@ -196,15 +196,20 @@ def run_gpu(args):
     def step(timing=None):
         if timing is not None:
             timing[0].record(stream)
-        qext.qext_pack_samples(spec.b, d_sx, ns, d_px, sh)
-        qext.qext_pack_samples(spec.b, d_sy, ns, d_py, sh)
-        if timing is not None:
-            timing[1].record(stream)
-        qext.qext_extract(plan, d_px, d_py, spec.nblocks, d_out, sh)
+        if args.unfused:
+            qext.qext_pack_samples(spec.b, d_sx, ns, d_px, sh)
+            qext.qext_pack_samples(spec.b, d_sy, ns, d_py, sh)
+            if timing is not None:
+                timing[1].record(stream)
+            qext.qext_extract(plan, d_px, d_py, spec.nblocks, d_out, sh)
+        else:
+            if timing is not None:
+                timing[1].record(stream)
+            qext.qext_extract_samples(plan, spec.b, d_sx, d_sy, ns, spec.nblocks, d_out, sh)
         if timing is not None:
             timing[2].record(stream)
 
-    launches_per_step = 3
+    launches_per_step = 3 if args.unfused else 1
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -234,22 +239,28 @@ def run_gpu(args):
 
     # dominant kernel and its roofline (algorithmic bytes / average launch time)
     peak, peak_src = measured_peaks()
-    ext_bytes = spec.nblocks * (2 * spec.n // 8) + out_words * 4
-    pack_bytes = ns * 2 + nwords_packed * 4
     ext_s = statistics.mean(ext_ms) * 1e-3
-    pack_s = statistics.mean(pack_ms) * 1e-3 / 2
-    if ext_s >= 2 * pack_s:
-        dom = {"kernel": "extract_kernel<16>", "bytes": ext_bytes, "t": ext_s}
+    if args.unfused:
+        ext_bytes = spec.nblocks * (2 * spec.n // 8) + out_words * 4
+        pack_bytes = ns * 2 + nwords_packed * 4
+        pack_s = statistics.mean(pack_ms) * 1e-3 / 2
+        if ext_s >= 2 * pack_s:
+            dom = {"kernel": "extract_tiled_kernel<16,0>", "bytes": ext_bytes, "t": ext_s}
+        else:
+            dom = {"kernel": "pack_kernel_vec<12>", "bytes": pack_bytes, "t": pack_s}
+        per_kernel = {"pack_x_plus_y": round(statistics.mean(pack_ms), 4), "extract": round(statistics.mean(ext_ms), 4)}
     else:
-        dom = {"kernel": "pack_kernel (b=12)", "bytes": pack_bytes, "t": pack_s}
+        # the fused kernel reads both sample arrays once and writes the output
+        dom = {"kernel": "extract_tiled_kernel<16,12> (fused ingest)", "bytes": 2 * ns * 2 + out_words * 4,
+               "t": ext_s}
+        per_kernel = {"extract_samples": round(statistics.mean(ext_ms), 4)}
     achieved = dom["bytes"] / dom["t"] / 1e9
     roofline = {"bound": "hbm", "kernel": dom["kernel"], "achieved": round(achieved, 1), "peak": peak,
                 "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": args.traffic,
-                "peak_source": peak_src + " hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured" else peak_src,
-                "per_kernel_ms": {"pack_x_plus_y": round(statistics.mean(pack_ms), 4),
-                                  "extract": round(statistics.mean(ext_ms), 4)},
-                "extract_frac": round(ext_bytes / ext_s / 1e9 / peak, 4),
-                "pack_frac": round(pack_bytes / pack_s / 1e9 / peak, 4)}
+                "algorithmic_bytes_per_launch": dom["bytes"],
+                "peak_source": ("measured hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured"
+                                else "fallback 6.8 TB/s"),
+                "per_kernel_ms": per_kernel}
 
     # end to end through the C ABI: pinned host samples in, output back out
     h_sx = torch.from_numpy(sx.view(np.int16)).pin_memory()
@@ -278,7 +289,7 @@ def run_gpu(args):
     te = max_over_ranks(e0.elapsed_time(e1) * 1e-3, world)
     e2e = {"value": round(world * args.steps * bits_per_step / te / 1e9, 3), "unit": UNIT,
            "h2d_bytes_per_step": 2 * ns * 2, "d2h_bytes_per_step": out_words * 4,
-           "path": "pinned host samples -> cudaMemcpyAsync -> qext_pack_samples x2 -> qext_extract -> host"}
+           "path": "pinned host samples -> cudaMemcpyAsync x2 -> step -> cudaMemcpyAsync -> pinned host output"}
     gpu_out = d_out.cpu().numpy().view(np.uint32)
 
     cpu = None
@@ -293,7 +304,9 @@ def run_gpu(args):
             "warmup": args.warmup, "ms_per_step": round(t / args.steps * 1e3, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic (seeded quantised-Gaussian 12-bit ADC samples, numpy PCG64)",
-            "config": workload_config(spec, info, world),
+            "config": dict(workload_config(spec, info, world), step=(
+                "qext_pack_samples(x), qext_pack_samples(y), qext_extract" if args.unfused
+                else "qext_extract_samples (fused ingest + extraction, one kernel)")),
             "input_gbps": round(input_gbps, 2),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "clocks": {k: clk.get(k) for k in ("sm_mhz", "sm_max_mhz", "reasons", "samples", "source")},
@@ -313,9 +326,11 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["qext", "reference"], default="qext")
     ap.add_argument("--nblocks", type=int, default=1 << 20, help="block pairs per step per GPU")
-    ap.add_argument("--cpu-sample-blocks", type=int, default=4096)
-    ap.add_argument("--ref-sample-blocks", type=int, default=1024)
+    ap.add_argument("--cpu-sample-blocks", type=int, default=1 << 20)
+    ap.add_argument("--ref-sample-blocks", type=int, default=1 << 17)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--unfused", action="store_true",
+                    help="step = qext_pack_samples x2 + qext_extract instead of the fused qext_extract_samples")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per launch of the dominant kernel, if captured for this build")
     args = ap.parse_args(argv)

@@ -135,6 +135,39 @@ int qext_alg1_params(double N_samples, uint32_t b, double delta, double eps, uin
 int qext_extract(const qext_plan *p, const uint32_t *x, const uint32_t *y, uint64_t nblocks, uint32_t *out,
                  qext_cuda_stream stream);
 
+/* Flags of qext_extract_ex (launch shape only; the output never changes). */
+#define QEXT_F_DIRECT 0x1u /* skip shared-memory staging: each thread reads its block from global memory */
+#define QEXT_F_NBUF1 0x2u  /* one tile buffer per CTA (more CTAs per SM) instead of two (prefetch) */
+#define QEXT_F_TILE32 0x4u /* at most 32 blocks per tile */
+#define QEXT_F_TILE64 0x8u /* at most 64 blocks per tile (exclusive with TILE32) */
+#define QEXT_F_ALL 0xFu
+
+/*
+ * qext_extract_ex -- qext_extract with launch options (flags, 0 = the
+ * default path chosen by qext_extract).  Same arguments, ownership and errors;
+ * INVAL also for unknown flag bits.  The output is identical for every flag
+ * combination.
+ */
+int qext_extract_ex(const qext_plan *p, const uint32_t *x, const uint32_t *y, uint64_t nblocks, uint32_t *out,
+                    qext_cuda_stream stream, uint32_t flags);
+
+/*
+ * qext_extract_samples -- fused ingest + extraction: the same output as
+ * qext_pack_samples on each source followed by qext_extract, without the
+ * packed streams ever reaching device memory.  Raw b-bit ADC samples (the low
+ * b bits of each uint16; higher bits ignored) form the bit streams (Sec. 3,
+ * sample s at stream bits [s*b, (s+1)*b)), which are cut into n-bit blocks.
+ *   b          8, 12 or 16 (else UNSUPPORTED);
+ *   x_samples, y_samples  DEVICE pointers to nsamples uint16 each, 16-byte
+ *              aligned;
+ *   nblocks    whole blocks to extract, nblocks * n <= nsamples * b;
+ *   out        DEVICE pointer to ceil(nblocks*m/32) words, fully written.
+ * Kernels exist for q in {4, 16, 64}; other q return UNSUPPORTED.
+ * Asynchronous on stream.  Errors: INVAL, UNSUPPORTED, CUDA.
+ */
+int qext_extract_samples(const qext_plan *p, uint32_t b, const uint16_t *x_samples, const uint16_t *y_samples,
+                         uint64_t nsamples, uint64_t nblocks, uint32_t *out, qext_cuda_stream stream);
+
 /*
  * qext_pack_samples -- ingest: raw ADC samples to a packed stream.  Sample s
  * (b bits, the low bits of samples[s]) occupies stream bits [s*b, (s+1)*b)

@@ -16,8 +16,10 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libqext.so")
-SOURCES = ["qext_plan.cpp", "qext_api.cpp", "qext_extract.cu", "qext_ingest.cu"]
-HEADERS = [os.path.join(CSRC, "qext_internal.h"), os.path.join(ROOT, "include", "qext.h")]
+SOURCES = ["qext_plan.cpp", "qext_api.cpp", "qext_extract.cu", "qext_fused.cu", "qext_ingest.cu"]
+HEADERS = [os.path.join(CSRC, "qext_internal.h"), os.path.join(CSRC, "qext_device.cuh"),
+           os.path.join(CSRC, "qext_block.cuh"),
+           os.path.join(ROOT, "include", "qext.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
                      "-I" + os.path.join(ROOT, "include")]

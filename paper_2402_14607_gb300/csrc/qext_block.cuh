@@ -1,0 +1,337 @@
+// Per-block compute of Ext_IP (Definition 3.2) from a block's words, shared
+// by the extraction kernels, plus the raw-sample packing of the fused ingest.
+// See qext_device.cuh for the sliced GF(2) formulation.
+#pragma once
+
+#include "qext_device.cuh"
+
+namespace qxd {
+
+__device__ __forceinline__ uint4 lds4(const uint32_t *p) { return *reinterpret_cast<const uint4 *>(p); }
+
+// ---------------------------------------------------------------------------
+// Accumulator of one block's sliced Gram diagonals, q <= 32.
+// ---------------------------------------------------------------------------
+template <int Q>
+struct Acc {
+    static constexpr bool kKaratsuba = Q == 16;
+    static constexpr int NA = kKaratsuba ? 45 : 2 * Q - 1;
+    uint32_t a[NA];
+    __device__ __forceinline__ Acc() {
+#pragma unroll
+        for (int i = 0; i < NA; ++i) a[i] = 0;
+    }
+    // Sliced group of 32 elements: X[j], Y[j] = bit j of the 32 elements.
+    __device__ __forceinline__ void add(uint32_t (&X)[Q], uint32_t (&Y)[Q]) {
+        if constexpr (kKaratsuba) {
+            // one Karatsuba level over the element bits: low half L (bits
+            // 0..7), high half H (8..15), sum S = L + H
+            uint32_t *A = a, *B = a + 15, *C = a + 30;
+            uint32_t XS[8], YS[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                XS[j] = X[j] ^ X[j + 8];
+                YS[j] = Y[j] ^ Y[j + 8];
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+#pragma unroll
+                for (int l = 0; l < 8; ++l) {
+                    A[j + l] = lop_and_xor(X[j], Y[l], A[j + l]);
+                    B[j + l] = lop_and_xor(X[j + 8], Y[l + 8], B[j + l]);
+                    C[j + l] = lop_and_xor(XS[j], YS[l], C[j + l]);
+                }
+        } else {
+            gram_diagonals<Q, Q>(X, Y, a);
+        }
+    }
+    // z (2q-1 bits) = parities of the Gram diagonals
+    __device__ __forceinline__ uint64_t unreduced(const ShiftMuls &mu) {
+        if constexpr (kKaratsuba) {
+            // z = A + x^16 B + x^8 (C - A - B), combined word-wise, then parity
+            const uint32_t *A = a, *B = a + 15, *C = a + 30;
+            uint32_t W[31];
+#pragma unroll
+            for (int k = 0; k < 31; ++k) W[k] = 0;
+#pragma unroll
+            for (int k = 0; k < 15; ++k) {
+                const uint32_t mid = lop_xor3(C[k], A[k], B[k]);
+                W[k] ^= A[k];
+                W[k + 16] ^= B[k];
+                W[k + 8] ^= mid;
+            }
+            return parity_bits32<31>(W, mu);
+        } else {
+            return parity_bits64<2 * Q - 1>(a, mu);
+        }
+    }
+};
+
+// One block, q <= 32, from a block's words xs / ys (shared or global memory).
+// With vec, the block's 16-byte chunks are read starting at chunk rot.
+template <int Q>
+__device__ __forceinline__ uint64_t block_small_q(const uint32_t *xs, const uint32_t *ys, uint32_t wpb, int vec,
+                                                  uint32_t rot, const ShiftMuls &mu, const StreamArgs &s) {
+    Acc<Q> acc;
+    if constexpr (Q >= 4) {
+        if (vec && wpb == 2 * Q) {
+            // n_p = 64: two groups of 32 elements, 2Q/4 chunks, fully unrolled
+            constexpr uint32_t NCH = Q / 2;
+            const uint32_t r0 = rot & (NCH - 1);
+#pragma unroll
+            for (int g = 0; g < 2; ++g) {
+                uint32_t X[Q], Y[Q];
+#pragma unroll
+                for (int c = 0; c < Q / 4; ++c) {
+                    const uint32_t ch = (uint32_t(g * (Q / 4) + c) + r0) & (NCH - 1);
+                    const uint4 vx = lds4(xs + 4 * ch), vy = lds4(ys + 4 * ch);
+                    X[4 * c] = vx.x;
+                    X[4 * c + 1] = vx.y;
+                    X[4 * c + 2] = vx.z;
+                    X[4 * c + 3] = vx.w;
+                    Y[4 * c] = vy.x;
+                    Y[4 * c + 1] = vy.y;
+                    Y[4 * c + 2] = vy.z;
+                    Y[4 * c + 3] = vy.w;
+                }
+                slice<Q>(X, mu);
+                slice<Q>(Y, mu);
+                acc.add(X, Y);
+            }
+            return reduce_mod_p<Q>(acc.unreduced(mu), s);
+        }
+    }
+    if (vec) {
+        const uint32_t nch = wpb >> 2;
+        const uint32_t r0 = rot % nch;
+        if constexpr (Q >= 4) {
+            constexpr int CPG = Q / 4;  // chunks per group
+            for (uint32_t g = 0; g < nch; g += CPG) {
+                uint32_t X[Q], Y[Q];
+#pragma unroll
+                for (int c = 0; c < CPG; ++c) {
+                    uint4 vx = make_uint4(0, 0, 0, 0), vy = vx;
+                    if (g + c < nch) {
+                        uint32_t ch = g + c + r0;
+                        ch = ch >= nch ? ch - nch : ch;
+                        vx = lds4(xs + 4 * ch);
+                        vy = lds4(ys + 4 * ch);
+                    }
+                    X[4 * c] = vx.x;
+                    X[4 * c + 1] = vx.y;
+                    X[4 * c + 2] = vx.z;
+                    X[4 * c + 3] = vx.w;
+                    Y[4 * c] = vy.x;
+                    Y[4 * c + 1] = vy.y;
+                    Y[4 * c + 2] = vy.z;
+                    Y[4 * c + 3] = vy.w;
+                }
+                slice<Q>(X, mu);
+                slice<Q>(Y, mu);
+                acc.add(X, Y);
+            }
+        } else {
+            for (uint32_t c = 0; c < nch; ++c) {
+                uint32_t ch = c + r0;
+                ch = ch >= nch ? ch - nch : ch;
+                const uint4 vx = lds4(xs + 4 * ch), vy = lds4(ys + 4 * ch);
+                const uint32_t wx[4] = {vx.x, vx.y, vx.z, vx.w}, wy[4] = {vy.x, vy.y, vy.z, vy.w};
+#pragma unroll
+                for (int g = 0; g < 4 / Q; ++g) {
+                    uint32_t X[Q], Y[Q];
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) {
+                        X[i] = wx[g * Q + i];
+                        Y[i] = wy[g * Q + i];
+                    }
+                    slice<Q>(X, mu);
+                    slice<Q>(Y, mu);
+                    acc.add(X, Y);
+                }
+            }
+        }
+    } else {
+        for (uint32_t g0 = 0; g0 < wpb; g0 += Q) {
+            uint32_t X[Q], Y[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                X[i] = g0 + i < wpb ? xs[g0 + i] : 0u;
+                Y[i] = g0 + i < wpb ? ys[g0 + i] : 0u;
+            }
+            slice<Q>(X, mu);
+            slice<Q>(Y, mu);
+            acc.add(X, Y);
+        }
+    }
+    return reduce_mod_p<Q>(acc.unreduced(mu), s);
+}
+
+// ---------------------------------------------------------------------------
+// q = 64 (elements are word pairs: low word = bits 0..31, high = 32..63).
+// One Karatsuba level over the halves: z = A + x^64 B + x^32 (C - A - B) with
+// A = sum lo*lo, B = sum hi*hi, C = sum (lo^hi)*(lo^hi), each a sliced 32x32
+// Gram product over groups of 32 elements.  Transposition is linear, so C's
+// operands are sliced from the XOR of the raw halves.  The thread handles the
+// groups g_first, g_first + g_step, ... of its block.
+// ---------------------------------------------------------------------------
+template <int PART>
+__device__ __forceinline__ uint32_t pick64(uint32_t lo, uint32_t hi) {
+    return PART == 0 ? lo : PART == 1 ? hi : (lo ^ hi);
+}
+
+template <int PART>
+__device__ __forceinline__ uint64_t half_product64(const uint32_t *xs, const uint32_t *ys, uint32_t wpb, int vec,
+                                                   uint32_t rot, uint32_t g_first, uint32_t g_step,
+                                                   const ShiftMuls &mu) {
+    uint32_t acc[63];
+#pragma unroll
+    for (int i = 0; i < 63; ++i) acc[i] = 0;
+    for (uint32_t g0 = 64 * g_first; g0 < wpb; g0 += 64 * g_step) {
+        uint32_t X[32], Y[32];
+        if (vec) {
+            // 16 chunks of 2 elements each, rotated within the group
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+                const uint32_t w = g0 + 4 * ((uint32_t(c) + rot) & 15u);
+                uint4 vx = make_uint4(0, 0, 0, 0), vy = vx;
+                if (w < wpb) {
+                    vx = lds4(xs + w);
+                    vy = lds4(ys + w);
+                }
+                X[2 * c] = pick64<PART>(vx.x, vx.y);
+                X[2 * c + 1] = pick64<PART>(vx.z, vx.w);
+                Y[2 * c] = pick64<PART>(vy.x, vy.y);
+                Y[2 * c + 1] = pick64<PART>(vy.z, vy.w);
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+                const uint32_t w = g0 + 2 * e;
+                const bool in = w < wpb;
+                X[e] = in ? pick64<PART>(xs[w], xs[w + 1]) : 0u;
+                Y[e] = in ? pick64<PART>(ys[w], ys[w + 1]) : 0u;
+            }
+        }
+        slice<32>(X, mu);
+        slice<32>(Y, mu);
+        gram_diagonals<32, 32>(X, Y, acc);
+    }
+    return parity_bits64<63>(acc, mu);
+}
+
+__device__ __forceinline__ uint64_t combine_q64(uint64_t A, uint64_t B, uint64_t C, const StreamArgs &s) {
+    const uint64_t M = C ^ A ^ B;  // middle term, degree <= 62
+    return reduce_mod_p64(A ^ (M << 32), B ^ (M >> 32), s);
+}
+
+// ---------------------------------------------------------------------------
+// Fused ingest: pack the raw b-bit samples behind stream words [w0, w0 + nw)
+// straight into shared memory (sample s at stream bits [s*b, (s+1)*b), LSB
+// first; samples past nsamples read as 0).  One period per thread and step:
+//   b = 12: 8 samples (16 bytes) -> 3 words; b = 8: 4 samples -> 1 word;
+//   b = 16: 2 samples -> 1 word.
+// ---------------------------------------------------------------------------
+// 8 raw samples (16 bytes) at smp[s0 .. s0+8); samples at or past `avail`
+// read as 0.
+__device__ __forceinline__ uint4 load_period8(const uint16_t *__restrict__ smp, uint32_t s0, uint32_t avail) {
+    if (s0 + 8 <= avail) return __ldg(reinterpret_cast<const uint4 *>(smp + s0));
+    uint32_t q[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const uint32_t lo = s0 + 2 * j < avail ? __ldg(smp + s0 + 2 * j) : 0u;
+        const uint32_t hi = s0 + 2 * j + 1 < avail ? __ldg(smp + s0 + 2 * j + 1) : 0u;
+        q[j] = lo | (hi << 16);
+    }
+    return make_uint4(q[0], q[1], q[2], q[3]);
+}
+
+// The words a period of 8 samples yields: b = 12 -> 3 words, b = 8 -> 2 words
+// (two periods of 4), b = 16 -> 4 words.
+template <int B>
+struct PeriodOf {
+    static constexpr int kWords = B == 12 ? 3 : B == 8 ? 2 : 4;
+};
+
+template <int B>
+__device__ __forceinline__ void pack_period8(const uint4 v, uint32_t (&w)[PeriodOf<B>::kWords]) {
+    if constexpr (B == 12) {
+        // each sample pair q = s | t << 16 -> bits 0..23 of P = s | t << 12:
+        // bits 0..11 from q, bits 12..23 from q >> 4.  The bits of s and t
+        // above 12 fall outside bits 0..23 (t's land in byte 3), and the byte
+        // permutes below take bytes 0..2 of each P only.
+        const uint32_t q[4] = {v.x, v.y, v.z, v.w};
+        uint32_t P[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) P[j] = lop_select(q[j], __umulhi(q[j], 1u << 28), 0x00000FFFu);
+        w[0] = __byte_perm(P[0], P[1], 0x4210);
+        w[1] = __byte_perm(P[1], P[2], 0x5421);
+        w[2] = __byte_perm(P[2], P[3], 0x6542);
+    } else if constexpr (B == 8) {
+        w[0] = __byte_perm(v.x, v.y, 0x6420);  // low bytes of four samples
+        w[1] = __byte_perm(v.z, v.w, 0x6420);
+    } else {
+        w[0] = v.x;
+        w[1] = v.y;
+        w[2] = v.z;
+        w[3] = v.w;
+    }
+}
+
+// Fused ingest: pack the raw b-bit samples behind stream words [w0, w0 + nw)
+// of both sources straight into shared memory (sample s at stream bits
+// [s*b, (s+1)*b), LSB first; samples past nsamples read as 0).  Work comes in
+// periods of 8 samples; each thread loads kBatch periods of x and of y before
+// packing any, so that many 16-byte loads are in flight.  Indices are local to
+// the tile (32-bit); only the first and last period can straddle the tile.
+template <int B>
+__device__ __forceinline__ void pack_tile(const uint16_t *__restrict__ sx, const uint16_t *__restrict__ sy,
+                                          uint64_t nsamples, uint64_t w0, uint32_t nw, uint32_t *__restrict__ dx,
+                                          uint32_t *__restrict__ dy, uint32_t tid, uint32_t nthreads) {
+    constexpr uint32_t WP = PeriodOf<B>::kWords;  // words per period of 8 samples
+    constexpr int kBatch = 4;
+    const uint64_t p0 = w0 / WP;
+    const uint32_t phi = uint32_t(w0 - p0 * WP);  // tile words that precede w0 in period p0
+    const uint32_t nper = (phi + nw + WP - 1) / WP;
+    const uint64_t s_base = 8 * p0;
+    const uint64_t left = nsamples > s_base ? nsamples - s_base : 0;
+    const uint32_t avail = left > 0xFFFFFFF0ull ? 0xFFFFFFF0u : uint32_t(left);
+    const uint16_t *bx = sx + s_base, *by = sy + s_base;
+    for (uint32_t jb = tid; jb < nper; jb += kBatch * nthreads) {
+        uint4 vx[kBatch], vy[kBatch];
+#pragma unroll
+        for (int k = 0; k < kBatch; ++k) {
+            const uint32_t j = jb + k * nthreads;
+            vx[k] = vy[k] = make_uint4(0, 0, 0, 0);
+            if (j < nper) {
+                vx[k] = load_period8(bx, 8 * j, avail);
+                vy[k] = load_period8(by, 8 * j, avail);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kBatch; ++k) {
+            const uint32_t j = jb + k * nthreads;
+            if (j < nper) {
+                uint32_t wx[WP], wy[WP];
+                pack_period8<B>(vx[k], wx);
+                pack_period8<B>(vy[k], wy);
+                const uint32_t lw = WP * j - phi;  // tile word of the period's first word (wraps if < 0)
+                if (j > 0 && j + 1 < nper) {
+#pragma unroll
+                    for (uint32_t i = 0; i < WP; ++i) {
+                        dx[lw + i] = wx[i];
+                        dy[lw + i] = wy[i];
+                    }
+                } else {
+#pragma unroll
+                    for (uint32_t i = 0; i < WP; ++i)
+                        if (lw + i < nw) {
+                            dx[lw + i] = wx[i];
+                            dy[lw + i] = wy[i];
+                        }
+                }
+            }
+        }
+    }
+}
+
+}  // namespace qxd

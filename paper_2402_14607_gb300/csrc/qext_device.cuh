@@ -1,0 +1,354 @@
+// Device primitives of the extraction kernels (sm_103a): register bit-matrix
+// transposes, the sliced GF(2) Gram-diagonal accumulation of Ext_IP
+// (Definition 3.2), parity folding, reduction mod P, output assembly, and the
+// TMA bulk-copy / mbarrier helpers with bounded waits.
+//
+// Formulation.  For one block, Z = sum_i x_i * y_i in GF(2^q).  Reduction
+// mod P is F_2-linear, so the unreduced sum of carry-less products
+//     z_k = XOR_{i} XOR_{j+l=k} x_{i,j} & y_{i,l}      (k < 2q-1)
+// is accumulated first and reduced once per block.  Thirty-two elements are
+// "sliced": a register transpose turns q packed words (32/q elements each)
+// into q words S[j] whose bit s is bit j of element s.  Then
+//     acc[j+l] ^= SX[j] & SY[l]     (one LOP3 per 32 bit-products)
+// and z_k = parity(acc[k]) once all elements are in.  The slot order inside
+// the words is the same for x and y and the parity sums over slots, so the
+// order of elements (and of whole words) inside a block never matters.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "qext_internal.h"
+
+// Sticky device status word (defined in qext_ingest.cu).
+extern __device__ int qext_device_status_word;
+
+namespace qxd {
+
+// 2^G and 2^(32-G) for G = 1, 2, 4 (index log2 G).  Passed at run time so the
+// shifts of the transpose stages issue as IMAD / IMAD.HI on the FMA pipe
+// instead of SHF on the ALU pipe, which the AND/XOR work already saturates.
+struct ShiftMuls {
+    uint32_t lo[3];  // 2^G
+    uint32_t hi[3];  // 2^(32-G): umulhi(a, 2^(32-G)) = a >> G
+};
+
+// Everything a kernel needs to know about one stream pair.
+struct StreamArgs {
+    const uint32_t *x;      // packed words (or samples, for the fused ingest)
+    const uint32_t *y;
+    uint32_t *out;
+    uint64_t nblocks;
+    uint32_t wpb;           // words per block per source (n / 32)
+    uint32_t m;             // output bits per block
+    uint32_t ntaps;         // taps of P below x^q (0 for q = 1), descending, last 0
+    uint32_t taps[4];
+    uint32_t tap_mul[4];    // 2^taps[t] for t < ntaps, else 0 (run-time multipliers, see ShiftMuls)
+};
+
+__host__ __device__ inline ShiftMuls make_shift_muls() {
+    ShiftMuls mu;
+    for (int i = 0; i < 3; ++i) {
+        mu.lo[i] = 1u << (1 << i);
+        mu.hi[i] = 1u << (32 - (1 << i));
+    }
+    return mu;
+}
+
+// ---------------------------------------------------------------------------
+// Register bit-matrix primitives.
+// ---------------------------------------------------------------------------
+template <int G>
+__device__ __forceinline__ constexpr uint32_t low_mask() {
+    return G == 1 ? 0x55555555u : G == 2 ? 0x33333333u : G == 4 ? 0x0F0F0F0Fu : G == 8 ? 0x00FF00FFu : 0x0000FFFFu;
+}
+
+template <int G>
+__device__ __forceinline__ constexpr int log2_of() {
+    return G == 1 ? 0 : G == 2 ? 1 : 2;
+}
+
+// Single LOP3 instructions (truth tables over a = 0xF0, b = 0xCC, c = 0xAA).
+// (a & c) | (b & ~c): bitwise select of a where c is set, else b
+__device__ __forceinline__ uint32_t lop_select(uint32_t a, uint32_t b, uint32_t c) {
+    uint32_t d;
+    asm("lop3.b32 %0, %1, %2, %3, 0xE4;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+// c ^ (a & b): one GF(2) multiply-accumulate per bit
+__device__ __forceinline__ uint32_t lop_and_xor(uint32_t a, uint32_t b, uint32_t c) {
+    uint32_t d;
+    asm("lop3.b32 %0, %1, %2, %3, 0x6A;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+// a ^ b ^ c
+__device__ __forceinline__ uint32_t lop_xor3(uint32_t a, uint32_t b, uint32_t c) {
+    uint32_t d;
+    asm("lop3.b32 %0, %1, %2, %3, 0x96;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+
+// One exchange stage of a recursive bit transpose between words a and b:
+// in every 2G-bit lane, a keeps its low G bits and receives b's low G bits
+// on top; b receives a's high G bits below its own high G bits.
+template <int G>
+__device__ __forceinline__ void exchange(uint32_t &a, uint32_t &b, const ShiftMuls &mu) {
+    if constexpr (G == 16) {
+        const uint32_t na = __byte_perm(a, b, 0x5410), nb = __byte_perm(a, b, 0x7632);
+        a = na;
+        b = nb;
+    } else if constexpr (G == 8) {
+        const uint32_t na = __byte_perm(a, b, 0x6240), nb = __byte_perm(a, b, 0x7351);
+        a = na;
+        b = nb;
+    } else {
+        constexpr uint32_t M = low_mask<G>();
+        const uint32_t up = b * mu.lo[log2_of<G>()];           // b << G   (IMAD)
+        const uint32_t dn = __umulhi(a, mu.hi[log2_of<G>()]);  // a >> G   (IMAD.HI)
+        const uint32_t na = lop_select(a, up, M);
+        const uint32_t nb = lop_select(dn, b, M);
+        a = na;
+        b = nb;
+    }
+}
+
+// Transpose stages G = N/2 .. 1 over N words.  With N = Q <= 32 and Q-bit
+// elements packed 32/Q per word, word j afterwards holds bit j of every
+// element; with N = 32 it is the full 32x32 bit transpose.
+template <int N, int G>
+__device__ __forceinline__ void slice_stages(uint32_t (&w)[N], const ShiftMuls &mu) {
+    if constexpr (G >= 1) {
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+            if ((i & G) == 0) exchange<G>(w[i], w[i + G], mu);
+        slice_stages<N, G / 2>(w, mu);
+    }
+}
+
+template <int N>
+__device__ __forceinline__ void slice(uint32_t (&w)[N], const ShiftMuls &mu) {
+    if constexpr (N > 1) slice_stages<N, N / 2>(w, mu);
+}
+
+// acc[j + l] ^= X[j] & Y[l] for j < NX, l < NY (offsets into the arrays).
+template <int NX, int NY, int NA>
+__device__ __forceinline__ void gram_diagonals(const uint32_t *X, const uint32_t *Y, uint32_t (&acc)[NA]) {
+    static_assert(NA >= NX + NY - 1, "accumulator too short");
+#pragma unroll
+    for (int j = 0; j < NX; ++j)
+#pragma unroll
+        for (int l = 0; l < NY; ++l) acc[j + l] = lop_and_xor(X[j], Y[l], acc[j + l]);
+}
+
+// Parities of 32 words at once: after folding stages G = 16 .. 1 (each an
+// exchange followed by XOR of the pair), bit p of a[0] is the parity of the
+// original a[p].
+template <int G>
+__device__ __forceinline__ void parity_fold(uint32_t (&a)[32], const ShiftMuls &mu) {
+    if constexpr (G >= 1) {
+#pragma unroll
+        for (int i = 0; i < G; ++i) {
+            uint32_t u = a[i], v = a[i + G];
+            exchange<G>(u, v, mu);
+            a[i] = u ^ v;
+        }
+        parity_fold<G / 2>(a, mu);
+    }
+}
+
+template <int N, int G>
+__device__ __forceinline__ void parity_fold_n(uint32_t (&a)[N], const ShiftMuls &mu) {
+    if constexpr (G >= 1) {
+#pragma unroll
+        for (int i = 0; i < G; ++i) {
+            uint32_t u = a[i], v = a[i + G];
+            exchange<G>(u, v, mu);
+            a[i] = u ^ v;
+        }
+        parity_fold_n<N, G / 2>(a, mu);
+    }
+}
+
+// bit k of the result = parity(acc[k]) for k < K (K <= 32).  With N = the
+// power of two >= K, stages G = N/2 .. 1 leave, in every N-bit segment of
+// a[0], bit p = parity of that segment of acc[p]; XORing the 32/N segments
+// together finishes the parities.
+template <int K>
+__device__ __forceinline__ uint32_t parity_bits32(const uint32_t *acc, const ShiftMuls &mu) {
+    constexpr int N = K <= 1 ? 1 : K <= 2 ? 2 : K <= 4 ? 4 : K <= 8 ? 8 : K <= 16 ? 16 : 32;
+    uint32_t a[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) a[i] = i < K ? acc[i] : 0u;
+    parity_fold_n<N, N / 2>(a, mu);
+    uint32_t r = a[0];
+    if constexpr (N <= 16) r ^= r >> 16;
+    if constexpr (N <= 8) r ^= r >> 8;
+    if constexpr (N <= 4) r ^= r >> 4;
+    if constexpr (N <= 2) r ^= r >> 2;
+    if constexpr (N <= 1) r ^= r >> 1;
+    return r & (N == 32 ? 0xFFFFFFFFu : ((1u << N) - 1u));
+}
+
+template <int K>
+__device__ __forceinline__ uint64_t parity_bits64(const uint32_t *acc, const ShiftMuls &mu) {
+    if constexpr (K <= 32) {
+        return parity_bits32<K>(acc, mu);
+    } else {
+        return uint64_t(parity_bits32<32>(acc, mu)) | (uint64_t(parity_bits32<K - 32>(acc + 32, mu)) << 32);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Reduction mod P = x^q + sum_t x^taps[t] (taps end with 0).  Two folds of the
+// part at and above x^q suffice when the top tap c satisfies 2c - 2 < q
+// (checked at plan time).
+// ---------------------------------------------------------------------------
+template <int Q>
+__device__ __forceinline__ uint64_t reduce_mod_p(uint64_t z, const StreamArgs &s) {
+    if constexpr (Q == 1) {
+        return z & 1u;
+    } else if constexpr (Q <= 16) {
+        // 2q-1 <= 31 bits: 32-bit arithmetic, shifts by taps as IMADs
+        // unused taps carry multiplier 0, so no predicates are needed
+        uint32_t w = uint32_t(z);
+        constexpr uint32_t LOW = (1u << Q) - 1u;
+#pragma unroll
+        for (int f = 0; f < 2; ++f) {
+            const uint32_t hi = w >> Q;
+            w = lop_xor3(w & LOW, hi * s.tap_mul[0], hi * s.tap_mul[1]);
+            w = lop_xor3(w, hi * s.tap_mul[2], hi * s.tap_mul[3]);
+        }
+        return w;
+    } else {
+        constexpr uint64_t LOW = Q == 64 ? ~uint64_t(0) : (uint64_t(1) << (Q % 64)) - 1;
+#pragma unroll
+        for (int f = 0; f < 2; ++f) {
+            const uint64_t hi = z >> Q;
+            z &= LOW;
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+                if (t < int(s.ntaps)) z ^= hi << s.taps[t];
+        }
+        return z;
+    }
+}
+
+// 127-bit (lo, hi) reduced mod a degree-64 P.
+__device__ __forceinline__ uint64_t reduce_mod_p64(uint64_t lo, uint64_t hi, const StreamArgs &s) {
+    uint64_t carry = 0;
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+        if (t < int(s.ntaps)) {
+            const uint32_t sh = s.taps[t];
+            lo ^= hi << sh;
+            if (sh) carry ^= hi >> (64 - sh);
+        }
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+        if (t < int(s.ntaps)) lo ^= carry << s.taps[t];
+    return lo;
+}
+
+// ---------------------------------------------------------------------------
+// Output: 32 consecutive blocks base .. base+31 (base a multiple of 32, one
+// per lane, value v already truncated to m bits, 0 past nblocks) own exactly
+// m output words starting at word (base/32)*m.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void store_warp(uint64_t v, uint64_t base, uint64_t nblocks, uint32_t m,
+                                           uint32_t *__restrict__ out) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t word0 = (base >> 5) * m;
+    const uint64_t total = (nblocks * m + 31) >> 5;
+    if (m == 64) {
+        const uint64_t w = word0 + 2 * lane;
+        if (w < total) out[w] = uint32_t(v);
+        if (w + 1 < total) out[w + 1] = uint32_t(v >> 32);
+        return;
+    }
+    if ((32u % m) == 0) {
+        const uint32_t k = 32u / m;  // values per word
+        uint32_t word = uint32_t(v) << (m * (lane % k));
+        for (uint32_t off = 1; off < k; off <<= 1) word |= __shfl_xor_sync(0xffffffffu, word, int(off));
+        const uint64_t w = word0 + lane / k;
+        if (lane % k == 0 && w < total) out[w] = word;
+        return;
+    }
+    const uint32_t reach = 31u / m + 2u;  // most lanes that can meet one word
+    for (uint32_t r = 0; r * 32u < m; ++r) {
+        const uint32_t w = lane + 32u * r;
+        const uint32_t first = (32u * w) / m;
+        uint32_t word = 0;
+        for (uint32_t t = 0; t < reach; ++t) {
+            const uint32_t i = first + t;
+            const uint64_t vi = __shfl_sync(0xffffffffu, v, int(i < 32u ? i : 31u));
+            const int sft = int(i * m) - int(32u * w);
+            if (w < m && i < 32u && sft < 32) {
+                if (sft >= 0)
+                    word |= uint32_t(vi << sft);
+                else if (sft > -64)
+                    word |= uint32_t(vi >> (-sft));
+            }
+        }
+        if (w < m && word0 + w < total) out[word0 + w] = word;
+    }
+}
+
+__device__ __forceinline__ uint64_t mask_m(uint32_t m) {
+    return m >= 64 ? ~uint64_t(0) : ((uint64_t(1) << m) - 1);
+}
+
+// ---------------------------------------------------------------------------
+// TMA bulk copies and mbarriers (sm_90+ async proxy, used on sm_103a).
+// ---------------------------------------------------------------------------
+constexpr uint32_t kMaxPolls = 4u << 20;  // bounded mbarrier wait (polls)
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// 1-D bulk copy global -> shared, completion signalled on bar (16-byte
+// aligned addresses, size a multiple of 16).
+__device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Waits for phase `parity` of bar to complete; gives up after kMaxPolls.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    for (uint32_t i = 0; i < kMaxPolls; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void record_status(int code) { atomicCAS(&qext_device_status_word, 0, code); }
+
+}  // namespace qxd

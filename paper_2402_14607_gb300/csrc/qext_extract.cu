@@ -1,345 +1,256 @@
-// Per-block extraction kernels for Ext_IP^{n_p,q} (Definition 3.2) inside
-// Algorithm 1's block loop, for GB300 (sm_103a).
+// Per-block extraction Ext_IP^{n_p,q} (Definition 3.2) inside Algorithm 1's
+// block loop, for GB300 (sm_103a).  See qext_device.cuh for the sliced GF(2)
+// formulation.
 //
-// Formulation.  For one block, Z = sum_i x_i * y_i in GF(2^q).  Reduction
-// mod P is F_2-linear, so the unreduced sum of carry-less products
-//     z_k = XOR_{i} XOR_{j+l=k} x_{i,j} & y_{i,l}      (k < 2q-1)
-// is accumulated first and reduced once per block.  Thirty-two elements are
-// "sliced": a register transpose turns q packed words (32/q elements each)
-// into q words S[j] whose bit s is bit j of element s.  Then
-//     acc[j+l] ^= SX[j] & SY[l]     (one LOP3 per 32 bit-products)
-// and z_k = parity(acc[k]) after all elements are in.  The slot order inside
-// the words is the same for x and y, and the parity sums over slots, so the
-// element order inside a group never matters.
+// Tiled kernel (the main path).  A persistent CTA walks tiles of T
+// consecutive blocks.  Each tile of x and y arrives in shared memory by two
+// 1-D TMA bulk copies (cp.async.bulk, completion on an mbarrier); the copy of
+// the next tile is issued before the current one is computed (two buffers).
+// Each thread (two for q = 64) computes one block from shared memory, reading
+// its 16-byte chunks in a lane-rotated order so that eight consecutive lanes
+// hit eight different bank groups.  Block values go to shared memory and warps
+// assemble m-bit outputs of 32 consecutive blocks into whole words.
 //
-// Everything is exact GF(2): AND, XOR, shifts and byte permutes only.
+// Direct kernel (fallback for blocks too long to stage): each thread loads its
+// own block from global memory.
 #include <cuda_runtime.h>
 
 #include <cstdint>
 
+#include "qext_block.cuh"
 #include "qext_internal.h"
+
+using namespace qxd;
 
 namespace {
 
-// 2^G and 2^(32-G) for G = 1, 2, 4 (index log2 G).  Passed at run time so the
-// shifts of the transpose stages issue as IMAD / IMAD.HI on the FMA pipe
-// instead of SHF on the ALU pipe, which the AND/XOR work already saturates.
-struct ShiftMuls {
-    uint32_t lo[3];  // 2^G
-    uint32_t hi[3];  // 2^(32-G): umulhi(a, 2^(32-G)) = a >> G
-};
+constexpr int kThreads = 128;
+constexpr int kSmemBudget = 100 * 1024;  // per CTA: at least two CTAs per SM
 
-struct ExtractArgs {
-    const uint32_t *x;
-    const uint32_t *y;
-    uint32_t *out;
-    uint64_t nblocks;
-    uint32_t wpb;      // words per block per source (n / 32)
-    uint32_t m;        // output bits per block
-    uint32_t ntaps;    // taps of P below x^q (0 for q = 1)
-    uint32_t taps[4];  // descending, last is 0 (the constant term)
-    int vec16;         // x, y 16-byte aligned and wpb % 4 == 0
-    int vec8;          // x, y 8-byte aligned and wpb % 2 == 0
+struct TileArgs {
+    StreamArgs s;
+    const uint16_t *sx;  // raw ADC samples (fused ingest), else null
+    const uint16_t *sy;
+    uint64_t nsamples;
     ShiftMuls mu;
+    uint64_t ntiles;
+    uint32_t T;     // blocks per tile (multiple of 32)
+    uint32_t nbuf;  // 1 or 2 tile buffers
+    int tma;        // x, y 16-byte aligned: full tiles arrive by bulk copy
+    int vec;        // wpb % 4 == 0: 16-byte shared-memory reads
+};
+
+template <int Q>
+struct QTraits {
+    static constexpr int TPB = Q == 64 ? 2 : 1;  // threads per block
 };
 
 // ---------------------------------------------------------------------------
-// Register bit-matrix primitives.
+// Tiled kernel.  B = 0: packed words arrive by TMA; B = 8, 12, 16: the tile
+// is packed from raw samples by the CTA (fused ingest).
 // ---------------------------------------------------------------------------
-template <int G>
-__device__ __forceinline__ constexpr uint32_t low_mask() {
-    return G == 1 ? 0x55555555u : G == 2 ? 0x33333333u : G == 4 ? 0x0F0F0F0Fu : G == 8 ? 0x00FF00FFu : 0x0000FFFFu;
-}
+template <int Q, int B>
+__global__ void __launch_bounds__(kThreads) extract_tiled_kernel(const TileArgs ta) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    __shared__ __align__(8) uint64_t full[2];
+    __shared__ uint64_t vals[kThreads];
+    constexpr int TPB = QTraits<Q>::TPB;
+    const StreamArgs &s = ta.s;
+    const uint32_t tid = threadIdx.x;
+    const uint32_t T = ta.T;
+    const uint32_t tw = T * s.wpb;  // words per tile per source
+    const uint32_t nthreads = T * TPB;
+    uint32_t *bufs[2] = {smem, smem + (ta.nbuf > 1 ? 2 * tw : 0)};
 
-// One exchange stage of a recursive bit transpose between words a and b:
-// in every 2G-bit lane, a keeps its low G bits and receives b's low G bits
-// on top; b receives a's high G bits below its own high G bits.
-template <int G>
-__device__ __forceinline__ constexpr int log2_of() {
-    return G == 1 ? 0 : G == 2 ? 1 : 2;
-}
-
-template <int G>
-__device__ __forceinline__ void exchange(uint32_t &a, uint32_t &b, const ShiftMuls &mu) {
-    if constexpr (G == 16) {
-        const uint32_t na = __byte_perm(a, b, 0x5410), nb = __byte_perm(a, b, 0x7632);
-        a = na;
-        b = nb;
-    } else if constexpr (G == 8) {
-        const uint32_t na = __byte_perm(a, b, 0x6240), nb = __byte_perm(a, b, 0x7351);
-        a = na;
-        b = nb;
-    } else {
-        constexpr uint32_t M = low_mask<G>();
-        const uint32_t up = b * mu.lo[log2_of<G>()];             // b << G   (IMAD)
-        const uint32_t dn = __umulhi(a, mu.hi[log2_of<G>()]);    // a >> G   (IMAD.HI)
-        const uint32_t na = (a & M) | (up & ~M);
-        const uint32_t nb = (dn & M) | (b & ~M);
-        a = na;
-        b = nb;
+    if (tid == 0) {
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
+        fence_mbar_init();
     }
-}
+    __syncthreads();
 
-// Transpose stages G = Q/2 .. 1 over Q words: afterwards w[j] holds bit j of
-// every element (Q-bit elements packed 32/Q per word).
-template <int Q, int G>
-__device__ __forceinline__ void slice_stages(uint32_t (&w)[Q], const ShiftMuls &mu) {
-    if constexpr (G >= 1) {
-#pragma unroll
-        for (int i = 0; i < Q; ++i)
-            if ((i & G) == 0) exchange<G>(w[i], w[i + G], mu);
-        slice_stages<Q, G / 2>(w, mu);
-    }
-}
+    auto full_tile = [&](uint64_t t) { return (t + 1) * uint64_t(T) <= s.nblocks; };
+    auto issue = [&](uint64_t t, int b) {
+        const uint32_t bytes = tw * 4u;
+        mbar_expect_tx(&full[b], 2u * bytes);
+        tma_load_1d(bufs[b], s.x + t * tw, bytes, &full[b]);
+        tma_load_1d(bufs[b] + tw, s.y + t * tw, bytes, &full[b]);
+    };
 
-template <int Q>
-__device__ __forceinline__ void slice(uint32_t (&w)[Q], const ShiftMuls &mu) {
-    slice_stages<Q, Q / 2>(w, mu);
-}
-
-// acc[j + l] ^= X[j] & Y[l] for all j, l < Q (schoolbook Gram diagonals).
-template <int Q>
-__device__ __forceinline__ void gram_diagonals(const uint32_t (&X)[Q], const uint32_t (&Y)[Q], uint32_t (&acc)[2 * Q - 1]) {
-#pragma unroll
-    for (int j = 0; j < Q; ++j)
-#pragma unroll
-        for (int l = 0; l < Q; ++l) acc[j + l] ^= X[j] & Y[l];
-}
-
-// Parities of 32 words at once: after folding stages G = 16 .. 1 (each an
-// exchange followed by XOR of the pair), bit p of the result is the parity
-// of a[p].
-template <int G>
-__device__ __forceinline__ void parity_fold(uint32_t (&a)[32], const ShiftMuls &mu) {
-    if constexpr (G >= 1) {
-#pragma unroll
-        for (int i = 0; i < G; ++i) {
-            uint32_t u = a[i], v = a[i + G];
-            exchange<G>(u, v, mu);
-            a[i] = u ^ v;
+    uint64_t tile = blockIdx.x;
+    if (tid == 0 && ta.tma && tile < ta.ntiles && full_tile(tile)) issue(tile, 0);
+    for (uint32_t k = 0; tile < ta.ntiles; ++k, tile += gridDim.x) {
+        const int b = ta.nbuf > 1 ? int(k & 1u) : 0;
+        const uint64_t next = tile + gridDim.x;
+        if (tid == 0 && ta.tma) {
+            if (ta.nbuf > 1) {
+                if (next < ta.ntiles && full_tile(next)) issue(next, b ^ 1);  // prefetch
+            } else if (k > 0 && full_tile(tile)) {
+                issue(tile, 0);  // single buffer: free since the last __syncthreads
+            }
         }
-        parity_fold<G / 2>(a, mu);
-    }
-}
-
-template <int K>
-__device__ __forceinline__ uint32_t parity_bits32(const uint32_t *acc, const ShiftMuls &mu) {
-    uint32_t a[32];
-#pragma unroll
-    for (int i = 0; i < 32; ++i) a[i] = i < K ? acc[i] : 0u;
-    parity_fold<16>(a, mu);
-    return a[0];
-}
-
-// ---------------------------------------------------------------------------
-// Loads.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint4 ldg4(const uint32_t *p) {
-    return __ldg(reinterpret_cast<const uint4 *>(p));
-}
-
-// Q consecutive words of a block starting at word g0 (zero past wpb).
-template <int Q>
-__device__ __forceinline__ void load_group(const uint32_t *blk, uint32_t g0, uint32_t wpb, int vec16, uint32_t (&w)[Q]) {
-    if (g0 + Q <= wpb) {
-        if constexpr (Q % 4 == 0) {
-            if (vec16) {
-#pragma unroll
-                for (int i = 0; i < Q; i += 4) {
-                    const uint4 v = ldg4(blk + g0 + i);
-                    w[i] = v.x;
-                    w[i + 1] = v.y;
-                    w[i + 2] = v.z;
-                    w[i + 3] = v.w;
+        uint32_t *xs = bufs[b], *ys = bufs[b] + tw;
+        if constexpr (B != 0) {
+            const uint64_t nb = s.nblocks - tile * T < T ? s.nblocks - tile * T : T;
+            pack_tile<B>(ta.sx, ta.sy, ta.nsamples, tile * tw, uint32_t(nb * s.wpb), xs, ys, tid, nthreads);
+            __syncthreads();
+        } else if (ta.tma && full_tile(tile)) {
+            const uint32_t use = ta.nbuf > 1 ? (k >> 1) : k;
+            const bool ok = mbar_wait_bounded(&full[b], use & 1u);
+            if (!__syncthreads_and(ok)) {
+                if (tid == 0) {
+                    record_status(QEXT_E_TIMEOUT);
+                    // give the copies in flight a bounded chance to land
+                    mbar_wait_bounded(&full[b], use & 1u);
+                    if (ta.nbuf > 1) mbar_wait_bounded(&full[b ^ 1], ((k + 1) >> 1) & 1u);
                 }
                 return;
             }
-        }
-#pragma unroll
-        for (int i = 0; i < Q; ++i) w[i] = __ldg(blk + g0 + i);
-    } else {
-#pragma unroll
-        for (int i = 0; i < Q; ++i) w[i] = (g0 + i < wpb) ? __ldg(blk + g0 + i) : 0u;
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Reduction mod P = x^q + sum_t x^taps[t] (taps include 0).  Two folds of the
-// part at and above x^q suffice when the top tap c satisfies 2c - 2 < q
-// (checked at plan time).
-// ---------------------------------------------------------------------------
-template <int Q>
-__device__ __forceinline__ uint64_t reduce_small(uint64_t z, const ExtractArgs &a) {
-    if constexpr (Q == 1) {
-        return z & 1u;
-    } else {
-        constexpr uint64_t LOW = (uint64_t(1) << Q) - 1;
-#pragma unroll
-        for (int f = 0; f < 2; ++f) {
-            const uint64_t hi = z >> Q;
-            z &= LOW;
-#pragma unroll
-            for (int t = 0; t < 4; ++t)
-                if (t < int(a.ntaps)) z ^= hi << a.taps[t];
-        }
-        return z;
-    }
-}
-
-// 127-bit (lo, hi) reduced mod a degree-64 P.
-__device__ __forceinline__ uint64_t reduce_64(uint64_t lo, uint64_t hi, const ExtractArgs &a) {
-    uint64_t carry = 0;
-#pragma unroll
-    for (int t = 0; t < 4; ++t)
-        if (t < int(a.ntaps)) {
-            const uint32_t s = a.taps[t];
-            lo ^= hi << s;
-            if (s) carry ^= hi >> (64 - s);
-        }
-#pragma unroll
-    for (int t = 0; t < 4; ++t)
-        if (t < int(a.ntaps)) lo ^= carry << a.taps[t];
-    return lo;
-}
-
-// ---------------------------------------------------------------------------
-// One block: reduced Z (q bits; q <= 64).
-// ---------------------------------------------------------------------------
-template <int Q>
-__device__ __forceinline__ uint64_t block_value(const uint32_t *xb, const uint32_t *yb, const ExtractArgs &a) {
-    uint32_t acc[2 * Q - 1];
-#pragma unroll
-    for (int i = 0; i < 2 * Q - 1; ++i) acc[i] = 0;
-    for (uint32_t g0 = 0; g0 < a.wpb; g0 += Q) {
-        uint32_t X[Q], Y[Q];
-        load_group<Q>(xb, g0, a.wpb, a.vec16, X);
-        load_group<Q>(yb, g0, a.wpb, a.vec16, Y);
-        slice<Q>(X, a.mu);
-        slice<Q>(Y, a.mu);
-        gram_diagonals<Q>(X, Y, acc);
-    }
-    uint64_t z;
-    if constexpr (2 * Q - 1 <= 32) {
-        z = parity_bits32<2 * Q - 1>(acc, a.mu);
-    } else {
-        z = uint64_t(parity_bits32<32>(acc, a.mu)) | (uint64_t(parity_bits32<2 * Q - 1 - 32>(acc + 32, a.mu)) << 32);
-    }
-    return reduce_small<Q>(z, a);
-}
-
-// q = 64: elements are word pairs (low word = bits 0..31, high = 32..63).
-// One Karatsuba level over the halves:  z = A + x^64 B + x^32 (C - A - B),
-// A = sum lo*lo, B = sum hi*hi, C = sum (lo^hi)*(hi^lo); each a 32x32
-// sliced Gram product over groups of 32 elements.  Transposition is linear,
-// so C's operands are sliced from the XOR of the raw words.
-template <int PART>
-__device__ __forceinline__ void load_half64(const uint32_t *blk, uint32_t g0, uint32_t wpb, int vec8,
-                                            uint32_t (&w)[32]) {
-    // a group of 32 elements is the 64 words starting at g0; wpb is even
-#pragma unroll
-    for (int e = 0; e < 32; ++e) {
-        const uint32_t i = g0 + 2 * e;
-        uint32_t lo = 0, hi = 0;
-        if (i < wpb) {
-            if (vec8) {
-                const uint2 v = __ldg(reinterpret_cast<const uint2 *>(blk + i));
-                lo = v.x;
-                hi = v.y;
-            } else {
-                lo = __ldg(blk + i);
-                hi = __ldg(blk + i + 1);
+        } else {
+            const uint64_t nb = s.nblocks - tile * T < T ? s.nblocks - tile * T : T;
+            const uint64_t nw = nb * s.wpb;
+            for (uint64_t i = tid; i < nw; i += nthreads) {
+                xs[i] = __ldg(s.x + tile * tw + i);
+                ys[i] = __ldg(s.y + tile * tw + i);
             }
+            __syncthreads();
         }
-        w[e] = PART == 0 ? lo : PART == 1 ? hi : (lo ^ hi);
-    }
-}
 
-template <int PART>
-__device__ __forceinline__ uint64_t half_product64(const uint32_t *xb, const uint32_t *yb, const ExtractArgs &a) {
-    uint32_t acc[63];
-#pragma unroll
-    for (int i = 0; i < 63; ++i) acc[i] = 0;
-    for (uint32_t g0 = 0; g0 < a.wpb; g0 += 64) {
-        uint32_t X[32], Y[32];
-        load_half64<PART>(xb, g0, a.wpb, a.vec8, X);
-        load_half64<PART>(yb, g0, a.wpb, a.vec8, Y);
-        slice<32>(X, a.mu);
-        slice<32>(Y, a.mu);
-        gram_diagonals<32>(X, Y, acc);
-    }
-    return uint64_t(parity_bits32<32>(acc, a.mu)) | (uint64_t(parity_bits32<31>(acc + 32, a.mu)) << 32);
-}
-
-template <>
-__device__ __forceinline__ uint64_t block_value<64>(const uint32_t *xb, const uint32_t *yb, const ExtractArgs &a) {
-    const uint64_t A = half_product64<0>(xb, yb, a);
-    const uint64_t B = half_product64<1>(xb, yb, a);
-    const uint64_t C = half_product64<2>(xb, yb, a);
-    const uint64_t M = C ^ A ^ B;  // middle term, degree <= 62
-    const uint64_t lo = A ^ (M << 32);
-    const uint64_t hi = B ^ (M >> 32);
-    return reduce_64(lo, hi, a);
-}
-
-// ---------------------------------------------------------------------------
-// Output: 32 consecutive blocks (one per lane, starting at a multiple of 32)
-// own exactly m output words.  Lane w assembles word w (and w + 32) from the
-// m-bit values of the lanes whose bit ranges meet it.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void store_warp(uint64_t v, uint64_t base, const ExtractArgs &a) {
-    const uint32_t lane = threadIdx.x & 31u;
-    const uint32_t m = a.m;
-    const uint64_t word0 = (base >> 5) * m;
-    const uint64_t total = (a.nblocks * m + 31) >> 5;
-    const uint32_t reach = 31u / m + 2u;  // most lanes that can meet one word
-    for (uint32_t r = 0; r * 32u < m; ++r) {
-        const uint32_t w = lane + 32u * r;
-        const uint32_t first = (32u * w) / m;
-        uint32_t word = 0;
-        for (uint32_t t = 0; t < reach; ++t) {
-            const uint32_t i = first + t;
-            const uint64_t vi = __shfl_sync(0xffffffffu, v, int(i < 32u ? i : 31u));
-            const int s = int(i * m) - int(32u * w);
-            if (w < m && i < 32u && s < 32) {
-                if (s >= 0)
-                    word |= uint32_t(vi << s);
-                else if (s > -64)
-                    word |= uint32_t(vi >> (-s));
+        // compute: one block per thread (q = 64: two threads per block)
+        const uint32_t lb = tid / TPB;
+        const uint64_t blk = tile * T + lb;
+        uint64_t v = 0;
+        if constexpr (Q == 64) {
+            const uint32_t part = tid % TPB;
+            uint64_t A = 0, B = 0, C = 0;
+            if (blk < s.nblocks) {
+                const uint32_t *xb = xs + lb * s.wpb, *yb = ys + lb * s.wpb;
+                A = half_product64<0>(xb, yb, s.wpb, ta.vec, tid, part, TPB, ta.mu);
+                B = half_product64<1>(xb, yb, s.wpb, ta.vec, tid, part, TPB, ta.mu);
+                C = half_product64<2>(xb, yb, s.wpb, ta.vec, tid, part, TPB, ta.mu);
             }
+            A ^= __shfl_xor_sync(0xffffffffu, A, 1);
+            B ^= __shfl_xor_sync(0xffffffffu, B, 1);
+            C ^= __shfl_xor_sync(0xffffffffu, C, 1);
+            if (blk < s.nblocks) v = combine_q64(A, B, C, s) & mask_m(s.m);
+            if (part == 0) vals[lb] = v;
+        } else {
+            if (blk < s.nblocks)
+                v = block_small_q<Q>(xs + lb * s.wpb, ys + lb * s.wpb, s.wpb, ta.vec, tid, ta.mu, s) &
+                    mask_m(s.m);
+            vals[lb] = v;
         }
-        if (w < m && word0 + w < total) a.out[word0 + w] = word;
+        __syncthreads();
+        // output: warp w assembles blocks [32w, 32w + 32) of the tile
+        const uint32_t w = tid >> 5;
+        if (w < T / 32) store_warp(vals[32 * w + (tid & 31u)], tile * T + 32 * w, s.nblocks, s.m, s.out);
+        __syncthreads();
     }
 }
 
+// ---------------------------------------------------------------------------
+// Direct kernel: each thread loads its own block from global memory (blocks
+// too long to stage in shared memory).
+// ---------------------------------------------------------------------------
 template <int Q>
-__global__ void __launch_bounds__(128) extract_kernel(const ExtractArgs a) {
+__global__ void __launch_bounds__(kThreads) extract_direct_kernel(const StreamArgs s, const ShiftMuls mu) {
     const uint32_t lane = threadIdx.x & 31u;
     const uint64_t warp = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
-    const uint64_t mmask = a.m >= 64 ? ~uint64_t(0) : ((uint64_t(1) << a.m) - 1);
-    for (uint64_t base = warp * 32; base < a.nblocks; base += nwarps * 32) {
+    for (uint64_t base = warp * 32; base < s.nblocks; base += nwarps * 32) {
         const uint64_t blk = base + lane;
         uint64_t v = 0;
-        if (blk < a.nblocks) v = block_value<Q>(a.x + blk * a.wpb, a.y + blk * a.wpb, a) & mmask;
-        store_warp(v, base, a);
+        if (blk < s.nblocks) {
+            const uint32_t *xb = s.x + blk * s.wpb, *yb = s.y + blk * s.wpb;
+            if constexpr (Q == 64) {
+                const uint64_t A = half_product64<0>(xb, yb, s.wpb, 0, 0, 0, 1, mu);
+                const uint64_t B = half_product64<1>(xb, yb, s.wpb, 0, 0, 0, 1, mu);
+                const uint64_t C = half_product64<2>(xb, yb, s.wpb, 0, 0, 0, 1, mu);
+                v = combine_q64(A, B, C, s);
+            } else {
+                v = block_small_q<Q>(xb, yb, s.wpb, 0, 0, mu, s);
+            }
+            v &= mask_m(s.m);
+        }
+        store_warp(v, base, s.nblocks, s.m, s.out);
     }
 }
 
-template <int Q>
-int launch_q(const ExtractArgs &a, cudaStream_t s) {
-    static int grid_cap = 0;
-    if (!grid_cap) {
-        int dev = 0, sms = 0, per_sm = 0;
+struct LaunchCache {
+    int sms = 0;
+    int occ_tiled[6] = {0, 0, 0, 0, 0, 0};  // by T (32, 64, 128) and buffers (1, 2)
+    int occ_direct = 0;
+    bool attr = false;
+};
+
+template <int Q, int B>
+int launch_q(const StreamArgs &s, const uint16_t *sx, const uint16_t *sy, uint64_t nsamples, cudaStream_t st,
+             uint32_t flags) {
+    const bool force_direct = B == 0 && (flags & QEXT_F_DIRECT);
+    const uint32_t t_max = (flags & QEXT_F_TILE32) ? 32u : (flags & QEXT_F_TILE64) ? 64u : 128u;
+    const uint32_t nb_max = (flags & QEXT_F_NBUF1) ? 1u : 2u;
+    static LaunchCache cache;
+    const ShiftMuls mu = make_shift_muls();
+    if (!cache.sms) {
+        int dev = 0;
         if (cudaGetDevice(&dev) != cudaSuccess) return QEXT_E_CUDA;
-        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return QEXT_E_CUDA;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, extract_kernel<Q>, 128, 0) != cudaSuccess)
+        if (cudaDeviceGetAttribute(&cache.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             return QEXT_E_CUDA;
-        grid_cap = sms * (per_sm > 0 ? per_sm : 1);
     }
-    const uint64_t warps = (a.nblocks + 31) / 32;
-    const uint64_t ctas = (warps + 3) / 4;
-    const int grid = int(ctas < uint64_t(grid_cap) ? ctas : uint64_t(grid_cap));
-    extract_kernel<Q><<<grid, 128, 0, s>>>(a);
+    constexpr int TPB = QTraits<Q>::TPB;
+    // tile size: the largest T (multiple of 32, T * TPB <= kThreads) whose
+    // buffers fit the per-CTA budget, double-buffered if possible
+    uint32_t T = 0, nbuf = 0;
+    for (uint32_t t = kThreads / TPB < t_max ? kThreads / TPB : t_max; t >= 32 && !T; t /= 2)
+        for (uint32_t nb = nb_max; nb >= 1 && !T; --nb)
+            if (uint64_t(nb) * 2 * t * s.wpb * 4 <= uint64_t(kSmemBudget)) {
+                T = t;
+                nbuf = nb;
+            }
+    if (T && !force_direct) {
+        if (!cache.attr) {
+            if (cudaFuncSetAttribute(extract_tiled_kernel<Q, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     kSmemBudget) != cudaSuccess)
+                return QEXT_E_CUDA;
+            cache.attr = true;
+        }
+        TileArgs ta;
+        ta.s = s;
+        ta.sx = sx;
+        ta.sy = sy;
+        ta.nsamples = nsamples;
+        ta.mu = mu;
+        ta.T = T;
+        ta.nbuf = nbuf;
+        ta.ntiles = (s.nblocks + T - 1) / T;
+        const uintptr_t al = reinterpret_cast<uintptr_t>(s.x) | reinterpret_cast<uintptr_t>(s.y);
+        ta.tma = B == 0 && al % 16 == 0;
+        ta.vec = s.wpb % 4 == 0;
+        const size_t smem = size_t(nbuf) * 2 * T * s.wpb * 4;
+        const int ti = (T == 32 ? 0 : T == 64 ? 1 : 2) + 3 * int(nbuf - 1);
+        int &occ = cache.occ_tiled[ti];
+        if (!occ) {
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, extract_tiled_kernel<Q, B>, int(T * TPB), smem) !=
+                cudaSuccess)
+                return QEXT_E_CUDA;
+            if (occ < 1) occ = 1;
+        }
+        const uint64_t cap = uint64_t(cache.sms) * occ;
+        const int grid = int(ta.ntiles < cap ? ta.ntiles : cap);
+        extract_tiled_kernel<Q, B><<<grid, T * TPB, smem, st>>>(ta);
+    } else {
+        if (B != 0) return QEXT_E_UNSUPPORTED;  // fused ingest needs a staged tile
+        if (!cache.occ_direct) {
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cache.occ_direct, extract_direct_kernel<Q>, kThreads,
+                                                              0) != cudaSuccess)
+                return QEXT_E_CUDA;
+            if (cache.occ_direct < 1) cache.occ_direct = 1;
+        }
+        const uint64_t ctas = (s.nblocks + kThreads - 1) / kThreads;
+        const uint64_t cap = uint64_t(cache.sms) * cache.occ_direct;
+        const int grid = int(ctas < cap ? ctas : cap);
+        extract_direct_kernel<Q><<<grid, kThreads, 0, st>>>(s, mu);
+    }
     return cudaGetLastError() == cudaSuccess ? QEXT_OK : QEXT_E_CUDA;
 }
 
@@ -347,33 +258,57 @@ int launch_q(const ExtractArgs &a, cudaStream_t s) {
 
 namespace qext {
 
-int launch_extract(const qext_plan *p, const uint32_t *x, const uint32_t *y, uint64_t nblocks, uint32_t *out,
-                   qext_cuda_stream stream) {
-    ExtractArgs a;
-    a.x = x;
-    a.y = y;
-    a.out = out;
-    a.nblocks = nblocks;
-    a.wpb = p->n / 32;
-    a.m = p->m;
-    a.ntaps = p->ntaps;
-    for (int i = 0; i < 4; ++i) a.taps[i] = p->taps[i];
-    const uintptr_t al = reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y);
-    a.vec16 = (al % 16 == 0) && (a.wpb % 4 == 0);
-    a.vec8 = (al % 8 == 0) && (a.wpb % 2 == 0);
-    for (int i = 0; i < 3; ++i) {
-        a.mu.lo[i] = 1u << (1 << i);
-        a.mu.hi[i] = 1u << (32 - (1 << i));
+static StreamArgs stream_args(const qext_plan *p, const uint32_t *x, const uint32_t *y, uint64_t nblocks, uint32_t *out) {
+    StreamArgs s;
+    s.x = x;
+    s.y = y;
+    s.out = out;
+    s.nblocks = nblocks;
+    s.wpb = p->n / 32;
+    s.m = p->m;
+    s.ntaps = p->ntaps;
+    for (int i = 0; i < 4; ++i) {
+        s.taps[i] = p->taps[i];
+        s.tap_mul[i] = i < int(p->ntaps) ? 1u << (p->taps[i] & 31u) : 0u;
     }
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    return s;
+}
+
+int launch_extract(const qext_plan *p, const uint32_t *x, const uint32_t *y, uint64_t nblocks, uint32_t *out,
+                   qext_cuda_stream stream, uint32_t flags) {
+    const StreamArgs s = stream_args(p, x, y, nblocks, out);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     switch (p->q) {
-        case 1: return launch_q<1>(a, s);
-        case 2: return launch_q<2>(a, s);
-        case 4: return launch_q<4>(a, s);
-        case 8: return launch_q<8>(a, s);
-        case 16: return launch_q<16>(a, s);
-        case 32: return launch_q<32>(a, s);
-        case 64: return launch_q<64>(a, s);
+        case 1: return launch_q<1, 0>(s, nullptr, nullptr, 0, st, flags);
+        case 2: return launch_q<2, 0>(s, nullptr, nullptr, 0, st, flags);
+        case 4: return launch_q<4, 0>(s, nullptr, nullptr, 0, st, flags);
+        case 8: return launch_q<8, 0>(s, nullptr, nullptr, 0, st, flags);
+        case 16: return launch_q<16, 0>(s, nullptr, nullptr, 0, st, flags);
+        case 32: return launch_q<32, 0>(s, nullptr, nullptr, 0, st, flags);
+        case 64: return launch_q<64, 0>(s, nullptr, nullptr, 0, st, flags);
+        default: return QEXT_E_UNSUPPORTED;
+    }
+}
+
+template <int B>
+static int launch_samples_b(const qext_plan *p, const StreamArgs &s, const uint16_t *sx, const uint16_t *sy,
+                            uint64_t nsamples, cudaStream_t st, uint32_t flags) {
+    switch (p->q) {
+        case 64: return launch_q<64, B>(s, sx, sy, nsamples, st, flags);
+        default: return QEXT_E_UNSUPPORTED;
+    }
+}
+
+int launch_extract_samples(const qext_plan *p, uint32_t b, const uint16_t *sx, const uint16_t *sy,
+                           uint64_t nsamples, uint64_t nblocks, uint32_t *out, qext_cuda_stream stream,
+                           uint32_t flags) {
+    const StreamArgs s = stream_args(p, nullptr, nullptr, nblocks, out);
+    if (p->q == 4 || p->q == 16) return launch_fused_samples(p->q, b, s, sx, sy, nsamples, stream);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    switch (b) {
+        case 8: return launch_samples_b<8>(p, s, sx, sy, nsamples, st, flags);
+        case 12: return launch_samples_b<12>(p, s, sx, sy, nsamples, st, flags);
+        case 16: return launch_samples_b<16>(p, s, sx, sy, nsamples, st, flags);
         default: return QEXT_E_UNSUPPORTED;
     }
 }

@@ -20,6 +20,10 @@ struct qext_plan {
     int gpu_supported;   // a kernel exists for this q
 };
 
+namespace qxd {
+struct StreamArgs;
+}
+
 namespace qext {
 
 // Field degrees with a GPU kernel.
@@ -27,7 +31,12 @@ bool gpu_q_supported(uint32_t q);
 
 // Ingest and extraction launchers (defined in the .cu files).
 int launch_extract(const qext_plan *p, const uint32_t *x, const uint32_t *y, uint64_t nblocks, uint32_t *out,
-                   qext_cuda_stream stream);
+                   qext_cuda_stream stream, uint32_t flags);
+int launch_extract_samples(const qext_plan *p, uint32_t b, const uint16_t *sx, const uint16_t *sy,
+                           uint64_t nsamples, uint64_t nblocks, uint32_t *out, qext_cuda_stream stream,
+                           uint32_t flags);
+int launch_fused_samples(uint32_t q, uint32_t b, const qxd::StreamArgs &s, const uint16_t *sx, const uint16_t *sy,
+                         uint64_t nsamples, qext_cuda_stream stream);
 int launch_pack(uint32_t b, const uint16_t *samples, uint64_t nsamples, uint32_t *out, qext_cuda_stream stream);
 int read_device_status(int *status);
 

@@ -24,6 +24,10 @@ QEXT_E_TIMEOUT = -6
 QEXT_E_BUDGET = -7
 QEXT_E_STATE = -8
 QEXT_E_NOSPACE = -9
+QEXT_F_DIRECT = 0x1
+QEXT_F_NBUF1 = 0x2
+QEXT_F_TILE32 = 0x4
+QEXT_F_TILE64 = 0x8
 
 _lib = None
 
@@ -51,9 +55,12 @@ def lib():
     L.qext_plan_info.argtypes = [vp, P(u32), P(u32), P(u32), P(dbl), P(u64), P(i32)]
     L.qext_alg1_params.argtypes = [dbl, u32, dbl, dbl, P(u32), P(u32)]
     L.qext_extract.argtypes = [vp, vp, vp, u64, vp, vp]
+    L.qext_extract_ex.argtypes = [vp, vp, vp, u64, vp, vp, u32]
     L.qext_pack_samples.argtypes = [u32, vp, u64, vp, vp]
+    L.qext_extract_samples.argtypes = [vp, u32, vp, vp, u64, u64, vp, vp]
     L.qext_device_status.argtypes = [P(i32)]
     for name in ["qext_plan_create", "qext_destroy", "qext_plan_info", "qext_alg1_params", "qext_extract",
+                 "qext_extract_ex", "qext_extract_samples",
                  "qext_pack_samples", "qext_device_status"]:
         getattr(L, name).restype = i32
     _lib = L
@@ -139,6 +146,17 @@ def qext_alg1_params(N_samples: float, b: int, delta: float, eps: float):
 def qext_extract(plan: Plan, x, y, nblocks: int, out, stream=None) -> None:
     _check(lib().qext_extract(plan.handle, _ptr(x), _ptr(y), nblocks, _ptr(out), _stream(stream)),
            "qext_extract")
+
+
+def qext_extract_ex(plan: Plan, x, y, nblocks: int, out, stream=None, flags: int = 0) -> None:
+    _check(lib().qext_extract_ex(plan.handle, _ptr(x), _ptr(y), nblocks, _ptr(out), _stream(stream), flags),
+           "qext_extract_ex")
+
+
+def qext_extract_samples(plan: Plan, b: int, x_samples, y_samples, nsamples: int, nblocks: int, out,
+                         stream=None) -> None:
+    _check(lib().qext_extract_samples(plan.handle, b, _ptr(x_samples), _ptr(y_samples), nsamples, nblocks,
+                                      _ptr(out), _stream(stream)), "qext_extract_samples")
 
 
 def qext_pack_samples(b: int, samples, nsamples: int, out, stream=None) -> None:

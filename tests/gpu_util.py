@@ -23,13 +23,13 @@ def host_words(t: torch.Tensor) -> np.ndarray:
     return t.cpu().numpy().view(np.uint32)
 
 
-def gpu_extract(plan, x: np.ndarray, y: np.ndarray, nblocks: int, offset_words: int = 0) -> np.ndarray:
+def gpu_extract(plan, x: np.ndarray, y: np.ndarray, nblocks: int, offset_words: int = 0, flags: int = 0) -> np.ndarray:
     info = plan.info
     nout = -(-nblocks * info["m"] // 32)
     tx = dev_words(x, offset_words=offset_words)
     ty = dev_words(y, offset_words=offset_words)
     out = torch.full((nout + 8,), -1, dtype=torch.int32, device="cuda")  # sentinel past the end
-    qext.qext_extract(plan, tx, ty, nblocks, out)
+    qext.qext_extract_ex(plan, tx, ty, nblocks, out, None, flags)
     torch.cuda.synchronize()
     res = host_words(out)
     assert (res[nout:] == 0xFFFFFFFF).all(), "kernel wrote past the output"
@@ -43,11 +43,15 @@ def oracle_extract(plan, x, y, nblocks):
 
 
 def plan_for(q: int, n_p: int, m: int = 0):
-    """A plan with exactly this (q, n_p) (n_p >= 25): min-entropy n - 1/4 and
-    eps just above Theorem 3.1's bound for q, so every larger q misses eps."""
+    """A plan with exactly this (q, n_p), n_p >= 25.  k = n/2 + 12n/n_p makes
+    Algorithm 1's ceil(24/(2 delta - 1)) equal n_p, so no larger q qualifies;
+    eps is then any value above Theorem 3.1's bound for q."""
     n = q * n_p
-    k = n - 0.25
+    k = n / 2 + 12 * n / n_p
     l2 = oracle.log2_eps_block(n, k, q)
+    if l2 >= math.log2(0.999):
+        k = n - 0.25
+        l2 = oracle.log2_eps_block(n, k, q)
     p = qext.qext_plan_create(n, m, k, min(0.999, 2.0 ** (l2 + 1e-3)))
     assert (p.info["q"], p.info["n_p"]) == (q, n_p), p.info
     return p

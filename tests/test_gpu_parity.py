@@ -28,18 +28,21 @@ CASES = [
     (16, 64, 16, 4133, 0), (16, 64, 13, 1000, 0), (16, 70, 16, 97, 1), (16, 26, 9, 200, 0), (16, 64, 1, 31, 2),
     (32, 64, 32, 500, 0), (32, 33, 17, 65, 1), (32, 25, 32, 40, 0),
     (64, 64, 64, 300, 0), (64, 71, 41, 70, 1), (64, 64, 1, 100, 0), (64, 25, 64, 33, 0), (64, 64, 63, 257, 2),
+    (64, 64, 64, 1000, 0), (16, 64, 16, 20000, 0), (4, 64, 4, 30001, 0),    # many tiles per CTA
+    (16, 800, 16, 70, 0), (64, 200, 64, 40, 0), (8, 1600, 8, 33, 0),        # long blocks: direct fallback
 ]
 
 
+@pytest.mark.parametrize("flags", [0, qext.QEXT_F_DIRECT], ids=["tiled", "direct"])
 @pytest.mark.parametrize("q,n_p,m,nblocks,off", CASES)
-def test_extract_matches_oracle(q, n_p, m, nblocks, off):
+def test_extract_matches_oracle(q, n_p, m, nblocks, off, flags):
     plan = plan_for(q, n_p, m)
     n = q * n_p
     rng = np.random.Generator(np.random.PCG64(q * 1000 + n_p + m))
     words = nblocks * n // 32
     x = workloads.random_words(int(rng.integers(1 << 30)), words)
     y = workloads.random_words(int(rng.integers(1 << 30)), words)
-    got = gpu_extract(plan, x, y, nblocks, offset_words=off)
+    got = gpu_extract(plan, x, y, nblocks, offset_words=off, flags=flags)
     want = oracle_extract(plan, x, y, nblocks)
     assert got.shape == want.shape
     bad = np.nonzero(got != want)[0]
@@ -144,4 +147,68 @@ def test_config_large_single_stream_sampled():
     for l in sample:
         l = int(l)
         z = oracle.extract(16, 64, 16, poly, ox[l * wpb:(l + 1) * wpb], oy[l * wpb:(l + 1) * wpb], 1)
+        assert bits_at(got, l * 16, 16) == int(z[0]), "block %d" % l
+
+
+@pytest.mark.parametrize("q,b,nblocks,extra", [
+    (16, 12, 1000, 0), (16, 12, 4133, 5), (16, 12, 129, 1), (4, 8, 4099, 0), (4, 12, 777, 3), (4, 16, 64, 0),
+    (64, 12, 300, 1), (64, 16, 129, 0), (64, 8, 33, 2), (16, 8, 257, 0), (16, 16, 100, 7), (16, 12, 1, 0),
+])
+def test_extract_samples_matches_oracle(q, b, nblocks, extra):
+    """Fused ingest + extraction from raw b-bit samples (garbage above b) against
+    the oracle's packing followed by its extraction, every output bit."""
+    plan = plan_for(q, 64)
+    n = 64 * q
+    ns = -(-nblocks * n // b) + extra
+    s_x = workloads.adc_samples(q * 10 + b, ns, b, offset_amp=0.05)
+    s_y = workloads.adc_samples(q * 10 + b + 1, ns, b, offset_amp=0.05)
+    junk = np.uint16(0xFFFF ^ ((1 << b) - 1)) if b < 16 else np.uint16(0)
+    gx = torch.from_numpy((s_x | junk).view(np.int16)).cuda()
+    gy = torch.from_numpy((s_y | junk).view(np.int16)).cuda()
+    nout = -(-nblocks * q // 32)
+    out = torch.full((nout + 4,), -1, dtype=torch.int32, device="cuda")
+    qext.qext_extract_samples(plan, b, gx, gy, ns, nblocks, out)
+    torch.cuda.synchronize()
+    got = host_words(out)
+    assert (got[nout:] == 0xFFFFFFFF).all()
+    words = nblocks * n // 32
+    ox = oracle.pack_samples(b, s_x)[:words]
+    oy = oracle.pack_samples(b, s_y)[:words]
+    want = oracle_extract(plan, ox, oy, nblocks)
+    assert (got[:nout] == want).all()
+
+
+def test_extract_samples_rejects_short_input():
+    plan = plan_for(16, 64)
+    with pytest.raises(qext.QextError) as e:
+        qext.qext_extract_samples(plan, 12, 16, 16, 85, 1, 16)   # 85 samples < one 1024-bit block
+    assert e.value.code == qext.QEXT_E_INVAL
+    with pytest.raises(qext.QextError) as e:
+        qext.qext_extract_samples(plan, 10, 16, 16, 1000, 1, 16)
+    assert e.value.code == qext.QEXT_E_UNSUPPORTED
+
+
+def test_config_large_single_stream_fused_sampled():
+    """2^20 blocks x 1024 bits from 12-bit samples through the fused path
+    (the benchmark's launch), checked on sampled blocks against the oracle."""
+    spec = workloads.config_large_single()
+    plan = qext.qext_plan_create(spec.n, 0, spec.k, spec.eps)
+    sx, sy = spec.samples("x"), spec.samples("y")
+    out_words = spec.nblocks * 16 // 32
+    out = torch.full((out_words + 4,), -1, dtype=torch.int32, device="cuda")
+    qext.qext_extract_samples(plan, 12, torch.from_numpy(sx.view(np.int16)).cuda(),
+                              torch.from_numpy(sy.view(np.int16)).cuda(), sx.size, spec.nblocks, out)
+    torch.cuda.synchronize()
+    got = host_words(out)
+    assert (got[out_words:] == 0xFFFFFFFF).all()
+    words = spec.nbits // 32
+    ox = oracle.pack_samples(12, sx)[:words]
+    oy = oracle.pack_samples(12, sy)[:words]
+    rng = np.random.Generator(np.random.PCG64(7))
+    sample = np.unique(np.concatenate([rng.integers(0, spec.nblocks, 3000), np.arange(40),
+                                       np.arange(spec.nblocks - 40, spec.nblocks)]))
+    poly, _ = oracle.select_poly(16)
+    for l in sample:
+        l = int(l)
+        z = oracle.extract(16, 64, 16, poly, ox[l * 32:(l + 1) * 32], oy[l * 32:(l + 1) * 32], 1)
         assert bits_at(got, l * 16, 16) == int(z[0]), "block %d" % l
