@@ -181,6 +181,75 @@ int qext_extract_samples(const qext_plan *p, uint32_t b, const uint16_t *x_sampl
 int qext_pack_samples(uint32_t b, const uint16_t *samples, uint64_t nsamples, uint32_t *out,
                       qext_cuda_stream stream);
 
+/* ------------------------------------------------------------------------
+ * Streams: Algorithm 1 over raw data that arrives in chunks.
+ *
+ * The paper's extractor consumes the two sources strictly in time order,
+ * block l of x pairing with block l of y (Algorithm 1, the window I_l advanced
+ * by one block per step; Algorithm 2 carries the same cursor).  A qext_stream
+ * keeps, on the device, the unconsumed tail of each source (fewer than n
+ * bits) and the output bits not yet forming a whole word (fewer than 32), so
+ * that pushing a stream in pieces of any bit length yields exactly the output
+ * of one push of the whole (its concatenation of Z^(l), Theorem 3.4's
+ * m * floor(L/n) bits).  Not thread-safe; one CUDA stream per qext_stream.
+ * ------------------------------------------------------------------------ */
+typedef struct qext_stream qext_stream; /* opaque, host-owned, holds device memory */
+
+/* Allocates the device state for a plan (which must outlive the stream).
+ * Errors: INVAL, UNSUPPORTED (no GPU kernel for the plan), CUDA. */
+int qext_stream_create(const qext_plan *p, qext_stream **out);
+
+/* Frees the stream (NULL accepted).  Synchronise its CUDA stream first. */
+int qext_stream_destroy(qext_stream *s);
+
+/* Counters (host-side, exact): blocks output so far, tail bits held, output
+ * bits pending.  Any pointer may be NULL. */
+int qext_stream_info(const qext_stream *s, uint64_t *blocks_done, uint64_t *tail_bits, uint32_t *pending_bits);
+
+/*
+ * qext_stream_push -- appends nbits bits of each source and extracts every
+ * block that becomes complete.
+ *   x, y      DEVICE pointers to ceil(nbits/32) words each, 4-byte aligned;
+ *             stream bits [0, nbits) of the chunk (LSB-first), the rest of
+ *             the last word ignored.  16-byte alignment, with no tail or
+ *             pending bits held, takes the in-place TMA-staged kernel.
+ *   out       DEVICE pointer; receives the pending bits followed by the new
+ *             blocks' m-bit outputs.  out_capacity_words must be at least
+ *             ceil((pending + new_blocks*m)/32) (else NOSPACE, nothing done).
+ *   *out_words  complete output words written; the remaining bits (fewer
+ *             than 32) stay pending in the stream (out[*out_words] may have
+ *             been written as well).
+ * Asynchronous on `stream`: the caller's x, y, out must stay valid until it
+ * completes.  Errors: INVAL, NOSPACE, UNSUPPORTED (general path, blocks over
+ * 8192 bits), CUDA.
+ */
+int qext_stream_push(qext_stream *s, const uint32_t *x, const uint32_t *y, uint64_t nbits, uint32_t *out,
+                     uint64_t out_capacity_words, uint64_t *out_words, qext_cuda_stream stream);
+
+/*
+ * qext_stream_flush -- ends the stream: writes the pending output bits (if
+ * any) to out[0] (DEVICE, zero above *out_bits) and drops the incomplete
+ * block (Algorithm 1 outputs whole blocks only).  Counters keep blocks_done.
+ * Errors: INVAL, NOSPACE, CUDA.
+ */
+int qext_stream_flush(qext_stream *s, uint32_t *out, uint64_t out_capacity_words, uint32_t *out_bits,
+                      qext_cuda_stream stream);
+
+/* Bytes qext_stream_save writes for this stream (0 for NULL). */
+size_t qext_stream_state_size(const qext_stream *s);
+
+/*
+ * qext_stream_save / qext_stream_restore -- checkpoint of a stream's state
+ * (counters, tails, pending bits) into a HOST buffer, and a new stream from
+ * one.  Save waits for `stream` (it copies device state to the host).  A
+ * restored stream continues exactly where the saved one stood.  Restore
+ * needs a plan with the same n, m, q, n_p (else STATE).
+ * Errors: INVAL (bad buffer), NOSPACE, STATE, CUDA.
+ */
+int qext_stream_save(const qext_stream *s, void *host_buf, size_t capacity, size_t *size, qext_cuda_stream stream);
+int qext_stream_restore(const qext_plan *p, const void *host_buf, size_t size, qext_stream **out,
+                        qext_cuda_stream stream);
+
 /*
  * qext_device_status -- reads and clears the device status word of the
  * current device (QEXT_OK or QEXT_E_TIMEOUT from a kernel that gave up a

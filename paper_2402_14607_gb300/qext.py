@@ -59,9 +59,20 @@ def lib():
     L.qext_pack_samples.argtypes = [u32, vp, u64, vp, vp]
     L.qext_extract_samples.argtypes = [vp, u32, vp, vp, u64, u64, vp, vp]
     L.qext_device_status.argtypes = [P(i32)]
+    L.qext_stream_create.argtypes = [vp, P(vp)]
+    L.qext_stream_destroy.argtypes = [vp]
+    L.qext_stream_info.argtypes = [vp, P(u64), P(u64), P(u32)]
+    L.qext_stream_push.argtypes = [vp, vp, vp, u64, vp, u64, P(u64), vp]
+    L.qext_stream_flush.argtypes = [vp, vp, u64, P(u32), vp]
+    L.qext_stream_state_size.argtypes = [vp]
+    L.qext_stream_state_size.restype = ctypes.c_size_t
+    L.qext_stream_save.argtypes = [vp, vp, ctypes.c_size_t, P(ctypes.c_size_t), vp]
+    L.qext_stream_restore.argtypes = [vp, vp, ctypes.c_size_t, P(vp), vp]
     for name in ["qext_plan_create", "qext_destroy", "qext_plan_info", "qext_alg1_params", "qext_extract",
                  "qext_extract_ex", "qext_extract_samples",
-                 "qext_pack_samples", "qext_device_status"]:
+                 "qext_pack_samples", "qext_device_status", "qext_stream_create", "qext_stream_destroy",
+                 "qext_stream_info", "qext_stream_push", "qext_stream_flush", "qext_stream_save",
+                 "qext_stream_restore"]:
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -167,3 +178,68 @@ def qext_device_status() -> int:
     st = ctypes.c_int()
     _check(lib().qext_device_status(ctypes.byref(st)), "qext_device_status")
     return st.value
+
+
+class Stream:
+    """Owns a qext_stream handle (the plan must outlive it)."""
+
+    def __init__(self, handle: int, plan: Plan):
+        self.handle = handle
+        self.plan = plan
+
+    def close(self):
+        if self.handle:
+            lib().qext_stream_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def qext_stream_create(plan: Plan) -> Stream:
+    h = ctypes.c_void_p()
+    _check(lib().qext_stream_create(plan.handle, ctypes.byref(h)), "qext_stream_create")
+    return Stream(h.value, plan)
+
+
+def qext_stream_destroy(s: Stream) -> None:
+    s.close()
+
+
+def qext_stream_info(s: Stream):
+    a, b, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint32()
+    _check(lib().qext_stream_info(s.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "qext_stream_info")
+    return dict(blocks_done=a.value, tail_bits=b.value, pending_bits=c.value)
+
+
+def qext_stream_push(s: Stream, x, y, nbits: int, out, out_capacity_words: int, stream=None) -> int:
+    w = ctypes.c_uint64()
+    _check(lib().qext_stream_push(s.handle, _ptr(x), _ptr(y), nbits, _ptr(out), out_capacity_words,
+                                  ctypes.byref(w), _stream(stream)), "qext_stream_push")
+    return w.value
+
+
+def qext_stream_flush(s: Stream, out, out_capacity_words: int, stream=None) -> int:
+    b = ctypes.c_uint32()
+    _check(lib().qext_stream_flush(s.handle, _ptr(out), out_capacity_words, ctypes.byref(b), _stream(stream)),
+           "qext_stream_flush")
+    return b.value
+
+
+def qext_stream_save(s: Stream, stream=None) -> bytes:
+    n = lib().qext_stream_state_size(s.handle)
+    buf = ctypes.create_string_buffer(n)
+    size = ctypes.c_size_t()
+    _check(lib().qext_stream_save(s.handle, buf, n, ctypes.byref(size), _stream(stream)), "qext_stream_save")
+    return buf.raw[: size.value]
+
+
+def qext_stream_restore(plan: Plan, state: bytes, stream=None) -> Stream:
+    h = ctypes.c_void_p()
+    buf = ctypes.create_string_buffer(state, len(state))
+    _check(lib().qext_stream_restore(plan.handle, buf, len(state), ctypes.byref(h), _stream(stream)),
+           "qext_stream_restore")
+    return Stream(h.value, plan)
