@@ -250,6 +250,62 @@ int qext_stream_save(const qext_stream *s, void *host_buf, size_t capacity, size
 int qext_stream_restore(const qext_plan *p, const void *host_buf, size_t size, qext_stream **out,
                         qext_cuda_stream stream);
 
+/* ------------------------------------------------------------------------
+ * Batches: many stream pairs of uneven length and mixed block size in one
+ * persistent kernel launch (blocks are independent, Sec. 3.3, so the blocks
+ * of all streams can share one launch).
+ * ------------------------------------------------------------------------ */
+typedef struct qext_batch_item {
+    const qext_plan *plan; /* this stream's plan (q, n, m); must outlive the batch */
+    const uint32_t *x;     /* DEVICE, nblocks * n bits, 4-byte aligned (16: TMA staging) */
+    const uint32_t *y;     /* DEVICE, same layout as x */
+    uint64_t nblocks;      /* whole blocks of this stream */
+    uint32_t *out;         /* DEVICE, ceil(nblocks*m/32) words, fully written */
+} qext_batch_item;
+
+/* Launch shape of a batch (the autotuner's search space). */
+typedef struct qext_batch_config {
+    uint32_t blocks_per_thread_small; /* q <= 4: 1, 2 or 4 blocks per thread per tile */
+    uint32_t blocks_per_thread_mid;   /* 4 < q <= 16: 1, 2 or 4 */
+    uint32_t ctas_per_sm;             /* 1 .. 3 persistent CTAs per SM */
+    uint32_t order;                   /* 0: tiles by decreasing cost; 1: stream order */
+} qext_batch_config;
+
+typedef struct qext_batch qext_batch; /* opaque, host-owned, holds device memory */
+
+/*
+ * qext_batch_create -- builds the device descriptor and tile tables for the
+ * items (pointers are recorded, not copied: the buffers must stay valid and
+ * may be refilled between runs).  Default configuration; see autotune.
+ * Errors: INVAL (null or misaligned pointers), UNSUPPORTED (a plan without a
+ * GPU kernel, or blocks over 8192 bits), CUDA.
+ */
+int qext_batch_create(const qext_batch_item *items, uint32_t nitems, qext_batch **out);
+int qext_batch_destroy(qext_batch *b);
+
+/* Current configuration and tile count (either pointer may be NULL). */
+int qext_batch_get_config(const qext_batch *b, qext_batch_config *cfg, uint32_t *ntiles);
+/* Rebuilds the tile table for cfg (drops a captured graph).  Errors: INVAL. */
+int qext_batch_set_config(qext_batch *b, const qext_batch_config *cfg);
+
+/* One run: a memset of the tile counter and ONE kernel launch on `stream`,
+ * every item's output written.  Asynchronous.  Errors: INVAL, CUDA. */
+int qext_batch_run(qext_batch *b, qext_cuda_stream stream);
+
+/* Records one run into a CUDA graph (capture on `stream`, which must not be
+ * capturing already); qext_batch_launch replays it.  Errors: STATE (launch
+ * before capture), CUDA. */
+int qext_batch_capture(qext_batch *b, qext_cuda_stream stream);
+int qext_batch_launch(qext_batch *b, qext_cuda_stream stream);
+
+/*
+ * qext_batch_autotune -- times every configuration (tile shape for q <= 4 and
+ * q <= 16, CTAs per SM, tile order) on this batch's own data, `reps` runs
+ * each after a warm-up, keeps the fastest, and reports its time per run.
+ * Synchronises `stream`.  The outputs are those of a normal run.
+ */
+int qext_batch_autotune(qext_batch *b, uint32_t reps, qext_cuda_stream stream, float *best_ms);
+
 /*
  * qext_device_status -- reads and clears the device status word of the
  * current device (QEXT_OK or QEXT_E_TIMEOUT from a kernel that gave up a

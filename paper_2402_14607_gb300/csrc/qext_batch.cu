@@ -1,0 +1,422 @@
+// Batched extraction: many stream pairs of uneven length and mixed block size
+// (q = n/n_p in {1, 2, 4, 8, 16, 32, 64}) in ONE persistent kernel launch.
+//
+// Each stream's blocks are cut into tiles (T blocks; for q <= 16, T = 128 *
+// blocks-per-thread).  The tiles of all streams form a table on the device,
+// sorted by estimated cost, largest first; persistent CTAs take tiles from an
+// atomic counter (reset by a memset node before the kernel), so long q = 64
+// tiles start early and short tiles fill the end.  A tile arrives in shared
+// memory by two TMA bulk copies (mbarrier, bounded wait) when its stream is
+// 16-byte aligned, else by plain loads; threads compute blocks (Ext_IP,
+// Definition 3.2) exactly as the single-stream kernel does and warps assemble
+// the m-bit outputs of 32 consecutive blocks.
+//
+// Tile shape (blocks per thread for q = 4 and q = 16) and CTAs per SM are the
+// tunables; qext_batch_autotune times the candidates on the batch itself.
+// qext_batch_capture records memset + kernel into a CUDA graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "qext_block.cuh"
+#include "qext_internal.h"
+
+using namespace qxd;
+
+namespace {
+
+constexpr int kThreads = 128;
+constexpr int kSmemBytes = 64 * 1024;  // one tile buffer (x and y)
+
+struct BatchStreamDev {
+    StreamArgs s;
+    uint32_t q;
+    uint32_t tma;  // x, y 16-byte aligned
+};
+
+struct BatchTileDev {
+    uint32_t item;
+    uint32_t nb;     // blocks in the tile
+    uint64_t first;  // first block
+};
+
+__device__ __forceinline__ void load_tile(const StreamArgs &s, uint64_t first, uint32_t nb, int tma, uint32_t *xs,
+                                          uint32_t *ys, uint64_t *bar, uint32_t &uses, bool &ok) {
+    const uint32_t words = nb * s.wpb;
+    const uint32_t tid = threadIdx.x;
+    if (tma && (words % 4u) == 0) {
+        if (tid == 0) {
+            mbar_expect_tx(bar, 8u * words);
+            tma_load_1d(xs, s.x + first * s.wpb, 4u * words, bar);
+            tma_load_1d(ys, s.y + first * s.wpb, 4u * words, bar);
+        }
+        ok = mbar_wait_bounded(bar, uses & 1u);
+        ++uses;
+    } else {
+        for (uint32_t i = tid; i < words; i += blockDim.x) {
+            xs[i] = __ldg(s.x + first * s.wpb + i);
+            ys[i] = __ldg(s.y + first * s.wpb + i);
+        }
+        ok = true;
+    }
+}
+
+template <int Q>
+__device__ __forceinline__ void compute_tile(const StreamArgs &s, uint64_t first, uint32_t nb, const uint32_t *xs,
+                                             const uint32_t *ys, uint64_t *vals, const ShiftMuls &mu) {
+    const uint32_t tid = threadIdx.x;
+    if constexpr (Q == 64) {
+        // two threads per block, 64 blocks per pass
+        for (uint32_t base = 0; base < nb; base += kThreads / 2) {
+            const uint32_t lb = base + tid / 2, part = tid & 1u;
+            uint64_t A = 0, B = 0, C = 0;
+            if (lb < nb) {
+                const uint32_t *xb = xs + lb * s.wpb, *yb = ys + lb * s.wpb;
+                const int vec = s.wpb % 4 == 0;
+                A = half_product64<0>(xb, yb, s.wpb, vec, tid, part, 2, mu);
+                B = half_product64<1>(xb, yb, s.wpb, vec, tid, part, 2, mu);
+                C = half_product64<2>(xb, yb, s.wpb, vec, tid, part, 2, mu);
+            }
+            A ^= __shfl_xor_sync(0xffffffffu, A, 1);
+            B ^= __shfl_xor_sync(0xffffffffu, B, 1);
+            C ^= __shfl_xor_sync(0xffffffffu, C, 1);
+            if (lb < nb && part == 0) vals[lb] = combine_q64(A, B, C, s) & mask_m(s.m);
+        }
+    } else {
+        for (uint32_t lb = tid; lb < nb; lb += kThreads)
+            vals[lb] = block_small_q<Q>(xs + lb * s.wpb, ys + lb * s.wpb, s.wpb, s.wpb % 4 == 0, tid, mu, s) &
+                       mask_m(s.m);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) batch_kernel(const BatchStreamDev *__restrict__ items,
+                                                         const BatchTileDev *__restrict__ tiles, uint32_t ntiles,
+                                                         uint32_t *counter, const ShiftMuls mu) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t next_tile;
+    __shared__ uint64_t vals[512];
+    const uint32_t tid = threadIdx.x;
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    uint32_t uses = 0;
+    for (;;) {
+        if (tid == 0) next_tile = atomicAdd(counter, 1u);
+        __syncthreads();
+        const uint32_t t = next_tile;
+        if (t >= ntiles) return;
+        const BatchTileDev tl = tiles[t];
+        const BatchStreamDev it = items[tl.item];
+        const StreamArgs &s = it.s;
+        const uint32_t words = tl.nb * s.wpb;
+        uint32_t *xs = smem, *ys = smem + words;
+        bool ok;
+        load_tile(s, tl.first, tl.nb, it.tma, xs, ys, &bar, uses, ok);
+        if (!__syncthreads_and(ok)) {
+            if (tid == 0) {
+                record_status(QEXT_E_TIMEOUT);
+                mbar_wait_bounded(&bar, (uses - 1) & 1u);
+            }
+            return;
+        }
+        for (uint32_t i = tid; i < ((tl.nb + 31u) & ~31u); i += kThreads) vals[i] = 0;
+        __syncthreads();
+        switch (it.q) {
+            case 1: compute_tile<1>(s, tl.first, tl.nb, xs, ys, vals, mu); break;
+            case 2: compute_tile<2>(s, tl.first, tl.nb, xs, ys, vals, mu); break;
+            case 4: compute_tile<4>(s, tl.first, tl.nb, xs, ys, vals, mu); break;
+            case 8: compute_tile<8>(s, tl.first, tl.nb, xs, ys, vals, mu); break;
+            case 16: compute_tile<16>(s, tl.first, tl.nb, xs, ys, vals, mu); break;
+            case 32: compute_tile<32>(s, tl.first, tl.nb, xs, ys, vals, mu); break;
+            default: compute_tile<64>(s, tl.first, tl.nb, xs, ys, vals, mu); break;
+        }
+        __syncthreads();
+        // warps assemble 32 consecutive blocks at a time (tiles start at
+        // multiples of 32 blocks within their stream)
+        for (uint32_t g = tid >> 5; g * 32 < tl.nb; g += kThreads / 32)
+            store_warp(vals[32 * g + (tid & 31u)], tl.first + 32 * g, s.nblocks, s.m, s.out);
+        __syncthreads();
+    }
+}
+
+// relative cost of one block (ALU work), for ordering tiles
+double block_cost(uint32_t q, uint32_t wpb) {
+    const double per_word = q <= 4 ? 4.0 : q <= 16 ? 14.0 : q <= 32 ? 30.0 : 64.0;
+    return per_word * wpb;
+}
+
+}  // namespace
+
+struct qext_batch {
+    std::vector<BatchStreamDev> items;
+    std::vector<uint64_t> nblocks;
+    qext_batch_config cfg;
+    BatchStreamDev *d_items = nullptr;
+    BatchTileDev *d_tiles = nullptr;
+    uint32_t *d_counter = nullptr;
+    uint32_t ntiles = 0;
+    size_t tiles_cap = 0;
+    int sms = 0;
+    cudaGraphExec_t graph = nullptr;
+    cudaGraph_t graph_def = nullptr;
+};
+
+namespace {
+
+uint32_t tile_blocks(const qext_batch_config &c, uint32_t q, uint32_t wpb) {
+    uint32_t T;
+    if (q == 64)
+        T = 64;
+    else if (q == 32)
+        T = 128;
+    else if (q <= 4)
+        T = 128 * c.blocks_per_thread_small;
+    else
+        T = 128 * c.blocks_per_thread_mid;
+    // one tile (x and y) must fit the shared-memory buffer; keep T a multiple of 32
+    while (T > 32 && uint64_t(T) * wpb * 8 > uint64_t(kSmemBytes)) T /= 2;
+    if (T > 512) T = 512;
+    return T;
+}
+
+int build_tiles(qext_batch *b) {
+    struct HostTile {
+        BatchTileDev t;
+        double cost;
+    };
+    std::vector<HostTile> tiles;
+    for (uint32_t i = 0; i < b->items.size(); ++i) {
+        const BatchStreamDev &it = b->items[i];
+        const uint32_t T = tile_blocks(b->cfg, it.q, it.s.wpb);
+        if (uint64_t(T) * it.s.wpb * 8 > uint64_t(kSmemBytes)) return QEXT_E_UNSUPPORTED;
+        for (uint64_t f = 0; f < it.s.nblocks; f += T) {
+            HostTile h;
+            h.t.item = i;
+            h.t.first = f;
+            h.t.nb = uint32_t(std::min<uint64_t>(T, it.s.nblocks - f));
+            h.cost = h.t.nb * block_cost(it.q, it.s.wpb);
+            tiles.push_back(h);
+        }
+    }
+    if (b->cfg.order == 0)
+        std::stable_sort(tiles.begin(), tiles.end(), [](const HostTile &a, const HostTile &c) { return a.cost > c.cost; });
+    if (tiles.size() > 0xFFFFFFFFull) return QEXT_E_INVAL;
+    b->ntiles = uint32_t(tiles.size());
+    if (b->ntiles > b->tiles_cap) {
+        cudaFree(b->d_tiles);
+        b->d_tiles = nullptr;
+        if (cudaMalloc(&b->d_tiles, sizeof(BatchTileDev) * b->ntiles) != cudaSuccess) return QEXT_E_CUDA;
+        b->tiles_cap = b->ntiles;
+    }
+    std::vector<BatchTileDev> flat(b->ntiles);
+    for (uint32_t i = 0; i < b->ntiles; ++i) flat[i] = tiles[i].t;
+    if (b->ntiles && cudaMemcpy(b->d_tiles, flat.data(), sizeof(BatchTileDev) * b->ntiles,
+                                cudaMemcpyHostToDevice) != cudaSuccess)
+        return QEXT_E_CUDA;
+    return QEXT_OK;
+}
+
+int enqueue(qext_batch *b, cudaStream_t st) {
+    if (cudaMemsetAsync(b->d_counter, 0, sizeof(uint32_t), st) != cudaSuccess) return QEXT_E_CUDA;
+    if (!b->ntiles) return QEXT_OK;
+    const uint64_t cap = uint64_t(b->sms) * b->cfg.ctas_per_sm;
+    const int grid = int(std::min<uint64_t>(cap, b->ntiles));
+    batch_kernel<<<grid, kThreads, kSmemBytes, st>>>(b->d_items, b->d_tiles, b->ntiles, b->d_counter,
+                                                     make_shift_muls());
+    return cudaGetLastError() == cudaSuccess ? QEXT_OK : QEXT_E_CUDA;
+}
+
+void drop_graph(qext_batch *b) {
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->graph_def) cudaGraphDestroy(b->graph_def);
+    b->graph = nullptr;
+    b->graph_def = nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+int qext_batch_create(const qext_batch_item *items, uint32_t nitems, qext_batch **out) {
+    if (!out || (nitems && !items)) return QEXT_E_INVAL;
+    *out = nullptr;
+    static bool attr = false;
+    if (!attr) {
+        if (cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) !=
+            cudaSuccess)
+            return QEXT_E_CUDA;
+        attr = true;
+    }
+    qext_batch *b = new (std::nothrow) qext_batch();
+    if (!b) return QEXT_E_INVAL;
+    b->cfg.blocks_per_thread_small = 4;
+    b->cfg.blocks_per_thread_mid = 1;
+    b->cfg.ctas_per_sm = 3;
+    b->cfg.order = 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess) {
+        delete b;
+        return QEXT_E_CUDA;
+    }
+    for (uint32_t i = 0; i < nitems; ++i) {
+        const qext_batch_item &it = items[i];
+        if (!it.plan) {
+            qext_batch_destroy(b);
+            return QEXT_E_INVAL;
+        }
+        if (!it.plan->gpu_supported) {
+            qext_batch_destroy(b);
+            return QEXT_E_UNSUPPORTED;
+        }
+        const uintptr_t al = reinterpret_cast<uintptr_t>(it.x) | reinterpret_cast<uintptr_t>(it.y);
+        if (it.nblocks && (!it.x || !it.y || !it.out || al % 4 || reinterpret_cast<uintptr_t>(it.out) % 4)) {
+            qext_batch_destroy(b);
+            return QEXT_E_INVAL;
+        }
+        BatchStreamDev d;
+        std::memset(&d, 0, sizeof d);
+        d.s.x = it.x;
+        d.s.y = it.y;
+        d.s.out = it.out;
+        d.s.nblocks = it.nblocks;
+        d.s.wpb = it.plan->n / 32;
+        d.s.m = it.plan->m;
+        d.s.ntaps = it.plan->ntaps;
+        for (int k = 0; k < 4; ++k) {
+            d.s.taps[k] = it.plan->taps[k];
+            d.s.tap_mul[k] = k < int(it.plan->ntaps) ? 1u << (it.plan->taps[k] & 31u) : 0u;
+        }
+        d.q = it.plan->q;
+        d.tma = al % 16 == 0;
+        b->items.push_back(d);
+    }
+    if (cudaMalloc(&b->d_counter, sizeof(uint32_t)) != cudaSuccess ||
+        (nitems && cudaMalloc(&b->d_items, sizeof(BatchStreamDev) * nitems) != cudaSuccess)) {
+        qext_batch_destroy(b);
+        return QEXT_E_CUDA;
+    }
+    if (nitems &&
+        cudaMemcpy(b->d_items, b->items.data(), sizeof(BatchStreamDev) * nitems, cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
+        qext_batch_destroy(b);
+        return QEXT_E_CUDA;
+    }
+    const int rc = build_tiles(b);
+    if (rc != QEXT_OK) {
+        qext_batch_destroy(b);
+        return rc;
+    }
+    *out = b;
+    return QEXT_OK;
+}
+
+int qext_batch_destroy(qext_batch *b) {
+    if (!b) return QEXT_OK;
+    drop_graph(b);
+    cudaFree(b->d_items);
+    cudaFree(b->d_tiles);
+    cudaFree(b->d_counter);
+    delete b;
+    return QEXT_OK;
+}
+
+int qext_batch_get_config(const qext_batch *b, qext_batch_config *cfg, uint32_t *ntiles) {
+    if (!b) return QEXT_E_INVAL;
+    if (cfg) *cfg = b->cfg;
+    if (ntiles) *ntiles = b->ntiles;
+    return QEXT_OK;
+}
+
+int qext_batch_set_config(qext_batch *b, const qext_batch_config *cfg) {
+    if (!b || !cfg) return QEXT_E_INVAL;
+    const qext_batch_config &c = *cfg;
+    const bool ok = (c.blocks_per_thread_small == 1 || c.blocks_per_thread_small == 2 ||
+                     c.blocks_per_thread_small == 4) &&
+                    (c.blocks_per_thread_mid == 1 || c.blocks_per_thread_mid == 2 ||
+                     c.blocks_per_thread_mid == 4) &&
+                    c.ctas_per_sm >= 1 && c.ctas_per_sm <= 3 && c.order <= 1;
+    if (!ok) return QEXT_E_INVAL;
+    b->cfg = c;
+    drop_graph(b);
+    return build_tiles(b);
+}
+
+int qext_batch_run(qext_batch *b, qext_cuda_stream stream) {
+    if (!b) return QEXT_E_INVAL;
+    return enqueue(b, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int qext_batch_capture(qext_batch *b, qext_cuda_stream stream) {
+    if (!b) return QEXT_E_INVAL;
+    drop_graph(b);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return QEXT_E_CUDA;
+    const int rc = enqueue(b, st);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(st, &g);
+    if (rc != QEXT_OK || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return rc != QEXT_OK ? rc : QEXT_E_CUDA;
+    }
+    if (cudaGraphInstantiate(&b->graph, g, 0) != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return QEXT_E_CUDA;
+    }
+    b->graph_def = g;
+    return QEXT_OK;
+}
+
+int qext_batch_launch(qext_batch *b, qext_cuda_stream stream) {
+    if (!b) return QEXT_E_INVAL;
+    if (!b->graph) return QEXT_E_STATE;
+    return cudaGraphLaunch(b->graph, reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess ? QEXT_OK : QEXT_E_CUDA;
+}
+
+int qext_batch_autotune(qext_batch *b, uint32_t reps, qext_cuda_stream stream, float *best_ms) {
+    if (!b || reps == 0) return QEXT_E_INVAL;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return QEXT_E_CUDA;
+    qext_batch_config best = b->cfg;
+    float best_t = 1e30f;
+    int rc = QEXT_OK;
+    for (uint32_t small : {1u, 2u, 4u})
+        for (uint32_t mid : {1u, 2u})
+            for (uint32_t ctas : {2u, 3u})
+                for (uint32_t order : {0u, 1u}) {
+                    qext_batch_config c{small, mid, ctas, order};
+                    if ((rc = qext_batch_set_config(b, &c)) != QEXT_OK) goto done;
+                    if ((rc = enqueue(b, st)) != QEXT_OK) goto done;  // warm-up
+                    cudaEventRecord(e0, st);
+                    for (uint32_t r = 0; r < reps; ++r)
+                        if ((rc = enqueue(b, st)) != QEXT_OK) goto done;
+                    cudaEventRecord(e1, st);
+                    if (cudaEventSynchronize(e1) != cudaSuccess) {
+                        rc = QEXT_E_CUDA;
+                        goto done;
+                    }
+                    float ms = 0;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    ms /= float(reps);
+                    if (ms < best_t) {
+                        best_t = ms;
+                        best = c;
+                    }
+                }
+    rc = qext_batch_set_config(b, &best);
+    if (best_ms) *best_ms = best_t;
+done:
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
+}
+
+}  // extern "C"

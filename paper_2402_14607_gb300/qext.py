@@ -32,6 +32,16 @@ QEXT_F_TILE64 = 0x8
 _lib = None
 
 
+class BatchItem(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p),
+                ("nblocks", ctypes.c_uint64), ("out", ctypes.c_void_p)]
+
+
+class BatchConfig(ctypes.Structure):
+    _fields_ = [("blocks_per_thread_small", ctypes.c_uint32), ("blocks_per_thread_mid", ctypes.c_uint32),
+                ("ctas_per_sm", ctypes.c_uint32), ("order", ctypes.c_uint32)]
+
+
 class QextError(RuntimeError):
     def __init__(self, code: int, where: str = ""):
         self.code = code
@@ -68,11 +78,21 @@ def lib():
     L.qext_stream_state_size.restype = ctypes.c_size_t
     L.qext_stream_save.argtypes = [vp, vp, ctypes.c_size_t, P(ctypes.c_size_t), vp]
     L.qext_stream_restore.argtypes = [vp, vp, ctypes.c_size_t, P(vp), vp]
+    L.qext_batch_create.argtypes = [vp, u32, P(vp)]
+    L.qext_batch_destroy.argtypes = [vp]
+    L.qext_batch_get_config.argtypes = [vp, P(BatchConfig), P(u32)]
+    L.qext_batch_set_config.argtypes = [vp, P(BatchConfig)]
+    L.qext_batch_run.argtypes = [vp, vp]
+    L.qext_batch_capture.argtypes = [vp, vp]
+    L.qext_batch_launch.argtypes = [vp, vp]
+    L.qext_batch_autotune.argtypes = [vp, u32, vp, P(ctypes.c_float)]
     for name in ["qext_plan_create", "qext_destroy", "qext_plan_info", "qext_alg1_params", "qext_extract",
                  "qext_extract_ex", "qext_extract_samples",
                  "qext_pack_samples", "qext_device_status", "qext_stream_create", "qext_stream_destroy",
                  "qext_stream_info", "qext_stream_push", "qext_stream_flush", "qext_stream_save",
-                 "qext_stream_restore"]:
+                 "qext_stream_restore", "qext_batch_create", "qext_batch_destroy", "qext_batch_get_config",
+                 "qext_batch_set_config", "qext_batch_run", "qext_batch_capture", "qext_batch_launch",
+                 "qext_batch_autotune"]:
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -243,3 +263,68 @@ def qext_stream_restore(plan: Plan, state: bytes, stream=None) -> Stream:
     _check(lib().qext_stream_restore(plan.handle, buf, len(state), ctypes.byref(h), _stream(stream)),
            "qext_stream_restore")
     return Stream(h.value, plan)
+
+
+class Batch:
+    """Owns a qext_batch handle; keeps the plans (and buffers) alive."""
+
+    def __init__(self, handle: int, keep):
+        self.handle = handle
+        self._keep = keep
+
+    def close(self):
+        if self.handle:
+            lib().qext_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def qext_batch_create(items) -> Batch:
+    """items: sequence of (plan, x, y, nblocks, out)."""
+    arr = (BatchItem * max(1, len(items)))()
+    for i, (plan, x, y, nb, out) in enumerate(items):
+        arr[i] = BatchItem(plan.handle, _ptr(x), _ptr(y), nb, _ptr(out))
+    h = ctypes.c_void_p()
+    _check(lib().qext_batch_create(arr, len(items), ctypes.byref(h)), "qext_batch_create")
+    return Batch(h.value, [it for it in items])
+
+
+def qext_batch_destroy(b: Batch) -> None:
+    b.close()
+
+
+def qext_batch_get_config(b: Batch):
+    c = BatchConfig()
+    nt = ctypes.c_uint32()
+    _check(lib().qext_batch_get_config(b.handle, ctypes.byref(c), ctypes.byref(nt)), "qext_batch_get_config")
+    return dict(blocks_per_thread_small=c.blocks_per_thread_small, blocks_per_thread_mid=c.blocks_per_thread_mid,
+                ctas_per_sm=c.ctas_per_sm, order=c.order, ntiles=nt.value)
+
+
+def qext_batch_set_config(b: Batch, blocks_per_thread_small=4, blocks_per_thread_mid=1, ctas_per_sm=3,
+                          order=0) -> None:
+    c = BatchConfig(blocks_per_thread_small, blocks_per_thread_mid, ctas_per_sm, order)
+    _check(lib().qext_batch_set_config(b.handle, ctypes.byref(c)), "qext_batch_set_config")
+
+
+def qext_batch_run(b: Batch, stream=None) -> None:
+    _check(lib().qext_batch_run(b.handle, _stream(stream)), "qext_batch_run")
+
+
+def qext_batch_capture(b: Batch, stream=None) -> None:
+    _check(lib().qext_batch_capture(b.handle, _stream(stream)), "qext_batch_capture")
+
+
+def qext_batch_launch(b: Batch, stream=None) -> None:
+    _check(lib().qext_batch_launch(b.handle, _stream(stream)), "qext_batch_launch")
+
+
+def qext_batch_autotune(b: Batch, reps: int = 3, stream=None) -> float:
+    ms = ctypes.c_float()
+    _check(lib().qext_batch_autotune(b.handle, reps, _stream(stream), ctypes.byref(ms)), "qext_batch_autotune")
+    return ms.value

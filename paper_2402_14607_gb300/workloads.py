@@ -109,6 +109,9 @@ class StreamSpec:
 # the blocks of a stream by Theorem 3.3's sum; 256-bit blocks cannot reach
 # that and use 2^-9 per block (a parity / latency workload).
 EPS_BLOCK = {256: 2.0 ** -9, 1024: 2.0 ** -50, 4096: 2.0 ** -52}
+# Mixed 8/12-bit workloads: 1024-bit blocks of 8-bit samples carry k = 809,
+# whose q = 16 bound is 2^-41.7 per block; 2^-40 keeps q = n/64 for both b.
+EPS_BLOCK_MIXED = {256: 2.0 ** -9, 1024: 2.0 ** -40, 4096: 2.0 ** -52}
 
 
 def config_plain_small() -> StreamSpec:
@@ -132,7 +135,7 @@ def config_batched(master_seed: int = 3, nstreams: int = 64, lo: int = 12, hi: i
         u = int(round(rng.uniform(lo, hi)))
         n = int(rng.choice([256, 1024, 4096]))
         b = int(rng.choice([8, 12]))
-        specs.append(StreamSpec(n=n, nblocks=1 << u, b=b, seed_x=2 * s, seed_y=2 * s + 1, eps=EPS_BLOCK[n]))
+        specs.append(StreamSpec(n=n, nblocks=1 << u, b=b, seed_x=2 * s, seed_y=2 * s + 1, eps=EPS_BLOCK_MIXED[n]))
     return specs
 
 
