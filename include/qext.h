@@ -56,6 +56,7 @@ typedef struct CUstream_st *qext_cuda_stream;
 #define QEXT_E_BUDGET (-7)      /* device-memory budget exhausted (admission)         */
 #define QEXT_E_STATE (-8)       /* object used in a state that forbids the call       */
 #define QEXT_E_NOSPACE (-9)     /* caller's output buffer too small                   */
+#define QEXT_E_LIMIT (-10)      /* request exceeds a fixed capacity of the call       */
 
 /* Human-readable name of a status code (static string, never NULL). */
 const char *qext_status_string(int status);
@@ -305,6 +306,31 @@ int qext_batch_launch(qext_batch *b, qext_cuda_stream stream);
  * Synchronises `stream`.  The outputs are those of a normal run.
  */
 int qext_batch_autotune(qext_batch *b, uint32_t reps, qext_cuda_stream stream, float *best_ms);
+
+/*
+ * qext_batch_run_noalloc -- the same outputs as qext_batch_create +
+ * qext_batch_run on these items, for callers that cannot allocate device
+ * memory: code that owns a fixed device-memory budget set at start-up (an
+ * appliance or server whose admission control counts every byte), and code
+ * in a latency-critical loop where cudaMalloc / cudaFree would synchronise
+ * the device.  Nothing is allocated: the descriptors and the tile counter live
+ * in one static device array of the library (about 100 KB, present on every
+ * device that loads the library until the process exits).  The paper has no
+ * counterpart; this is a calling convention, not part of the method.
+ *   items, nitems  as for qext_batch_create; at most QEXT_NOALLOC_MAX_ITEMS
+ *                  items (else QEXT_E_LIMIT, nothing done).
+ * The first call on a device, with that device current, looks up the array's
+ * device address and sets the kernel's shared-memory limit; make that first
+ * call before any stream capture.  Every call reuses the same array: it is
+ * rewritten (counter reset to 0) by each call, so calls whose work overlaps
+ * on the GPU -- on different streams, or from different host threads without
+ * ordering -- race and give wrong outputs; order them on one stream.  The
+ * descriptor copy is staged from host memory before the call returns.
+ * Default tile configuration (no autotuning).  Errors: INVAL, UNSUPPORTED,
+ * LIMIT, CUDA.
+ */
+#define QEXT_NOALLOC_MAX_ITEMS 1024
+int qext_batch_run_noalloc(const qext_batch_item *items, uint32_t nitems, qext_cuda_stream stream);
 
 /*
  * qext_device_status -- reads and clears the device status word of the

@@ -17,8 +17,10 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstddef>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -420,3 +422,164 @@ done:
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free batch run (qext_batch_run_noalloc).  Same per-tile work as
+// batch_kernel, but the descriptors and the tile counter live in a fixed
+// static device array instead of cudaMalloc'ed tables, and tiles are found
+// from per-stream tile prefix counts rather than a tile table.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct NoallocScratch {
+    uint32_t counter;  // next tile; 0 at the start of every call
+    uint32_t nitems;
+    uint64_t total_tiles;
+    uint64_t tile_prefix[QEXT_NOALLOC_MAX_ITEMS + 1];  // tiles of the items before item i
+    uint32_t tile_blocks[QEXT_NOALLOC_MAX_ITEMS];
+    BatchStreamDev items[QEXT_NOALLOC_MAX_ITEMS];
+};
+
+// Scratch of the allocation-free entry point: one per device, held until the
+// process exits, shared by every call (see qext_batch_run_noalloc).
+static __device__ __align__(256) unsigned char qext_noalloc_scratch[sizeof(NoallocScratch)];
+
+__global__ void __launch_bounds__(kThreads) batch_noalloc_kernel(NoallocScratch *sc, const ShiftMuls mu) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t next_tile;
+    __shared__ uint64_t vals[512];
+    const uint32_t tid = threadIdx.x;
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    uint32_t uses = 0;
+    for (;;) {
+        if (tid == 0) next_tile = atomicAdd(&sc->counter, 1u);
+        __syncthreads();
+        const uint64_t t = next_tile;
+        if (t >= sc->total_tiles) return;
+        uint32_t lo = 0, hi = sc->nitems;  // last item whose prefix <= t
+        while (lo + 1 < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (sc->tile_prefix[mid] <= t)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        const BatchStreamDev it = sc->items[lo];
+        const StreamArgs &s = it.s;
+        const uint32_t T = sc->tile_blocks[lo];
+        const uint64_t first = (t - sc->tile_prefix[lo]) * T;
+        const uint32_t nb = uint32_t(s.nblocks - first < T ? s.nblocks - first : T);
+        const uint32_t words = nb * s.wpb;
+        uint32_t *xs = smem, *ys = smem + words;
+        bool ok;
+        load_tile(s, first, nb, it.tma, xs, ys, &bar, uses, ok);
+        if (!__syncthreads_and(ok)) {
+            if (tid == 0) {
+                record_status(QEXT_E_TIMEOUT);
+                mbar_wait_bounded(&bar, (uses - 1) & 1u);
+            }
+            return;
+        }
+        for (uint32_t i = tid; i < ((nb + 31u) & ~31u); i += kThreads) vals[i] = 0;
+        __syncthreads();
+        switch (it.q) {
+            case 1: compute_tile<1>(s, first, nb, xs, ys, vals, mu); break;
+            case 2: compute_tile<2>(s, first, nb, xs, ys, vals, mu); break;
+            case 4: compute_tile<4>(s, first, nb, xs, ys, vals, mu); break;
+            case 8: compute_tile<8>(s, first, nb, xs, ys, vals, mu); break;
+            case 16: compute_tile<16>(s, first, nb, xs, ys, vals, mu); break;
+            case 32: compute_tile<32>(s, first, nb, xs, ys, vals, mu); break;
+            default: compute_tile<64>(s, first, nb, xs, ys, vals, mu); break;
+        }
+        __syncthreads();
+        for (uint32_t g = tid >> 5; g * 32 < nb; g += kThreads / 32)
+            store_warp(vals[32 * g + (tid & 31u)], first + 32 * g, s.nblocks, s.m, s.out);
+        __syncthreads();
+    }
+}
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_dev[kNoallocMaxDevices];                 // device address of the scratch, per device
+unsigned char g_noalloc_stage[sizeof(NoallocScratch)];  // host staging (static: no heap)
+
+}  // namespace
+
+extern "C" int qext_batch_run_noalloc(const qext_batch_item *items, uint32_t nitems, qext_cuda_stream stream) {
+    if (nitems > QEXT_NOALLOC_MAX_ITEMS) return QEXT_E_LIMIT;
+    if (nitems && !items) return QEXT_E_INVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return QEXT_E_CUDA;
+    if (dev < 0 || dev >= kNoallocMaxDevices) return QEXT_E_LIMIT;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    // one-time set-up on this device (the first call, with the device current)
+    if (!g_noalloc_dev[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, qext_noalloc_scratch) != cudaSuccess || !p) return QEXT_E_CUDA;
+        if (cudaFuncSetAttribute(batch_noalloc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) !=
+            cudaSuccess)
+            return QEXT_E_CUDA;
+        g_noalloc_dev[dev] = p;
+    }
+    NoallocScratch *h = reinterpret_cast<NoallocScratch *>(g_noalloc_stage);
+    h->counter = 0;
+    h->nitems = nitems;
+    for (uint32_t i = 0; i < nitems; ++i)
+        if (!items[i].plan) return QEXT_E_INVAL;
+    // heavier streams first, so their tiles are taken first
+    uint32_t order[QEXT_NOALLOC_MAX_ITEMS];
+    for (uint32_t i = 0; i < nitems; ++i) order[i] = i;
+    std::stable_sort(order, order + nitems,
+                     [&](uint32_t a, uint32_t c) { return items[a].plan->q > items[c].plan->q; });
+    qext_batch_config cfg{4, 1, 3, 0};
+    uint64_t tiles = 0;
+    for (uint32_t k = 0; k < nitems; ++k) {
+        const qext_batch_item &it = items[order[k]];
+        if (!it.plan->gpu_supported) return QEXT_E_UNSUPPORTED;
+        const uintptr_t al = reinterpret_cast<uintptr_t>(it.x) | reinterpret_cast<uintptr_t>(it.y);
+        if (it.nblocks && (!it.x || !it.y || !it.out || al % 4 || reinterpret_cast<uintptr_t>(it.out) % 4))
+            return QEXT_E_INVAL;
+        BatchStreamDev &d = h->items[k];
+        std::memset(&d, 0, sizeof d);
+        d.s.x = it.x;
+        d.s.y = it.y;
+        d.s.out = it.out;
+        d.s.nblocks = it.nblocks;
+        d.s.wpb = it.plan->n / 32;
+        d.s.m = it.plan->m;
+        d.s.ntaps = it.plan->ntaps;
+        for (int j = 0; j < 4; ++j) {
+            d.s.taps[j] = it.plan->taps[j];
+            d.s.tap_mul[j] = j < int(it.plan->ntaps) ? 1u << (it.plan->taps[j] & 31u) : 0u;
+        }
+        d.q = it.plan->q;
+        d.tma = al % 16 == 0;
+        const uint32_t T = tile_blocks(cfg, d.q, d.s.wpb);
+        if (uint64_t(T) * d.s.wpb * 8 > uint64_t(kSmemBytes)) return QEXT_E_UNSUPPORTED;
+        h->tile_blocks[k] = T;
+        h->tile_prefix[k] = tiles;
+        tiles += (it.nblocks + T - 1) / T;
+    }
+    if (tiles > 0xFFFFFFFFull) return QEXT_E_LIMIT;
+    h->tile_prefix[nitems] = tiles;
+    h->total_tiles = tiles;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    // the whole header plus the used part of the item table; the copy from
+    // pageable host memory is staged before cudaMemcpyAsync returns
+    const size_t bytes = offsetof(NoallocScratch, items) + sizeof(BatchStreamDev) * nitems;
+    if (cudaMemcpyAsync(g_noalloc_dev[dev], g_noalloc_stage, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return QEXT_E_CUDA;
+    if (!tiles) return QEXT_OK;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return QEXT_E_CUDA;
+    const uint64_t cap = uint64_t(sms) * cfg.ctas_per_sm;
+    const int grid = int(tiles < cap ? tiles : cap);
+    batch_noalloc_kernel<<<grid, kThreads, kSmemBytes, st>>>(static_cast<NoallocScratch *>(g_noalloc_dev[dev]),
+                                                              make_shift_muls());
+    return cudaGetLastError() == cudaSuccess ? QEXT_OK : QEXT_E_CUDA;
+}

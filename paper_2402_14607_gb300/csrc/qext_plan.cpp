@@ -154,6 +154,7 @@ const char *qext_status_string(int status) {
         case QEXT_E_BUDGET: return "QEXT_E_BUDGET: device memory budget exhausted";
         case QEXT_E_STATE: return "QEXT_E_STATE: call not allowed in the object's state";
         case QEXT_E_NOSPACE: return "QEXT_E_NOSPACE: output buffer too small";
+        case QEXT_E_LIMIT: return "QEXT_E_LIMIT: request exceeds a fixed capacity";
         default: return "QEXT_E_UNKNOWN";
     }
 }

@@ -24,6 +24,8 @@ QEXT_E_TIMEOUT = -6
 QEXT_E_BUDGET = -7
 QEXT_E_STATE = -8
 QEXT_E_NOSPACE = -9
+QEXT_E_LIMIT = -10
+QEXT_NOALLOC_MAX_ITEMS = 1024
 QEXT_F_DIRECT = 0x1
 QEXT_F_NBUF1 = 0x2
 QEXT_F_TILE32 = 0x4
@@ -86,13 +88,14 @@ def lib():
     L.qext_batch_capture.argtypes = [vp, vp]
     L.qext_batch_launch.argtypes = [vp, vp]
     L.qext_batch_autotune.argtypes = [vp, u32, vp, P(ctypes.c_float)]
+    L.qext_batch_run_noalloc.argtypes = [vp, u32, vp]
     for name in ["qext_plan_create", "qext_destroy", "qext_plan_info", "qext_alg1_params", "qext_extract",
                  "qext_extract_ex", "qext_extract_samples",
                  "qext_pack_samples", "qext_device_status", "qext_stream_create", "qext_stream_destroy",
                  "qext_stream_info", "qext_stream_push", "qext_stream_flush", "qext_stream_save",
                  "qext_stream_restore", "qext_batch_create", "qext_batch_destroy", "qext_batch_get_config",
                  "qext_batch_set_config", "qext_batch_run", "qext_batch_capture", "qext_batch_launch",
-                 "qext_batch_autotune"]:
+                 "qext_batch_autotune", "qext_batch_run_noalloc"]:
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -328,3 +331,11 @@ def qext_batch_autotune(b: Batch, reps: int = 3, stream=None) -> float:
     ms = ctypes.c_float()
     _check(lib().qext_batch_autotune(b.handle, reps, _stream(stream), ctypes.byref(ms)), "qext_batch_autotune")
     return ms.value
+
+
+def qext_batch_run_noalloc(items, stream=None) -> None:
+    """items: sequence of (plan, x, y, nblocks, out); see include/qext.h."""
+    arr = (BatchItem * max(1, len(items)))()
+    for i, (plan, x, y, nb, out) in enumerate(items):
+        arr[i] = BatchItem(plan.handle, _ptr(x), _ptr(y), nb, _ptr(out))
+    _check(lib().qext_batch_run_noalloc(arr, len(items), _stream(stream)), "qext_batch_run_noalloc")
