@@ -332,6 +332,70 @@ int qext_batch_autotune(qext_batch *b, uint32_t reps, qext_cuda_stream stream, f
 #define QEXT_NOALLOC_MAX_ITEMS 1024
 int qext_batch_run_noalloc(const qext_batch_item *items, uint32_t nitems, qext_cuda_stream stream);
 
+/* ------------------------------------------------------------------------
+ * Serving: continuous batching of requests from many QRNG channels.
+ *
+ * A channel is a pair of raw streams with its own plan; a request carries the
+ * next piece of a channel's streams in HOST memory (pinned memory lets the
+ * copies overlap) and receives the m-bit outputs of the blocks it completes,
+ * concatenated (a block straddling two requests completes in the later one;
+ * the channel's chaining state stays on the device).  Requests of a channel
+ * run one at a time in arrival order; requests of different channels that
+ * arrive while others are on the GPU are admitted as soon as device memory
+ * within the HBM budget frees up, and share batched kernel launches.
+ * ------------------------------------------------------------------------ */
+typedef struct qext_server qext_server;
+
+typedef struct qext_server_config {
+    uint64_t hbm_budget_bytes; /* device memory for requests in flight (one arena) */
+    uint32_t max_batch;        /* requests per round, 1 .. QEXT_NOALLOC_MAX_ITEMS */
+    uint32_t fake_executor;    /* 1: schedule only, no GPU (outputs not written) */
+} qext_server_config;
+
+typedef struct qext_completion {
+    uint64_t request_id;
+    uint32_t channel;
+    int32_t status;      /* QEXT_OK or the error of this request */
+    uint64_t out_bits;   /* output bits written to the request's buffer */
+    uint64_t blocks;     /* blocks the request completed */
+    double submit_s;     /* steady-clock seconds at submit */
+    double done_s;       /* steady-clock seconds when the output was on the host */
+    double latency_s;    /* done_s - submit_s */
+    uint32_t batched;    /* 1 if it ran in the round's batched launch */
+    uint32_t reserved;
+} qext_completion;
+
+typedef struct qext_server_stats {
+    uint64_t submitted, completed, rounds, max_round;
+    uint64_t bits_out;
+    uint64_t bytes_in_use, peak_bytes, budget_bytes;
+} qext_server_stats;
+
+/* Starts the scheduler thread; allocates the whole budget as one device
+ * arena (unless fake_executor).  Errors: INVAL, CUDA. */
+int qext_server_create(const qext_server_config *cfg, qext_server **out);
+/* Finishes every submitted request, stops the thread, frees everything. */
+int qext_server_destroy(qext_server *s);
+/* Adds a channel (plan must outlive the server); *channel receives its id.
+ * Errors: INVAL, UNSUPPORTED, CUDA. */
+int qext_server_add_channel(qext_server *s, const qext_plan *p, uint32_t *channel);
+/*
+ * qext_server_submit -- queues a request.
+ *   b          0: x_host / y_host hold `count` stream bits as packed uint32
+ *              words; 1..16: they hold `count` b-bit samples as uint16.
+ *   out_host   HOST buffer of out_capacity_words >= ceil((count_bits/n + 2)
+ *              * m / 32) words (else NOSPACE); written before completion.
+ * The host buffers must stay valid until the request completes.
+ * Errors: INVAL, NOSPACE, BUDGET (larger than the whole budget).
+ */
+int qext_server_submit(qext_server *s, uint32_t channel, uint32_t b, const void *x_host, const void *y_host,
+                       uint64_t count, uint32_t *out_host, uint64_t out_capacity_words, uint64_t *request_id);
+/* Moves up to max completions (oldest first) into out; *n receives the count. */
+int qext_server_poll(qext_server *s, qext_completion *out, uint32_t max, uint32_t *n);
+/* Waits until every submitted request has completed.  Errors: TIMEOUT. */
+int qext_server_drain(qext_server *s, double timeout_s);
+int qext_server_get_stats(qext_server *s, qext_server_stats *st);
+
 /*
  * qext_device_status -- reads and clears the device status word of the
  * current device (QEXT_OK or QEXT_E_TIMEOUT from a kernel that gave up a

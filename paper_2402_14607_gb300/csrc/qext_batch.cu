@@ -583,3 +583,71 @@ extern "C" int qext_batch_run_noalloc(const qext_batch_item *items, uint32_t nit
                                                               make_shift_muls());
     return cudaGetLastError() == cudaSuccess ? QEXT_OK : QEXT_E_CUDA;
 }
+
+// ---------------------------------------------------------------------------
+// Batch launch from caller-provided tables (the serving loop's rounds): the
+// descriptors are written to a pinned host staging buffer, copied to the
+// caller's device table asynchronously and consumed by the same kernel as the
+// allocation-free entry point.  The staging buffer must not be reused until
+// the copy has completed (the caller orders that with events).
+// ---------------------------------------------------------------------------
+namespace qext {
+
+size_t batch_table_bytes() { return sizeof(NoallocScratch); }
+
+int batch_launch_tables(const qext_batch_item *items, uint32_t nitems, void *d_table, void *h_stage,
+                        qext_cuda_stream stream) {
+    if (nitems > QEXT_NOALLOC_MAX_ITEMS) return QEXT_E_LIMIT;
+    static bool attr = false;
+    if (!attr) {
+        if (cudaFuncSetAttribute(batch_noalloc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) !=
+            cudaSuccess)
+            return QEXT_E_CUDA;
+        attr = true;
+    }
+    NoallocScratch *h = static_cast<NoallocScratch *>(h_stage);
+    h->counter = 0;
+    h->nitems = nitems;
+    const qext_batch_config cfg{4, 1, 3, 0};
+    uint64_t tiles = 0;
+    for (uint32_t k = 0; k < nitems; ++k) {
+        const qext_batch_item &it = items[k];
+        BatchStreamDev &d = h->items[k];
+        std::memset(&d, 0, sizeof d);
+        d.s.x = it.x;
+        d.s.y = it.y;
+        d.s.out = it.out;
+        d.s.nblocks = it.nblocks;
+        d.s.wpb = it.plan->n / 32;
+        d.s.m = it.plan->m;
+        d.s.ntaps = it.plan->ntaps;
+        for (int j = 0; j < 4; ++j) {
+            d.s.taps[j] = it.plan->taps[j];
+            d.s.tap_mul[j] = j < int(it.plan->ntaps) ? 1u << (it.plan->taps[j] & 31u) : 0u;
+        }
+        d.q = it.plan->q;
+        d.tma = ((reinterpret_cast<uintptr_t>(it.x) | reinterpret_cast<uintptr_t>(it.y)) % 16) == 0;
+        const uint32_t T = tile_blocks(cfg, d.q, d.s.wpb);
+        if (uint64_t(T) * d.s.wpb * 8 > uint64_t(kSmemBytes)) return QEXT_E_UNSUPPORTED;
+        h->tile_blocks[k] = T;
+        h->tile_prefix[k] = tiles;
+        tiles += (it.nblocks + T - 1) / T;
+    }
+    h->tile_prefix[nitems] = tiles;
+    h->total_tiles = tiles;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const size_t bytes = offsetof(NoallocScratch, items) + sizeof(BatchStreamDev) * nitems;
+    if (cudaMemcpyAsync(d_table, h_stage, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return QEXT_E_CUDA;
+    if (!tiles) return QEXT_OK;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return QEXT_E_CUDA;
+    const uint64_t cap = uint64_t(sms) * cfg.ctas_per_sm;
+    const int grid = int(tiles < cap ? tiles : cap);
+    batch_noalloc_kernel<<<grid, kThreads, kSmemBytes, st>>>(static_cast<NoallocScratch *>(d_table),
+                                                              make_shift_muls());
+    return cudaGetLastError() == cudaSuccess ? QEXT_OK : QEXT_E_CUDA;
+}
+
+}  // namespace qext

@@ -20,6 +20,19 @@ struct qext_plan {
     int gpu_supported;   // a kernel exists for this q
 };
 
+// Device-resident state of a stream (qext_stream.cu).
+struct qext_stream {
+    const qext_plan *plan;
+    uint32_t n, m, wpb;
+    uint64_t blocks_done;   // blocks output so far
+    uint64_t tail_bits;     // t < n
+    uint32_t pending_bits;  // p < 32
+    int cur;                // which tail buffer holds the tail
+    uint32_t *tail[2][2];   // [buffer][source], wpb + 1 words each (device)
+    uint32_t *pending;      // 1 word (device)
+    int device;
+};
+
 namespace qxd {
 struct StreamArgs;
 }
@@ -39,5 +52,11 @@ int launch_fused_samples(uint32_t q, uint32_t b, const qxd::StreamArgs &s, const
                          uint64_t nsamples, qext_cuda_stream stream);
 int launch_pack(uint32_t b, const uint16_t *samples, uint64_t nsamples, uint32_t *out, qext_cuda_stream stream);
 int read_device_status(int *status);
+
+// Batched launch from caller-provided device tables / pinned host staging
+// (qext_batch.cu); used by the serving loop.
+size_t batch_table_bytes();
+int batch_launch_tables(const qext_batch_item *items, uint32_t nitems, void *d_table, void *h_stage,
+                        qext_cuda_stream stream);
 
 }  // namespace qext

@@ -26,18 +26,6 @@
 
 using namespace qxd;
 
-struct qext_stream {
-    const qext_plan *plan;
-    uint32_t n, m, wpb;
-    uint64_t blocks_done;   // blocks output so far
-    uint64_t tail_bits;     // t < n
-    uint32_t pending_bits;  // p < 32
-    int cur;                // which tail buffer holds the tail
-    uint32_t *tail[2][2];   // [buffer][source], wpb + 1 words each (device)
-    uint32_t *pending;      // 1 word (device)
-    int device;
-};
-
 namespace {
 
 constexpr int kStreamThreads = 32;

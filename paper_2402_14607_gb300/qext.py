@@ -44,6 +44,23 @@ class BatchConfig(ctypes.Structure):
                 ("ctas_per_sm", ctypes.c_uint32), ("order", ctypes.c_uint32)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("max_batch", ctypes.c_uint32),
+                ("fake_executor", ctypes.c_uint32)]
+
+
+class Completion(ctypes.Structure):
+    _fields_ = [("request_id", ctypes.c_uint64), ("channel", ctypes.c_uint32), ("status", ctypes.c_int32),
+                ("out_bits", ctypes.c_uint64), ("blocks", ctypes.c_uint64), ("submit_s", ctypes.c_double),
+                ("done_s", ctypes.c_double), ("latency_s", ctypes.c_double), ("batched", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint64) for k in ("submitted", "completed", "rounds", "max_round", "bits_out",
+                                               "bytes_in_use", "peak_bytes", "budget_bytes")]
+
+
 class QextError(RuntimeError):
     def __init__(self, code: int, where: str = ""):
         self.code = code
@@ -89,13 +106,22 @@ def lib():
     L.qext_batch_launch.argtypes = [vp, vp]
     L.qext_batch_autotune.argtypes = [vp, u32, vp, P(ctypes.c_float)]
     L.qext_batch_run_noalloc.argtypes = [vp, u32, vp]
+    L.qext_server_create.argtypes = [P(ServerConfig), P(vp)]
+    L.qext_server_destroy.argtypes = [vp]
+    L.qext_server_add_channel.argtypes = [vp, vp, P(u32)]
+    L.qext_server_submit.argtypes = [vp, u32, u32, vp, vp, u64, vp, u64, P(u64)]
+    L.qext_server_poll.argtypes = [vp, P(Completion), u32, P(u32)]
+    L.qext_server_drain.argtypes = [vp, dbl]
+    L.qext_server_get_stats.argtypes = [vp, P(ServerStats)]
     for name in ["qext_plan_create", "qext_destroy", "qext_plan_info", "qext_alg1_params", "qext_extract",
                  "qext_extract_ex", "qext_extract_samples",
                  "qext_pack_samples", "qext_device_status", "qext_stream_create", "qext_stream_destroy",
                  "qext_stream_info", "qext_stream_push", "qext_stream_flush", "qext_stream_save",
                  "qext_stream_restore", "qext_batch_create", "qext_batch_destroy", "qext_batch_get_config",
                  "qext_batch_set_config", "qext_batch_run", "qext_batch_capture", "qext_batch_launch",
-                 "qext_batch_autotune", "qext_batch_run_noalloc"]:
+                 "qext_batch_autotune", "qext_batch_run_noalloc", "qext_server_create", "qext_server_destroy",
+                 "qext_server_add_channel", "qext_server_submit", "qext_server_poll", "qext_server_drain",
+                 "qext_server_get_stats"]:
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -339,3 +365,78 @@ def qext_batch_run_noalloc(items, stream=None) -> None:
     for i, (plan, x, y, nb, out) in enumerate(items):
         arr[i] = BatchItem(plan.handle, _ptr(x), _ptr(y), nb, _ptr(out))
     _check(lib().qext_batch_run_noalloc(arr, len(items), _stream(stream)), "qext_batch_run_noalloc")
+
+
+class Server:
+    """Owns a qext_server handle; keeps plans and submitted host buffers
+    alive until their requests complete."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+        self._keep = {}
+        self._plans = []
+
+    def close(self):
+        if self.handle:
+            lib().qext_server_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def qext_server_create(hbm_budget_bytes: int, max_batch: int = 256, fake_executor: bool = False) -> Server:
+    cfg = ServerConfig(hbm_budget_bytes, max_batch, 1 if fake_executor else 0)
+    h = ctypes.c_void_p()
+    _check(lib().qext_server_create(ctypes.byref(cfg), ctypes.byref(h)), "qext_server_create")
+    return Server(h.value)
+
+
+def qext_server_destroy(s: Server) -> None:
+    s.close()
+
+
+def qext_server_add_channel(s: Server, plan: Plan) -> int:
+    c = ctypes.c_uint32()
+    _check(lib().qext_server_add_channel(s.handle, plan.handle, ctypes.byref(c)), "qext_server_add_channel")
+    s._plans.append(plan)
+    return c.value
+
+
+def qext_server_submit(s: Server, channel: int, b: int, x_host, y_host, count: int, out_host,
+                       out_capacity_words: int) -> int:
+    """x_host / y_host / out_host: host tensors (pinned for overlap) or int
+    addresses; they are kept alive until the request completes."""
+    rid = ctypes.c_uint64()
+    _check(lib().qext_server_submit(s.handle, channel, b, _ptr(x_host), _ptr(y_host), count, _ptr(out_host),
+                                    out_capacity_words, ctypes.byref(rid)), "qext_server_submit")
+    s._keep[rid.value] = (x_host, y_host, out_host)
+    return rid.value
+
+
+def qext_server_poll(s: Server, max_n: int = 1024):
+    arr = (Completion * max_n)()
+    n = ctypes.c_uint32()
+    _check(lib().qext_server_poll(s.handle, arr, max_n, ctypes.byref(n)), "qext_server_poll")
+    out = []
+    for i in range(n.value):
+        c = arr[i]
+        out.append(dict(request_id=c.request_id, channel=c.channel, status=c.status, out_bits=c.out_bits,
+                        blocks=c.blocks, submit_s=c.submit_s, done_s=c.done_s, latency_s=c.latency_s,
+                        batched=bool(c.batched)))
+        s._keep.pop(c.request_id, None)
+    return out
+
+
+def qext_server_drain(s: Server, timeout_s: float = 60.0) -> None:
+    _check(lib().qext_server_drain(s.handle, timeout_s), "qext_server_drain")
+
+
+def qext_server_get_stats(s: Server) -> dict:
+    st = ServerStats()
+    _check(lib().qext_server_get_stats(s.handle, ctypes.byref(st)), "qext_server_get_stats")
+    return {k: getattr(st, k) for k, _ in ServerStats._fields_}
