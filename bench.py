@@ -153,6 +153,137 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+# Batched and serving measurements (GPU)
+# ---------------------------------------------------------------------------
+def measure_batched(args, dev):
+    """64 stream pairs (block counts 2^U, U ~ U(12, 20); n over {256, 1024,
+    4096}), uniformly random packed words generated on the device: one
+    autotuned batched launch replayed from a CUDA graph, against the plain
+    single-stream path (one qext_extract per stream) on the same data."""
+    import torch
+
+    from paper_2402_14607_gb300 import qext, workloads
+    specs = workloads.config_batched()
+    plans, items = {}, []
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(3)
+    total_in = total_out_bits = 0
+    for sp in specs:
+        key = (sp.n, sp.k, sp.eps)
+        if key not in plans:
+            plans[key] = qext.qext_plan_create(sp.n, 0, sp.k, sp.eps)
+        plan = plans[key]
+        words = sp.nblocks * sp.n // 32
+        x = torch.randint(-2 ** 31, 2 ** 31 - 1, (words,), dtype=torch.int32, device=dev, generator=gen)
+        y = torch.randint(-2 ** 31, 2 ** 31 - 1, (words,), dtype=torch.int32, device=dev, generator=gen)
+        out = torch.empty(-(-sp.nblocks * plan.info["m"] // 32), dtype=torch.int32, device=dev)
+        items.append((plan, x, y, sp.nblocks, out))
+        total_in += 2 * words * 4
+        total_out_bits += sp.nblocks * plan.info["m"]
+    stream = torch.cuda.Stream(device=dev)
+    b = qext.qext_batch_create(items)
+    tuned_ms = qext.qext_batch_autotune(b, 2, stream)
+    cfg = qext.qext_batch_get_config(b)
+    qext.qext_batch_capture(b, stream)
+    reps = max(3, min(args.steps, 20))
+    for _ in range(2):
+        qext.qext_batch_launch(b, stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        qext.qext_batch_launch(b, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_batch = e0.elapsed_time(e1) * 1e-3 / reps
+    ref = [it[4].clone() for it in items]
+    # plain single-stream path on the same streams
+    sh = int(stream.cuda_stream)
+    for plan, x, y, nb, out in items:
+        qext.qext_extract(plan, x, y, nb, out, sh)
+    e0.record(stream)
+    for _ in range(reps):
+        for plan, x, y, nb, out in items:
+            qext.qext_extract(plan, x, y, nb, out, sh)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_plain = e0.elapsed_time(e1) * 1e-3 / reps
+    same = all(torch.equal(r, it[4]) for r, it in zip(ref, items))
+    b.close()
+    return {"workload": "64 stream pairs, 2^U blocks (U~U(12,20)), n in {256,1024,4096}, random words on device",
+            "streams": len(items), "input_bytes": total_in, "extracted_bits": total_out_bits,
+            "batched_graph_gbps": round(total_out_bits / t_batch / 1e9, 2), "batched_ms": round(t_batch * 1e3, 3),
+            "plain_per_stream_gbps": round(total_out_bits / t_plain / 1e9, 2), "plain_ms": round(t_plain * 1e3, 3),
+            "input_tb_per_s_batched": round(total_in / t_batch / 1e12, 3),
+            "autotuned": {k: cfg[k] for k in ("blocks_per_thread_small", "blocks_per_thread_mid", "ctas_per_sm",
+                                              "order", "ntiles")}, "autotune_best_ms": round(tuned_ms, 3),
+            "outputs_equal_plain": same, "launches_per_run": 1}
+
+
+def measure_serving(args, dev):
+    """Poisson arrivals at 2000 requests/s from 256 channels, 2^10..2^18
+    block pairs per request (rounded to multiples of 3 so requests hold whole
+    12-bit samples), n per channel over {256, 1024, 4096}; raw 12-bit samples
+    pre-staged in pinned host memory (a shared pool); 64 GB admission budget.
+    Latency = submit -> output on the host."""
+    import threading
+
+    import torch
+
+    from paper_2402_14607_gb300 import qext, workloads
+    reqs = workloads.serving_requests(nreq=args.serving_requests)
+    eps = workloads.EPS_BLOCK_MIXED
+    kb = {n: workloads.block_min_entropy(n, 12, workloads.adc_min_entropy(12)) for n in (256, 1024, 4096)}
+    plans = {n: qext.qext_plan_create(n, 0, kb[n], eps[n]) for n in (256, 1024, 4096)}
+    max_samples = max(3 * ((r["nblocks"] + 2) // 3) * r["n"] // 12 for r in reqs)
+    pool_x = torch.from_numpy(workloads.adc_samples(41, max_samples, 12).view(np.int16)).pin_memory()
+    pool_y = torch.from_numpy(workloads.adc_samples(42, max_samples, 12).view(np.int16)).pin_memory()
+    outs = []
+    srv = qext.qext_server_create(hbm_budget_bytes=64 << 30, max_batch=256)
+    chan_of = {}
+    for r in reqs:
+        if r["channel"] not in chan_of:
+            chan_of[r["channel"]] = qext.qext_server_add_channel(srv, plans[r["n"]])
+    prepared = []
+    for r in reqs:
+        nb = 3 * max(1, round(r["nblocks"] / 3))
+        count = nb * r["n"] // 12
+        cap = (nb + 2) * plans[r["n"]].info["m"] // 32 + 2
+        out = torch.empty(cap, dtype=torch.int32).pin_memory()
+        outs.append(out)
+        prepared.append((r["t"], chan_of[r["channel"]], count, out, cap, nb * plans[r["n"]].info["m"]))
+    t_start = time.perf_counter() + 0.05
+
+    def feeder():
+        for t, c, count, out, cap, _ in prepared:
+            delay = t_start + t - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            qext.qext_server_submit(srv, c, 12, pool_x, pool_y, count, out, cap)
+
+    th = threading.Thread(target=feeder)
+    th.start()
+    th.join()
+    qext.qext_server_drain(srv, 300.0)
+    done = qext.qext_server_poll(srv, len(reqs) + 10)
+    st = qext.qext_server_get_stats(srv)
+    srv.close()
+    lat = np.array([d["latency_s"] for d in done]) * 1e3
+    first = min(d["submit_s"] for d in done)
+    last = max(d["done_s"] for d in done)
+    bits = sum(d["out_bits"] for d in done)
+    in_bits = sum(2 * p[2] * 12 for p in prepared)
+    return {"workload": "%d requests, Poisson 2000/s, 256 channels, 2^10..2^18 block pairs, 12-bit samples, "
+                        "n in {256,1024,4096}, 64 GB budget" % len(reqs),
+            "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
+            "mean_ms": round(float(lat.mean()), 3), "aggregate_extracted_gbps": round(bits / (last - first) / 1e9, 2),
+            "aggregate_input_gbps": round(in_bits / (last - first) / 1e9, 1),
+            "offered_load_req_per_s": 2000, "completed": len(done),
+            "all_ok": all(d["status"] == 0 for d in done), "rounds": st["rounds"], "max_round": st["max_round"],
+            "peak_device_bytes": st["peak_bytes"], "batched_fraction": round(
+                sum(1 for d in done if d["batched"]) / max(1, len(done)), 3)}
+
+
+# ---------------------------------------------------------------------------
 # GPU leg
 # ---------------------------------------------------------------------------
 def run_gpu(args):
@@ -262,35 +393,37 @@ def run_gpu(args):
                                 else "fallback 6.8 TB/s"),
                 "per_kernel_ms": per_kernel}
 
-    # end to end through the C ABI: pinned host samples in, output back out
+    # end to end through the C ABI with HOST buffers: qext_pipeline_run copies
+    # pinned host samples in, extracts and copies the output back, per step
+    gpu_out = d_out.cpu().numpy().view(np.uint32)
+    del d_px, d_py
     h_sx = torch.from_numpy(sx.view(np.int16)).pin_memory()
     h_sy = torch.from_numpy(sy.view(np.int16)).pin_memory()
     h_out = torch.empty(out_words, dtype=torch.int32).pin_memory()
-
-    def e2e_step():
-        with torch.cuda.stream(stream):
-            d_sx.copy_(h_sx, non_blocking=True)
-            d_sy.copy_(h_sy, non_blocking=True)
-        step()
-        with torch.cuda.stream(stream):
-            h_out.copy_(d_out, non_blocking=True)
-
+    pp = qext.qext_pipeline_create(plan, spec.b, args.e2e_chunk_blocks)
     for _ in range(max(1, min(args.warmup, 3))):
-        e2e_step()
-    torch.cuda.synchronize()
+        qext.qext_pipeline_run(pp, h_sx, h_sy, ns, spec.nblocks, h_out)
     if world > 1:
         dist.barrier()
-    e0, e1 = ev(), ev()
-    e0.record(stream)
+    t0 = time.perf_counter()
     for _ in range(args.steps):
-        e2e_step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    te = max_over_ranks(e0.elapsed_time(e1) * 1e-3, world)
+        qext.qext_pipeline_run(pp, h_sx, h_sy, ns, spec.nblocks, h_out)
+    te = max_over_ranks(time.perf_counter() - t0, world)
+    e2e_ok = bool((h_out.numpy().view(np.uint32) == gpu_out).all())
     e2e = {"value": round(world * args.steps * bits_per_step / te / 1e9, 3), "unit": UNIT,
            "h2d_bytes_per_step": 2 * ns * 2, "d2h_bytes_per_step": out_words * 4,
-           "path": "pinned host samples -> cudaMemcpyAsync x2 -> step -> cudaMemcpyAsync -> pinned host output"}
-    gpu_out = d_out.cpu().numpy().view(np.uint32)
+           "path": "qext_pipeline_run: pinned host samples -> H2D chunks -> qext_extract_samples -> D2H, "
+                   "three CUDA streams overlapped, chunk %d blocks" % qext.qext_pipeline_info(pp)["chunk_blocks"],
+           "matches_device_path": e2e_ok}
+    pp.close()
+    del h_sx, h_sy
+
+    extra = {}
+    if not args.no_extra and world == 1:
+        torch.cuda.empty_cache()
+        extra["batched"] = measure_batched(args, dev)
+        torch.cuda.empty_cache()
+        extra["serving"] = measure_serving(args, dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -312,6 +445,7 @@ def run_gpu(args):
             "clocks": {k: clk.get(k) for k in ("sm_mhz", "sm_max_mhz", "reasons", "samples", "source")},
             "gpu_launches": launches_per_step * args.steps,
         }
+        line.update(extra)
         print(json.dumps(line), flush=True)
     plan.close()
     if world > 1:
@@ -329,6 +463,9 @@ def main(argv=None):
     ap.add_argument("--cpu-sample-blocks", type=int, default=1 << 20)
     ap.add_argument("--ref-sample-blocks", type=int, default=1 << 17)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the batched and serving measurements")
+    ap.add_argument("--e2e-chunk-blocks", type=int, default=1 << 17)
+    ap.add_argument("--serving-requests", type=int, default=300)
     ap.add_argument("--unfused", action="store_true",
                     help="step = qext_pack_samples x2 + qext_extract instead of the fused qext_extract_samples")
     ap.add_argument("--traffic", type=float, default=None,

@@ -396,6 +396,34 @@ int qext_server_poll(qext_server *s, qext_completion *out, uint32_t max, uint32_
 int qext_server_drain(qext_server *s, double timeout_s);
 int qext_server_get_stats(qext_server *s, qext_server_stats *st);
 
+/* ------------------------------------------------------------------------
+ * Host-to-host extraction with overlapped copies.
+ * ------------------------------------------------------------------------ */
+typedef struct qext_pipeline qext_pipeline; /* opaque, holds device buffers and CUDA streams */
+
+/*
+ * qext_pipeline_create -- device buffers for two chunks of chunk_blocks
+ * blocks (rounded up so that a chunk holds whole samples and whole output
+ * words; qext_pipeline_info reports the value used).
+ *   b   0: input is packed uint32 words; 8, 12 or 16: raw samples in uint16
+ *       containers, extracted by the fused kernel (q in {4, 16, 64}).
+ * Errors: INVAL, UNSUPPORTED, CUDA.
+ */
+int qext_pipeline_create(const qext_plan *p, uint32_t b, uint64_t chunk_blocks, qext_pipeline **out);
+int qext_pipeline_info(const qext_pipeline *pp, uint64_t *chunk_blocks);
+int qext_pipeline_destroy(qext_pipeline *pp);
+
+/*
+ * qext_pipeline_run -- extracts nblocks blocks from HOST streams x_host,
+ * y_host (count samples, or count bits for b = 0; nblocks * n <= count
+ * bits) into out_host (HOST, ceil(nblocks*m/32) words), chunk by chunk with
+ * copies in, kernels and copies out overlapped.  Synchronous: returns when the
+ * output is in out_host.  Page-locked host memory makes the copies
+ * asynchronous (pageable memory works, slower).  Errors: INVAL, CUDA.
+ */
+int qext_pipeline_run(qext_pipeline *pp, const void *x_host, const void *y_host, uint64_t count, uint64_t nblocks,
+                      uint32_t *out_host);
+
 /*
  * qext_device_status -- reads and clears the device status word of the
  * current device (QEXT_OK or QEXT_E_TIMEOUT from a kernel that gave up a

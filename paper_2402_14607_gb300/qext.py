@@ -113,6 +113,10 @@ def lib():
     L.qext_server_poll.argtypes = [vp, P(Completion), u32, P(u32)]
     L.qext_server_drain.argtypes = [vp, dbl]
     L.qext_server_get_stats.argtypes = [vp, P(ServerStats)]
+    L.qext_pipeline_create.argtypes = [vp, u32, u64, P(vp)]
+    L.qext_pipeline_info.argtypes = [vp, P(u64)]
+    L.qext_pipeline_destroy.argtypes = [vp]
+    L.qext_pipeline_run.argtypes = [vp, vp, vp, u64, u64, vp]
     for name in ["qext_plan_create", "qext_destroy", "qext_plan_info", "qext_alg1_params", "qext_extract",
                  "qext_extract_ex", "qext_extract_samples",
                  "qext_pack_samples", "qext_device_status", "qext_stream_create", "qext_stream_destroy",
@@ -121,7 +125,8 @@ def lib():
                  "qext_batch_set_config", "qext_batch_run", "qext_batch_capture", "qext_batch_launch",
                  "qext_batch_autotune", "qext_batch_run_noalloc", "qext_server_create", "qext_server_destroy",
                  "qext_server_add_channel", "qext_server_submit", "qext_server_poll", "qext_server_drain",
-                 "qext_server_get_stats"]:
+                 "qext_server_get_stats", "qext_pipeline_create", "qext_pipeline_info", "qext_pipeline_destroy",
+                 "qext_pipeline_run"]:
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -440,3 +445,41 @@ def qext_server_get_stats(s: Server) -> dict:
     st = ServerStats()
     _check(lib().qext_server_get_stats(s.handle, ctypes.byref(st)), "qext_server_get_stats")
     return {k: getattr(st, k) for k, _ in ServerStats._fields_}
+
+
+class Pipeline:
+    def __init__(self, handle: int, plan: Plan):
+        self.handle = handle
+        self.plan = plan
+
+    def close(self):
+        if self.handle:
+            lib().qext_pipeline_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def qext_pipeline_create(plan: Plan, b: int, chunk_blocks: int) -> Pipeline:
+    h = ctypes.c_void_p()
+    _check(lib().qext_pipeline_create(plan.handle, b, chunk_blocks, ctypes.byref(h)), "qext_pipeline_create")
+    return Pipeline(h.value, plan)
+
+
+def qext_pipeline_info(pp: Pipeline) -> dict:
+    cb = ctypes.c_uint64()
+    _check(lib().qext_pipeline_info(pp.handle, ctypes.byref(cb)), "qext_pipeline_info")
+    return dict(chunk_blocks=cb.value)
+
+
+def qext_pipeline_destroy(pp: Pipeline) -> None:
+    pp.close()
+
+
+def qext_pipeline_run(pp: Pipeline, x_host, y_host, count: int, nblocks: int, out_host) -> None:
+    _check(lib().qext_pipeline_run(pp.handle, _ptr(x_host), _ptr(y_host), count, nblocks, _ptr(out_host)),
+           "qext_pipeline_run")

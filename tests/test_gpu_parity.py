@@ -212,3 +212,36 @@ def test_config_large_single_stream_fused_sampled():
         l = int(l)
         z = oracle.extract(16, 64, 16, poly, ox[l * 32:(l + 1) * 32], oy[l * 32:(l + 1) * 32], 1)
         assert bits_at(got, l * 16, 16) == int(z[0]), "block %d" % l
+
+
+@pytest.mark.parametrize("q,b,nblocks,chunk", [(16, 12, 5000, 700), (16, 0, 3001, 512), (4, 8, 9000, 1000),
+                                               (64, 12, 400, 100), (64, 0, 257, 64), (16, 16, 100, 1000)])
+def test_pipeline_host_to_host_matches_oracle(q, b, nblocks, chunk):
+    """qext_pipeline_run from pinned host buffers, chunked and overlapped,
+    against the oracle (the benchmark's end-to-end path)."""
+    plan = plan_for(q, 64)
+    n = 64 * q
+    pp = qext.qext_pipeline_create(plan, b, chunk)
+    assert qext.qext_pipeline_info(pp)["chunk_blocks"] >= chunk
+    if b:
+        ns = -(-nblocks * n // b) + 3
+        sx = workloads.adc_samples(b + q, ns, b)
+        sy = workloads.adc_samples(b + q + 1, ns, b)
+        hx = torch.from_numpy(sx.view(np.int16)).pin_memory()
+        hy = torch.from_numpy(sy.view(np.int16)).pin_memory()
+        count = ns
+        ox = oracle.pack_samples(b, sx)[: nblocks * n // 32]
+        oy = oracle.pack_samples(b, sy)[: nblocks * n // 32]
+    else:
+        ox = workloads.random_words(q + 5, nblocks * n // 32)
+        oy = workloads.random_words(q + 6, nblocks * n // 32)
+        hx = torch.from_numpy(ox.view(np.int32)).pin_memory()
+        hy = torch.from_numpy(oy.view(np.int32)).pin_memory()
+        count = nblocks * n
+    nout = -(-nblocks * q // 32)
+    out = torch.full((nout + 2,), -1, dtype=torch.int32).pin_memory()
+    qext.qext_pipeline_run(pp, hx, hy, count, nblocks, out)
+    got = out.numpy().view(np.uint32)
+    assert (got[nout:] == 0xFFFFFFFF).all()
+    assert (got[:nout] == oracle_extract(plan, ox, oy, nblocks)).all()
+    pp.close()
