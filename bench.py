@@ -44,6 +44,26 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+def measured_traffic(name, sources):
+    """ncu DRAM bytes per launch recorded in profiles/<name>.md, if the kernel
+    sources are unchanged since the capture (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", name + ".md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    fields = dict(line.split(":", 1) for line in text.splitlines()
+                  if line.startswith(("traffic_bytes_per_launch:", "kernel_sources_sha256:")))
+    h = hashlib.sha256()
+    for f in sources:
+        with open(os.path.join(ROOT, "paper_2402_14607_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    if fields.get("kernel_sources_sha256", "").strip() != h.hexdigest()[:16]:
+        return None
+    return int(fields["traffic_bytes_per_launch"])
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -376,18 +396,22 @@ def run_gpu(args):
         pack_bytes = ns * 2 + nwords_packed * 4
         pack_s = statistics.mean(pack_ms) * 1e-3 / 2
         if ext_s >= 2 * pack_s:
-            dom = {"kernel": "extract_tiled_kernel<16,0>", "bytes": ext_bytes, "t": ext_s}
+            dom = {"kernel": "extract_tiled_kernel<16,0>", "bytes": ext_bytes, "t": ext_s,
+               "traffic": measured_traffic("tiled_extract_q16_large_single_stream",
+                                           ["qext_extract.cu", "qext_block.cuh", "qext_device.cuh"])}
         else:
-            dom = {"kernel": "pack_kernel_vec<12>", "bytes": pack_bytes, "t": pack_s}
+            dom = {"kernel": "pack_kernel_vec<12>", "bytes": pack_bytes, "t": pack_s, "traffic": None}
         per_kernel = {"pack_x_plus_y": round(statistics.mean(pack_ms), 4), "extract": round(statistics.mean(ext_ms), 4)}
     else:
         # the fused kernel reads both sample arrays once and writes the output
-        dom = {"kernel": "extract_tiled_kernel<16,12> (fused ingest)", "bytes": 2 * ns * 2 + out_words * 4,
-               "t": ext_s}
+        dom = {"kernel": "extract_fused_kernel<16,12> (fused ingest)", "bytes": 2 * ns * 2 + out_words * 4,
+               "t": ext_s, "traffic": measured_traffic("fused_ingest_q16_b12_large_single_stream",
+                                                       ["qext_fused.cu", "qext_block.cuh", "qext_device.cuh"])}
         per_kernel = {"extract_samples": round(statistics.mean(ext_ms), 4)}
     achieved = dom["bytes"] / dom["t"] / 1e9
     roofline = {"bound": "hbm", "kernel": dom["kernel"], "achieved": round(achieved, 1), "peak": peak,
-                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": args.traffic,
+                "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": args.traffic if args.traffic is not None else dom["traffic"],
                 "algorithmic_bytes_per_launch": dom["bytes"],
                 "peak_source": ("measured hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured"
                                 else "fallback 6.8 TB/s"),

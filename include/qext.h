@@ -141,7 +141,11 @@ int qext_extract(const qext_plan *p, const uint32_t *x, const uint32_t *y, uint6
 #define QEXT_F_NBUF1 0x2u  /* one tile buffer per CTA (more CTAs per SM) instead of two (prefetch) */
 #define QEXT_F_TILE32 0x4u /* at most 32 blocks per tile */
 #define QEXT_F_TILE64 0x8u /* at most 64 blocks per tile (exclusive with TILE32) */
-#define QEXT_F_ALL 0xFu
+#define QEXT_F_TEST_TIMEOUT 0x10u /* test of failure detection: every CTA arms its tile barrier but issues no
+                                   copy, gives up its bounded wait after a few polls, records QEXT_E_TIMEOUT
+                                   (qext_device_status) and returns; outputs are not written.  Needs 16-byte
+                                   aligned x, y and a staged tile (else INVAL). */
+#define QEXT_F_ALL 0x1Fu
 
 /*
  * qext_extract_ex -- qext_extract with launch options (flags, 0 = the

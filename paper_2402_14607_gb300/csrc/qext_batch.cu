@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(const BatchStreamDev *_
         load_tile(s, tl.first, tl.nb, it.tma, xs, ys, &bar, uses, ok);
         if (!__syncthreads_and(ok)) {
             if (tid == 0) {
-                record_status(QEXT_E_TIMEOUT);
+                record_status(s.status, QEXT_E_TIMEOUT);
                 mbar_wait_bounded(&bar, (uses - 1) & 1u);
             }
             return;
@@ -296,6 +296,7 @@ int qext_batch_create(const qext_batch_item *items, uint32_t nitems, qext_batch 
             d.s.taps[k] = it.plan->taps[k];
             d.s.tap_mul[k] = k < int(it.plan->ntaps) ? 1u << (it.plan->taps[k] & 31u) : 0u;
         }
+        d.s.status = qext::device_status_ptr();
         d.q = it.plan->q;
         d.tma = al % 16 == 0;
         b->items.push_back(d);
@@ -480,7 +481,7 @@ __global__ void __launch_bounds__(kThreads) batch_noalloc_kernel(NoallocScratch 
         load_tile(s, first, nb, it.tma, xs, ys, &bar, uses, ok);
         if (!__syncthreads_and(ok)) {
             if (tid == 0) {
-                record_status(QEXT_E_TIMEOUT);
+                record_status(s.status, QEXT_E_TIMEOUT);
                 mbar_wait_bounded(&bar, (uses - 1) & 1u);
             }
             return;
@@ -557,6 +558,7 @@ extern "C" int qext_batch_run_noalloc(const qext_batch_item *items, uint32_t nit
             d.s.taps[j] = it.plan->taps[j];
             d.s.tap_mul[j] = j < int(it.plan->ntaps) ? 1u << (it.plan->taps[j] & 31u) : 0u;
         }
+        d.s.status = qext::device_status_ptr();
         d.q = it.plan->q;
         d.tma = al % 16 == 0;
         const uint32_t T = tile_blocks(cfg, d.q, d.s.wpb);
@@ -625,6 +627,7 @@ int batch_launch_tables(const qext_batch_item *items, uint32_t nitems, void *d_t
             d.s.taps[j] = it.plan->taps[j];
             d.s.tap_mul[j] = j < int(it.plan->ntaps) ? 1u << (it.plan->taps[j] & 31u) : 0u;
         }
+        d.s.status = qext::device_status_ptr();
         d.q = it.plan->q;
         d.tma = ((reinterpret_cast<uintptr_t>(it.x) | reinterpret_cast<uintptr_t>(it.y)) % 16) == 0;
         const uint32_t T = tile_blocks(cfg, d.q, d.s.wpb);

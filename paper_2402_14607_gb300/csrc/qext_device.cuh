@@ -21,9 +21,6 @@
 
 #include "qext_internal.h"
 
-// Sticky device status word (defined in qext_ingest.cu).
-extern __device__ int qext_device_status_word;
-
 namespace qxd {
 
 // 2^G and 2^(32-G) for G = 1, 2, 4 (index log2 G).  Passed at run time so the
@@ -45,6 +42,7 @@ struct StreamArgs {
     uint32_t ntaps;         // taps of P below x^q (0 for q = 1), descending, last 0
     uint32_t taps[4];
     uint32_t tap_mul[4];    // 2^taps[t] for t < ntaps, else 0 (run-time multipliers, see ShiftMuls)
+    int *status;            // device status word (qext_device_status), or null
 };
 
 __host__ __device__ inline ShiftMuls make_shift_muls() {
@@ -342,13 +340,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Waits for phase `parity` of bar to complete; gives up after kMaxPolls.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
-    for (uint32_t i = 0; i < kMaxPolls; ++i)
+// Waits for phase `parity` of bar to complete; gives up after max_polls.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint32_t max_polls = kMaxPolls) {
+    for (uint32_t i = 0; i < max_polls; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
 
-__device__ __forceinline__ void record_status(int code) { atomicCAS(&qext_device_status_word, 0, code); }
+// Sticky: the first error recorded stays until the host reads it.
+__device__ __forceinline__ void record_status(int *status, int code) {
+    if (status) atomicCAS(status, 0, code);
+}
 
 }  // namespace qxd

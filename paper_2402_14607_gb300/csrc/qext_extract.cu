@@ -38,6 +38,8 @@ struct TileArgs {
     uint32_t nbuf;  // 1 or 2 tile buffers
     int tma;        // x, y 16-byte aligned: full tiles arrive by bulk copy
     int vec;        // wpb % 4 == 0: 16-byte shared-memory reads
+    uint32_t max_polls;  // bound of every mbarrier wait
+    int no_copy;         // test of the timeout path: arm the barrier, issue no copy
 };
 
 template <int Q>
@@ -73,6 +75,7 @@ __global__ void __launch_bounds__(kThreads) extract_tiled_kernel(const TileArgs 
     auto issue = [&](uint64_t t, int b) {
         const uint32_t bytes = tw * 4u;
         mbar_expect_tx(&full[b], 2u * bytes);
+        if (ta.no_copy) return;  // the completion never comes: the wait must give up
         tma_load_1d(bufs[b], s.x + t * tw, bytes, &full[b]);
         tma_load_1d(bufs[b] + tw, s.y + t * tw, bytes, &full[b]);
     };
@@ -96,13 +99,15 @@ __global__ void __launch_bounds__(kThreads) extract_tiled_kernel(const TileArgs 
             __syncthreads();
         } else if (ta.tma && full_tile(tile)) {
             const uint32_t use = ta.nbuf > 1 ? (k >> 1) : k;
-            const bool ok = mbar_wait_bounded(&full[b], use & 1u);
+            const bool ok = mbar_wait_bounded(&full[b], use & 1u, ta.max_polls);
             if (!__syncthreads_and(ok)) {
                 if (tid == 0) {
-                    record_status(QEXT_E_TIMEOUT);
+                    record_status(s.status, QEXT_E_TIMEOUT);
                     // give the copies in flight a bounded chance to land
-                    mbar_wait_bounded(&full[b], use & 1u);
-                    if (ta.nbuf > 1) mbar_wait_bounded(&full[b ^ 1], ((k + 1) >> 1) & 1u);
+                    if (!ta.no_copy) {
+                        mbar_wait_bounded(&full[b], use & 1u, ta.max_polls);
+                        if (ta.nbuf > 1) mbar_wait_bounded(&full[b ^ 1], ((k + 1) >> 1) & 1u, ta.max_polls);
+                    }
                 }
                 return;
             }
@@ -186,7 +191,7 @@ struct LaunchCache {
 template <int Q, int B>
 int launch_q(const StreamArgs &s, const uint16_t *sx, const uint16_t *sy, uint64_t nsamples, cudaStream_t st,
              uint32_t flags) {
-    const bool force_direct = B == 0 && (flags & QEXT_F_DIRECT);
+    const bool force_direct = B == 0 && (flags & QEXT_F_DIRECT) && !(flags & QEXT_F_TEST_TIMEOUT);
     const uint32_t t_max = (flags & QEXT_F_TILE32) ? 32u : (flags & QEXT_F_TILE64) ? 64u : 128u;
     const uint32_t nb_max = (flags & QEXT_F_NBUF1) ? 1u : 2u;
     static LaunchCache cache;
@@ -226,6 +231,9 @@ int launch_q(const StreamArgs &s, const uint16_t *sx, const uint16_t *sy, uint64
         const uintptr_t al = reinterpret_cast<uintptr_t>(s.x) | reinterpret_cast<uintptr_t>(s.y);
         ta.tma = B == 0 && al % 16 == 0;
         ta.vec = s.wpb % 4 == 0;
+        ta.no_copy = B == 0 && (flags & QEXT_F_TEST_TIMEOUT) ? 1 : 0;
+        ta.max_polls = ta.no_copy ? 256u : kMaxPolls;
+        if (ta.no_copy && !ta.tma) return QEXT_E_INVAL;  // the test needs the bulk-copy path
         const size_t smem = size_t(nbuf) * 2 * T * s.wpb * 4;
         const int ti = (T == 32 ? 0 : T == 64 ? 1 : 2) + 3 * int(nbuf - 1);
         int &occ = cache.occ_tiled[ti];
@@ -271,6 +279,7 @@ static StreamArgs stream_args(const qext_plan *p, const uint32_t *x, const uint3
         s.taps[i] = p->taps[i];
         s.tap_mul[i] = i < int(p->ntaps) ? 1u << (p->taps[i] & 31u) : 0u;
     }
+    s.status = device_status_ptr();
     return s;
 }
 

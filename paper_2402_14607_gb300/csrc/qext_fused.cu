@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(kConsumers + kProducers) extract_fused_kernel(
         for (uint64_t tile = blockIdx.x; tile < fa.ntiles; tile += gridDim.x, ++k) {
             const uint32_t b = k & 1u, use = k >> 1;
             if (use > 0 && !mbar_wait_bounded(&empty[b], (use - 1) & 1u)) {
-                record_status(QEXT_E_TIMEOUT);
+                record_status(s.status, QEXT_E_TIMEOUT);
                 return;
             }
             uint32_t *xs = smem + 2 * b * tw, *ys = xs + tw;
@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(kConsumers + kProducers) extract_fused_kernel(
         for (uint64_t tile = blockIdx.x; tile < fa.ntiles; tile += gridDim.x, ++k) {
             const uint32_t b = k & 1u, use = k >> 1;
             if (!mbar_wait_bounded(&full[b], use & 1u)) {
-                record_status(QEXT_E_TIMEOUT);
+                record_status(s.status, QEXT_E_TIMEOUT);
                 return;
             }
             const uint32_t *xs = smem + 2 * b * tw, *ys = xs + tw;

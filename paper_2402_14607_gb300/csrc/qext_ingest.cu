@@ -8,8 +8,9 @@
 #include "qext_internal.h"
 
 // Sticky device status (QEXT_OK or a negative QEXT_E_* code) written by
-// kernels that give up a bounded wait; read and cleared by the host.
-__device__ int qext_device_status_word = 0;
+// kernels that give up a bounded wait; read and cleared by the host.  Kernels
+// of the other translation units receive its device address (device_status_ptr).
+static __device__ int qext_device_status_word = 0;
 
 namespace {
 
@@ -146,6 +147,18 @@ int launch_pack(uint32_t b, const uint16_t *samples, uint64_t nsamples, uint32_t
         pack_kernel<<<grid_for(nperiods), 256, 0, st>>>(samples, nsamples, b, S, L, out, nwords, nperiods);
     }
     return cudaGetLastError() == cudaSuccess ? QEXT_OK : QEXT_E_CUDA;
+}
+
+int *device_status_ptr() {
+    static int *ptrs[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    if (!ptrs[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, qext_device_status_word) != cudaSuccess) return nullptr;
+        ptrs[dev] = static_cast<int *>(p);
+    }
+    return ptrs[dev];
 }
 
 int read_device_status(int *status) {

@@ -52,6 +52,9 @@ int launch_fused_samples(uint32_t q, uint32_t b, const qxd::StreamArgs &s, const
                          uint64_t nsamples, qext_cuda_stream stream);
 int launch_pack(uint32_t b, const uint16_t *samples, uint64_t nsamples, uint32_t *out, qext_cuda_stream stream);
 int read_device_status(int *status);
+// Device address of the status word of the current device (null if the
+// lookup failed); kernels record QEXT_E_* codes there.
+int *device_status_ptr();
 
 // Batched launch from caller-provided device tables / pinned host staging
 // (qext_batch.cu); used by the serving loop.

@@ -249,6 +249,7 @@ int qext_stream_push(qext_stream *s, const uint32_t *x, const uint32_t *y, uint6
                 g.s.taps[i] = s->plan->taps[i];
                 g.s.tap_mul[i] = i < int(s->plan->ntaps) ? 1u << (s->plan->taps[i] & 31u) : 0u;
             }
+            g.s.status = qext::device_status_ptr();
             g.tx = s->tail[s->cur][0];
             g.ty = s->tail[s->cur][1];
             g.t = t;

@@ -30,6 +30,7 @@ QEXT_F_DIRECT = 0x1
 QEXT_F_NBUF1 = 0x2
 QEXT_F_TILE32 = 0x4
 QEXT_F_TILE64 = 0x8
+QEXT_F_TEST_TIMEOUT = 0x10
 
 _lib = None
 

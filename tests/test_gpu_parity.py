@@ -245,3 +245,23 @@ def test_pipeline_host_to_host_matches_oracle(q, b, nblocks, chunk):
     assert (got[nout:] == 0xFFFFFFFF).all()
     assert (got[:nout] == oracle_extract(plan, ox, oy, nblocks)).all()
     pp.close()
+
+
+def test_bounded_wait_times_out_and_context_survives():
+    """Failure detection without a fault: the tile barrier is armed but no
+    copy is issued, so every CTA's bounded wait runs out; the kernel records
+    QEXT_E_TIMEOUT and returns, the host reads the status, and the next
+    extraction on the same context is correct."""
+    plan = plan_for(16, 64)
+    nb = 4096
+    x = workloads.random_words(71, nb * 32)
+    y = workloads.random_words(72, nb * 32)
+    tx, ty = dev_words(x), dev_words(y)
+    out = torch.zeros(nb // 2, dtype=torch.int32, device="cuda")
+    assert qext.qext_device_status() == qext.QEXT_OK
+    qext.qext_extract_ex(plan, tx, ty, nb, out, None, qext.QEXT_F_TEST_TIMEOUT)
+    torch.cuda.synchronize()
+    assert qext.qext_device_status() == qext.QEXT_E_TIMEOUT
+    assert qext.qext_device_status() == qext.QEXT_OK          # read clears it
+    assert (gpu_extract(plan, x, y, nb) == oracle_extract(plan, x, y, nb)).all()
+    assert qext.qext_device_status() == qext.QEXT_OK
