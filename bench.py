@@ -404,9 +404,10 @@ def run_gpu(args):
         per_kernel = {"pack_x_plus_y": round(statistics.mean(pack_ms), 4), "extract": round(statistics.mean(ext_ms), 4)}
     else:
         # the fused kernel reads both sample arrays once and writes the output
-        dom = {"kernel": "extract_fused_kernel<16,12> (fused ingest)", "bytes": 2 * ns * 2 + out_words * 4,
-               "t": ext_s, "traffic": measured_traffic("fused_ingest_q16_b12_large_single_stream",
-                                                       ["qext_fused.cu", "qext_block.cuh", "qext_device.cuh"])}
+        dom = {"kernel": "extract_tiled_kernel<16,12> (fused ingest: TMA raw tiles packed in place)",
+               "bytes": 2 * ns * 2 + out_words * 4, "t": ext_s,
+               "traffic": measured_traffic("fused_ingest_q16_b12_large_single_stream",
+                                           ["qext_extract.cu", "qext_block.cuh", "qext_device.cuh"])}
         per_kernel = {"extract_samples": round(statistics.mean(ext_ms), 4)}
     achieved = dom["bytes"] / dom["t"] / 1e9
     roofline = {"bound": "hbm", "kernel": dom["kernel"], "achieved": round(achieved, 1), "peak": peak,

@@ -173,6 +173,14 @@ int qext_extract_ex(const qext_plan *p, const uint32_t *x, const uint32_t *y, ui
 int qext_extract_samples(const qext_plan *p, uint32_t b, const uint16_t *x_samples, const uint16_t *y_samples,
                          uint64_t nsamples, uint64_t nblocks, uint32_t *out, qext_cuda_stream stream);
 
+/* Flag of qext_extract_samples_ex: q = 4, 16 with warp-specialised CTAs
+ * (producer warps pack from global memory while consumer warps extract)
+ * instead of TMA-loaded raw tiles packed in place.  Same output. */
+#define QEXT_F_WARP_SPECIALIZED 0x20u
+int qext_extract_samples_ex(const qext_plan *p, uint32_t b, const uint16_t *x_samples, const uint16_t *y_samples,
+                            uint64_t nsamples, uint64_t nblocks, uint32_t *out, qext_cuda_stream stream,
+                            uint32_t flags);
+
 /*
  * qext_pack_samples -- ingest: raw ADC samples to a packed stream.  Sample s
  * (b bits, the low bits of samples[s]) occupies stream bits [s*b, (s+1)*b)

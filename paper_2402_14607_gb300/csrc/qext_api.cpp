@@ -30,7 +30,14 @@ int qext_extract(const qext_plan *p, const uint32_t *x, const uint32_t *y, uint6
 
 int qext_extract_samples(const qext_plan *p, uint32_t b, const uint16_t *x_samples, const uint16_t *y_samples,
                          uint64_t nsamples, uint64_t nblocks, uint32_t *out, qext_cuda_stream stream) {
+    return qext_extract_samples_ex(p, b, x_samples, y_samples, nsamples, nblocks, out, stream, 0);
+}
+
+int qext_extract_samples_ex(const qext_plan *p, uint32_t b, const uint16_t *x_samples, const uint16_t *y_samples,
+                            uint64_t nsamples, uint64_t nblocks, uint32_t *out, qext_cuda_stream stream,
+                            uint32_t flags) {
     if (!p) return QEXT_E_INVAL;
+    if (flags & ~uint32_t(QEXT_F_WARP_SPECIALIZED)) return QEXT_E_INVAL;
     if (!p->gpu_supported) return QEXT_E_UNSUPPORTED;
     if (b != 8 && b != 12 && b != 16) return QEXT_E_UNSUPPORTED;
     if (p->q != 4 && p->q != 16 && p->q != 64) return QEXT_E_UNSUPPORTED;
@@ -38,7 +45,7 @@ int qext_extract_samples(const qext_plan *p, uint32_t b, const uint16_t *x_sampl
     if (nsamples > UINT64_MAX / 16 || nblocks > (nsamples * b) / p->n) return QEXT_E_INVAL;
     if (!x_samples || !y_samples || !out || !aligned(x_samples, 16) || !aligned(y_samples, 16) || !aligned(out, 4))
         return QEXT_E_INVAL;
-    return qext::launch_extract_samples(p, b, x_samples, y_samples, nsamples, nblocks, out, stream, 0);
+    return qext::launch_extract_samples(p, b, x_samples, y_samples, nsamples, nblocks, out, stream, flags);
 }
 
 int qext_pack_samples(uint32_t b, const uint16_t *samples, uint64_t nsamples, uint32_t *out,

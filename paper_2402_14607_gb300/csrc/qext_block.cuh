@@ -334,4 +334,50 @@ __device__ __forceinline__ void pack_tile(const uint16_t *__restrict__ sx, const
     }
 }
 
+// Fused ingest from a raw-sample tile already in shared memory: the periods
+// of 8 samples covering stream words [w0, w0 + nw) of each source (raw_x[j],
+// raw_y[j] = period p0 + j) are packed IN PLACE, the packed words landing over
+// the front of the same buffers (tile word i at raw_x[0..], raw_y[0..]).
+// Rounds of kPer periods per thread: every thread loads its round's periods,
+// the CTA synchronises, then stores.  A round's stores reach at most byte
+// (WP*4) * (periods so far), which never passes the raw bytes already loaded
+// (WP*4 <= 16 bytes per period), so no period is overwritten before it is read.
+template <int B>
+__device__ __forceinline__ void pack_tile_in_place(uint4 *raw_x, uint4 *raw_y, uint32_t phi, uint32_t nw,
+                                                   uint32_t tid, uint32_t nthreads) {
+    constexpr uint32_t WP = PeriodOf<B>::kWords;
+    constexpr int kPer = 2;
+    const uint32_t nper = (phi + nw + WP - 1) / WP;
+    uint32_t *dx = reinterpret_cast<uint32_t *>(raw_x), *dy = reinterpret_cast<uint32_t *>(raw_y);
+    for (uint32_t base = 0; base < nper; base += kPer * nthreads) {
+        uint4 vx[kPer], vy[kPer];
+#pragma unroll
+        for (int r = 0; r < kPer; ++r) {
+            const uint32_t j = base + tid + r * nthreads;
+            if (j < nper) {
+                vx[r] = raw_x[j];
+                vy[r] = raw_y[j];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < kPer; ++r) {
+            const uint32_t j = base + tid + r * nthreads;
+            if (j < nper) {
+                uint32_t wx[WP], wy[WP];
+                pack_period8<B>(vx[r], wx);
+                pack_period8<B>(vy[r], wy);
+                const uint32_t lw = WP * j - phi;
+#pragma unroll
+                for (uint32_t i = 0; i < WP; ++i)
+                    if (lw + i < nw) {
+                        dx[lw + i] = wx[i];
+                        dy[lw + i] = wy[i];
+                    }
+            }
+        }
+    }
+    __syncthreads();
+}
+
 }  // namespace qxd

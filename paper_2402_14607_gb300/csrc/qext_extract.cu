@@ -40,6 +40,7 @@ struct TileArgs {
     int vec;        // wpb % 4 == 0: 16-byte shared-memory reads
     uint32_t max_polls;  // bound of every mbarrier wait
     int no_copy;         // test of the timeout path: arm the barrier, issue no copy
+    uint32_t raw_periods;  // fused ingest: raw buffer capacity per source, in periods of 8 samples
 };
 
 template <int Q>
@@ -81,6 +82,7 @@ __global__ void __launch_bounds__(kThreads) extract_tiled_kernel(const TileArgs 
     };
 
     uint64_t tile = blockIdx.x;
+    uint32_t raw_uses = 0;  // fused ingest: completed uses of full[0]
     if (tid == 0 && ta.tma && tile < ta.ntiles && full_tile(tile)) issue(tile, 0);
     for (uint32_t k = 0; tile < ta.ntiles; ++k, tile += gridDim.x) {
         const int b = ta.nbuf > 1 ? int(k & 1u) : 0;
@@ -94,9 +96,40 @@ __global__ void __launch_bounds__(kThreads) extract_tiled_kernel(const TileArgs 
         }
         uint32_t *xs = bufs[b], *ys = bufs[b] + tw;
         if constexpr (B != 0) {
+            // fused ingest: the tile's raw samples arrive by TMA and are packed
+            // in place (one buffer per CTA), else they are packed from global
+            // memory (the stream's last tiles)
+            constexpr uint32_t WP = PeriodOf<B>::kWords;
             const uint64_t nb = s.nblocks - tile * T < T ? s.nblocks - tile * T : T;
-            pack_tile<B>(ta.sx, ta.sy, ta.nsamples, tile * tw, uint32_t(nb * s.wpb), xs, ys, tid, nthreads);
-            __syncthreads();
+            const uint32_t nw = uint32_t(nb * s.wpb);
+            const uint64_t w0 = tile * tw, p0 = w0 / WP;
+            const uint32_t phi = uint32_t(w0 - p0 * WP), nper = (phi + nw + WP - 1) / WP;
+            // raw buffers of raw_periods periods each, or (no raw staging) the
+            // packed tile's usual x / y halves
+            uint4 *raw_x = reinterpret_cast<uint4 *>(smem);
+            uint4 *raw_y = ta.raw_periods ? raw_x + ta.raw_periods : reinterpret_cast<uint4 *>(smem + tw);
+            xs = reinterpret_cast<uint32_t *>(raw_x);
+            ys = reinterpret_cast<uint32_t *>(raw_y);
+            bool packed = false;
+            if (ta.raw_periods && nper <= ta.raw_periods && 8 * (p0 + nper) <= ta.nsamples) {
+                if (tid == 0) {
+                    mbar_expect_tx(&full[0], 32u * nper);
+                    tma_load_1d(raw_x, ta.sx + 8 * p0, 16u * nper, &full[0]);
+                    tma_load_1d(raw_y, ta.sy + 8 * p0, 16u * nper, &full[0]);
+                }
+                const bool ok = mbar_wait_bounded(&full[0], raw_uses & 1u, ta.max_polls);
+                ++raw_uses;
+                if (!__syncthreads_and(ok)) {
+                    if (tid == 0) record_status(s.status, QEXT_E_TIMEOUT);
+                    return;
+                }
+                pack_tile_in_place<B>(raw_x, raw_y, phi, nw, tid, nthreads);
+                packed = true;
+            }
+            if (!packed) {
+                pack_tile<B>(ta.sx, ta.sy, ta.nsamples, w0, nw, xs, ys, tid, nthreads);
+                __syncthreads();
+            }
         } else if (ta.tma && full_tile(tile)) {
             const uint32_t use = ta.nbuf > 1 ? (k >> 1) : k;
             const bool ok = mbar_wait_bounded(&full[b], use & 1u, ta.max_polls);
@@ -183,7 +216,7 @@ __global__ void __launch_bounds__(kThreads) extract_direct_kernel(const StreamAr
 
 struct LaunchCache {
     int sms = 0;
-    int occ_tiled[6] = {0, 0, 0, 0, 0, 0};  // by T (32, 64, 128) and buffers (1, 2)
+    int occ_tiled[12] = {};  // by T (32, 64, 128), buffers (1, 2) and fused ingest
     int occ_direct = 0;
     bool attr = false;
 };
@@ -204,7 +237,16 @@ int launch_q(const StreamArgs &s, const uint16_t *sx, const uint16_t *sy, uint64
     }
     constexpr int TPB = QTraits<Q>::TPB;
     // tile size: the largest T (multiple of 32, T * TPB <= kThreads) whose
-    // buffers fit the per-CTA budget, double-buffered if possible
+    // buffers fit the per-CTA budget, double-buffered if possible; the fused
+    // ingest keeps one raw-sample buffer per source (packed in place)
+    uint32_t raw_periods = 0;
+    if constexpr (B != 0) {
+        constexpr uint32_t WP = PeriodOf<B>::kWords;
+        const uint32_t T0 = kThreads / TPB;
+        raw_periods = (T0 * s.wpb + WP - 1) / WP + 2;
+        const size_t smem = size_t(2) * 16 * raw_periods;
+        if (smem > size_t(kSmemBudget)) raw_periods = 0;
+    }
     uint32_t T = 0, nbuf = 0;
     for (uint32_t t = kThreads / TPB < t_max ? kThreads / TPB : t_max; t >= 32 && !T; t /= 2)
         for (uint32_t nb = nb_max; nb >= 1 && !T; --nb)
@@ -234,8 +276,18 @@ int launch_q(const StreamArgs &s, const uint16_t *sx, const uint16_t *sy, uint64
         ta.no_copy = B == 0 && (flags & QEXT_F_TEST_TIMEOUT) ? 1 : 0;
         ta.max_polls = ta.no_copy ? 256u : kMaxPolls;
         if (ta.no_copy && !ta.tma) return QEXT_E_INVAL;  // the test needs the bulk-copy path
-        const size_t smem = size_t(nbuf) * 2 * T * s.wpb * 4;
-        const int ti = (T == 32 ? 0 : T == 64 ? 1 : 2) + 3 * int(nbuf - 1);
+        ta.raw_periods = 0;
+        size_t smem = size_t(nbuf) * 2 * T * s.wpb * 4;
+        if constexpr (B != 0) {
+            nbuf = 1;
+            ta.nbuf = 1;
+            T = kThreads / TPB;
+            ta.T = T;
+            ta.ntiles = (s.nblocks + T - 1) / T;
+            ta.raw_periods = raw_periods;
+            smem = raw_periods ? size_t(2) * 16 * raw_periods : size_t(2) * T * s.wpb * 4;
+        }
+        const int ti = (T == 32 ? 0 : T == 64 ? 1 : 2) + 3 * int(nbuf - 1) + (B != 0 ? 6 : 0);
         int &occ = cache.occ_tiled[ti];
         if (!occ) {
             if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, extract_tiled_kernel<Q, B>, int(T * TPB), smem) !=
@@ -303,6 +355,8 @@ template <int B>
 static int launch_samples_b(const qext_plan *p, const StreamArgs &s, const uint16_t *sx, const uint16_t *sy,
                             uint64_t nsamples, cudaStream_t st, uint32_t flags) {
     switch (p->q) {
+        case 4: return launch_q<4, B>(s, sx, sy, nsamples, st, flags);
+        case 16: return launch_q<16, B>(s, sx, sy, nsamples, st, flags);
         case 64: return launch_q<64, B>(s, sx, sy, nsamples, st, flags);
         default: return QEXT_E_UNSUPPORTED;
     }
@@ -312,7 +366,8 @@ int launch_extract_samples(const qext_plan *p, uint32_t b, const uint16_t *sx, c
                            uint64_t nsamples, uint64_t nblocks, uint32_t *out, qext_cuda_stream stream,
                            uint32_t flags) {
     const StreamArgs s = stream_args(p, nullptr, nullptr, nblocks, out);
-    if (p->q == 4 || p->q == 16) return launch_fused_samples(p->q, b, s, sx, sy, nsamples, stream);
+    if ((flags & QEXT_F_WARP_SPECIALIZED) && (p->q == 4 || p->q == 16))
+        return launch_fused_samples(p->q, b, s, sx, sy, nsamples, stream);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     switch (b) {
         case 8: return launch_samples_b<8>(p, s, sx, sy, nsamples, st, flags);

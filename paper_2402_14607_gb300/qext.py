@@ -31,6 +31,7 @@ QEXT_F_NBUF1 = 0x2
 QEXT_F_TILE32 = 0x4
 QEXT_F_TILE64 = 0x8
 QEXT_F_TEST_TIMEOUT = 0x10
+QEXT_F_WARP_SPECIALIZED = 0x20
 
 _lib = None
 
@@ -88,6 +89,7 @@ def lib():
     L.qext_extract_ex.argtypes = [vp, vp, vp, u64, vp, vp, u32]
     L.qext_pack_samples.argtypes = [u32, vp, u64, vp, vp]
     L.qext_extract_samples.argtypes = [vp, u32, vp, vp, u64, u64, vp, vp]
+    L.qext_extract_samples_ex.argtypes = [vp, u32, vp, vp, u64, u64, vp, vp, u32]
     L.qext_device_status.argtypes = [P(i32)]
     L.qext_stream_create.argtypes = [vp, P(vp)]
     L.qext_stream_destroy.argtypes = [vp]
@@ -119,7 +121,7 @@ def lib():
     L.qext_pipeline_destroy.argtypes = [vp]
     L.qext_pipeline_run.argtypes = [vp, vp, vp, u64, u64, vp]
     for name in ["qext_plan_create", "qext_destroy", "qext_plan_info", "qext_alg1_params", "qext_extract",
-                 "qext_extract_ex", "qext_extract_samples",
+                 "qext_extract_ex", "qext_extract_samples", "qext_extract_samples_ex",
                  "qext_pack_samples", "qext_device_status", "qext_stream_create", "qext_stream_destroy",
                  "qext_stream_info", "qext_stream_push", "qext_stream_flush", "qext_stream_save",
                  "qext_stream_restore", "qext_batch_create", "qext_batch_destroy", "qext_batch_get_config",
@@ -223,6 +225,12 @@ def qext_extract_samples(plan: Plan, b: int, x_samples, y_samples, nsamples: int
                          stream=None) -> None:
     _check(lib().qext_extract_samples(plan.handle, b, _ptr(x_samples), _ptr(y_samples), nsamples, nblocks,
                                       _ptr(out), _stream(stream)), "qext_extract_samples")
+
+
+def qext_extract_samples_ex(plan: Plan, b: int, x_samples, y_samples, nsamples: int, nblocks: int, out,
+                            stream=None, flags: int = 0) -> None:
+    _check(lib().qext_extract_samples_ex(plan.handle, b, _ptr(x_samples), _ptr(y_samples), nsamples, nblocks,
+                                         _ptr(out), _stream(stream), flags), "qext_extract_samples_ex")
 
 
 def qext_pack_samples(b: int, samples, nsamples: int, out, stream=None) -> None:

@@ -154,7 +154,8 @@ def test_config_large_single_stream_sampled():
     (16, 12, 1000, 0), (16, 12, 4133, 5), (16, 12, 129, 1), (4, 8, 4099, 0), (4, 12, 777, 3), (4, 16, 64, 0),
     (64, 12, 300, 1), (64, 16, 129, 0), (64, 8, 33, 2), (16, 8, 257, 0), (16, 16, 100, 7), (16, 12, 1, 0),
 ])
-def test_extract_samples_matches_oracle(q, b, nblocks, extra):
+@pytest.mark.parametrize("flags", [0, qext.QEXT_F_WARP_SPECIALIZED], ids=["tma_in_place", "warp_specialized"])
+def test_extract_samples_matches_oracle(q, b, nblocks, extra, flags):
     """Fused ingest + extraction from raw b-bit samples (garbage above b) against
     the oracle's packing followed by its extraction, every output bit."""
     plan = plan_for(q, 64)
@@ -167,7 +168,7 @@ def test_extract_samples_matches_oracle(q, b, nblocks, extra):
     gy = torch.from_numpy((s_y | junk).view(np.int16)).cuda()
     nout = -(-nblocks * q // 32)
     out = torch.full((nout + 4,), -1, dtype=torch.int32, device="cuda")
-    qext.qext_extract_samples(plan, b, gx, gy, ns, nblocks, out)
+    qext.qext_extract_samples_ex(plan, b, gx, gy, ns, nblocks, out, None, flags)
     torch.cuda.synchronize()
     got = host_words(out)
     assert (got[nout:] == 0xFFFFFFFF).all()
