@@ -404,10 +404,10 @@ def run_gpu(args):
         per_kernel = {"pack_x_plus_y": round(statistics.mean(pack_ms), 4), "extract": round(statistics.mean(ext_ms), 4)}
     else:
         # the fused kernel reads both sample arrays once and writes the output
-        dom = {"kernel": "extract_tiled_kernel<16,12> (fused ingest: TMA raw tiles packed in place)",
+        dom = {"kernel": "extract_raw_kernel<16,12> (per-warp TMA pipelines, samples packed in registers)",
                "bytes": 2 * ns * 2 + out_words * 4, "t": ext_s,
-               "traffic": measured_traffic("fused_ingest_q16_b12_large_single_stream",
-                                           ["qext_extract.cu", "qext_block.cuh", "qext_device.cuh"])}
+               "traffic": measured_traffic("raw_ingest_q16_b12_large_single_stream",
+                                           ["qext_extract_raw.cu", "qext_block.cuh", "qext_device.cuh"])}
         per_kernel = {"extract_samples": round(statistics.mean(ext_ms), 4)}
     achieved = dom["bytes"] / dom["t"] / 1e9
     roofline = {"bound": "hbm", "kernel": dom["kernel"], "achieved": round(achieved, 1), "peak": peak,
@@ -435,11 +435,30 @@ def run_gpu(args):
         qext.qext_pipeline_run(pp, h_sx, h_sy, ns, spec.nblocks, h_out)
     te = max_over_ranks(time.perf_counter() - t0, world)
     e2e_ok = bool((h_out.numpy().view(np.uint32) == gpu_out).all())
+    # the host link: one step's input copied host -> device alone (pinned,
+    # the same bytes), the bound of the end-to-end number
+    d_sx = torch.empty_like(h_sx, device=dev)
+    d_sy = torch.empty_like(h_sy, device=dev)
+    link = []
+    for _ in range(3):
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record()
+        d_sx.copy_(h_sx, non_blocking=True)
+        d_sy.copy_(h_sy, non_blocking=True)
+        c1.record()
+        torch.cuda.synchronize()
+        link.append(c0.elapsed_time(c1) * 1e-3)
+    link_gbs = 2 * ns * 2 / statistics.median(link) / 1e9
+    del d_sx, d_sy
+    link_bound = bits_per_step / (2 * ns * 2 / (link_gbs * 1e9)) / 1e9
     e2e = {"value": round(world * args.steps * bits_per_step / te / 1e9, 3), "unit": UNIT,
            "h2d_bytes_per_step": 2 * ns * 2, "d2h_bytes_per_step": out_words * 4,
            "path": "qext_pipeline_run: pinned host samples -> H2D chunks -> qext_extract_samples -> D2H, "
                    "three CUDA streams overlapped, chunk %d blocks" % qext.qext_pipeline_info(pp)["chunk_blocks"],
-           "matches_device_path": e2e_ok}
+           "matches_device_path": e2e_ok,
+           "h2d_link_gbs": round(link_gbs, 1),
+           "link_bound_value": round(link_bound, 3),
+           "frac_of_link_bound": round(args.steps * bits_per_step / te / 1e9 / link_bound, 4)}
     pp.close()
     del h_sx, h_sy
 

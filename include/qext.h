@@ -173,10 +173,23 @@ int qext_extract_ex(const qext_plan *p, const uint32_t *x, const uint32_t *y, ui
 int qext_extract_samples(const qext_plan *p, uint32_t b, const uint16_t *x_samples, const uint16_t *y_samples,
                          uint64_t nsamples, uint64_t nblocks, uint32_t *out, qext_cuda_stream stream);
 
-/* Flag of qext_extract_samples_ex: q = 4, 16 with warp-specialised CTAs
- * (producer warps pack from global memory while consumer warps extract)
- * instead of TMA-loaded raw tiles packed in place.  Same output. */
+/*
+ * qext_extract_samples_ex -- qext_extract_samples with launch options (0 =
+ * the default path).  The default for q = 4, 16 with n_p = 64 runs one copy
+ * pipeline per warp: each warp TMA-copies the raw samples of 32 blocks into
+ * its own shared-memory buffer and every lane packs its block's samples in
+ * registers.  Other shapes use CTA-wide tiles of raw samples, TMA-copied and
+ * packed in place in shared memory.  The output is identical for every flag
+ * combination; INVAL for unknown flag bits.
+ */
+/* q = 4, 16: warp-specialised CTAs (producer warps pack from global memory
+ * into shared memory while consumer warps extract). */
 #define QEXT_F_WARP_SPECIALIZED 0x20u
+/* Two raw-sample buffers (per warp, or per CTA with CTA-wide tiles), the next
+ * copy issued one whole tile ahead (more shared memory, fewer warps per SM). */
+#define QEXT_F_RAW_PREFETCH 0x40u
+/* CTA-wide tiles packed in place even where the per-warp kernel applies. */
+#define QEXT_F_CTA_TILES 0x80u
 int qext_extract_samples_ex(const qext_plan *p, uint32_t b, const uint16_t *x_samples, const uint16_t *y_samples,
                             uint64_t nsamples, uint64_t nblocks, uint32_t *out, qext_cuda_stream stream,
                             uint32_t flags);

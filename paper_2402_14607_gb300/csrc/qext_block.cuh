@@ -377,6 +377,7 @@ __device__ __forceinline__ void pack_tile_in_place(uint4 *raw_x, uint4 *raw_y, u
             }
         }
     }
+    fence_proxy_async_smem();  // the buffer is refilled by a bulk copy after this tile
     __syncthreads();
 }
 

@@ -41,6 +41,7 @@ struct TileArgs {
     uint32_t max_polls;  // bound of every mbarrier wait
     int no_copy;         // test of the timeout path: arm the barrier, issue no copy
     uint32_t raw_periods;  // fused ingest: raw buffer capacity per source, in periods of 8 samples
+    int raw_prefetch;      // fused ingest: two raw buffers, next tile's copy issued before computing
 };
 
 template <int Q>
@@ -63,7 +64,7 @@ __global__ void __launch_bounds__(kThreads) extract_tiled_kernel(const TileArgs 
     const uint32_t T = ta.T;
     const uint32_t tw = T * s.wpb;  // words per tile per source
     const uint32_t nthreads = T * TPB;
-    uint32_t *bufs[2] = {smem, smem + (ta.nbuf > 1 ? 2 * tw : 0)};
+    uint32_t *const buf1 = smem + (ta.nbuf > 1 ? 2 * tw : 0);  // second tile buffer
 
     if (tid == 0) {
         mbar_init(&full[0], 1);
@@ -77,12 +78,33 @@ __global__ void __launch_bounds__(kThreads) extract_tiled_kernel(const TileArgs 
         const uint32_t bytes = tw * 4u;
         mbar_expect_tx(&full[b], 2u * bytes);
         if (ta.no_copy) return;  // the completion never comes: the wait must give up
-        tma_load_1d(bufs[b], s.x + t * tw, bytes, &full[b]);
-        tma_load_1d(bufs[b] + tw, s.y + t * tw, bytes, &full[b]);
+        uint32_t *dst = b ? buf1 : smem;
+        tma_load_1d(dst, s.x + t * tw, bytes, &full[b]);
+        tma_load_1d(dst + tw, s.y + t * tw, bytes, &full[b]);
     };
 
     uint64_t tile = blockIdx.x;
-    uint32_t raw_uses = 0;  // fused ingest: completed uses of full[0]
+    uint32_t raw_uses0 = 0, raw_uses1 = 0;  // fused ingest: completed uses of full[0], full[1]
+    bool prefetched = false;         // fused ingest (thread 0): this tile's copy was issued last iteration
+    // fused ingest: the raw samples of tile t fit the raw buffer and lie in the array
+    auto raw_tile_ok = [&](uint64_t t) {
+        if (!ta.raw_periods || B == 0) return false;
+        constexpr uint32_t WP = B == 12 ? 3u : B == 8 ? 2u : 4u;
+        const uint64_t nbt = s.nblocks - t * T < T ? s.nblocks - t * T : T;
+        const uint64_t w0t = t * tw, p0t = w0t / WP;
+        const uint32_t np = uint32_t((w0t - p0t * WP + nbt * s.wpb + WP - 1) / WP);
+        return np <= ta.raw_periods && 8 * (p0t + np) <= ta.nsamples;
+    };
+    auto issue_raw = [&](uint64_t t, int rbuf) {
+        constexpr uint32_t WP = B == 12 ? 3u : B == 8 ? 2u : 4u;
+        const uint64_t nbt = s.nblocks - t * T < T ? s.nblocks - t * T : T;
+        const uint64_t w0t = t * tw, p0t = w0t / WP;
+        const uint32_t np = uint32_t((w0t - p0t * WP + nbt * s.wpb + WP - 1) / WP);
+        uint4 *rx = reinterpret_cast<uint4 *>(smem) + size_t(rbuf) * 2 * ta.raw_periods, *ry = rx + ta.raw_periods;
+        mbar_expect_tx(&full[rbuf], 32u * np);
+        tma_load_1d(rx, ta.sx + 8 * p0t, 16u * np, &full[rbuf]);
+        tma_load_1d(ry, ta.sy + 8 * p0t, 16u * np, &full[rbuf]);
+    };
     if (tid == 0 && ta.tma && tile < ta.ntiles && full_tile(tile)) issue(tile, 0);
     for (uint32_t k = 0; tile < ta.ntiles; ++k, tile += gridDim.x) {
         const int b = ta.nbuf > 1 ? int(k & 1u) : 0;
@@ -94,7 +116,7 @@ __global__ void __launch_bounds__(kThreads) extract_tiled_kernel(const TileArgs 
                 issue(tile, 0);  // single buffer: free since the last __syncthreads
             }
         }
-        uint32_t *xs = bufs[b], *ys = bufs[b] + tw;
+        uint32_t *xs = b ? buf1 : smem, *ys = xs + tw;
         if constexpr (B != 0) {
             // fused ingest: the tile's raw samples arrive by TMA and are packed
             // in place (one buffer per CTA), else they are packed from global
@@ -103,24 +125,30 @@ __global__ void __launch_bounds__(kThreads) extract_tiled_kernel(const TileArgs 
             const uint64_t nb = s.nblocks - tile * T < T ? s.nblocks - tile * T : T;
             const uint32_t nw = uint32_t(nb * s.wpb);
             const uint64_t w0 = tile * tw, p0 = w0 / WP;
-            const uint32_t phi = uint32_t(w0 - p0 * WP), nper = (phi + nw + WP - 1) / WP;
+            const uint32_t phi = uint32_t(w0 - p0 * WP);
             // raw buffers of raw_periods periods each, or (no raw staging) the
             // packed tile's usual x / y halves
-            uint4 *raw_x = reinterpret_cast<uint4 *>(smem);
+            const int rb = ta.raw_prefetch ? int(k & 1u) : 0;  // raw buffer of this tile
+            uint4 *raw_x = reinterpret_cast<uint4 *>(smem) + size_t(rb) * 2 * ta.raw_periods;
             uint4 *raw_y = ta.raw_periods ? raw_x + ta.raw_periods : reinterpret_cast<uint4 *>(smem + tw);
             xs = reinterpret_cast<uint32_t *>(raw_x);
             ys = reinterpret_cast<uint32_t *>(raw_y);
             bool packed = false;
-            if (ta.raw_periods && nper <= ta.raw_periods && 8 * (p0 + nper) <= ta.nsamples) {
+            if (raw_tile_ok(tile)) {
                 if (tid == 0) {
-                    mbar_expect_tx(&full[0], 32u * nper);
-                    tma_load_1d(raw_x, ta.sx + 8 * p0, 16u * nper, &full[0]);
-                    tma_load_1d(raw_y, ta.sy + 8 * p0, 16u * nper, &full[0]);
+                    if (!prefetched) issue_raw(tile, rb);
+                    prefetched = ta.raw_prefetch && next < ta.ntiles && raw_tile_ok(next);
+                    if (prefetched) issue_raw(next, rb ^ 1);
                 }
-                const bool ok = mbar_wait_bounded(&full[0], raw_uses & 1u, ta.max_polls);
-                ++raw_uses;
+                const uint32_t use = rb ? raw_uses1++ : raw_uses0++;
+                const bool ok = mbar_wait_bounded(&full[rb], use & 1u, ta.max_polls);
                 if (!__syncthreads_and(ok)) {
-                    if (tid == 0) record_status(s.status, QEXT_E_TIMEOUT);
+                    if (tid == 0) {
+                        record_status(s.status, QEXT_E_TIMEOUT);
+                        // give the copies in flight a bounded chance to land
+                        mbar_wait_bounded(&full[rb], use & 1u, ta.max_polls);
+                        if (prefetched) mbar_wait_bounded(&full[rb ^ 1], (rb ? raw_uses0 : raw_uses1) & 1u, ta.max_polls);
+                    }
                     return;
                 }
                 pack_tile_in_place<B>(raw_x, raw_y, phi, nw, tid, nthreads);
@@ -160,17 +188,17 @@ __global__ void __launch_bounds__(kThreads) extract_tiled_kernel(const TileArgs 
         uint64_t v = 0;
         if constexpr (Q == 64) {
             const uint32_t part = tid % TPB;
-            uint64_t A = 0, B = 0, C = 0;
+            uint64_t A = 0, Bm = 0, C = 0;
             if (blk < s.nblocks) {
                 const uint32_t *xb = xs + lb * s.wpb, *yb = ys + lb * s.wpb;
                 A = half_product64<0>(xb, yb, s.wpb, ta.vec, tid, part, TPB, ta.mu);
-                B = half_product64<1>(xb, yb, s.wpb, ta.vec, tid, part, TPB, ta.mu);
+                Bm = half_product64<1>(xb, yb, s.wpb, ta.vec, tid, part, TPB, ta.mu);
                 C = half_product64<2>(xb, yb, s.wpb, ta.vec, tid, part, TPB, ta.mu);
             }
             A ^= __shfl_xor_sync(0xffffffffu, A, 1);
-            B ^= __shfl_xor_sync(0xffffffffu, B, 1);
+            Bm ^= __shfl_xor_sync(0xffffffffu, Bm, 1);
             C ^= __shfl_xor_sync(0xffffffffu, C, 1);
-            if (blk < s.nblocks) v = combine_q64(A, B, C, s) & mask_m(s.m);
+            if (blk < s.nblocks) v = combine_q64(A, Bm, C, s) & mask_m(s.m);
             if (part == 0) vals[lb] = v;
         } else {
             if (blk < s.nblocks)
@@ -216,7 +244,7 @@ __global__ void __launch_bounds__(kThreads) extract_direct_kernel(const StreamAr
 
 struct LaunchCache {
     int sms = 0;
-    int occ_tiled[12] = {};  // by T (32, 64, 128), buffers (1, 2) and fused ingest
+    int occ_tiled[24] = {};  // by T (32, 64, 128), buffers (1, 2), fused ingest, raw prefetch
     int occ_direct = 0;
     bool attr = false;
 };
@@ -278,6 +306,7 @@ int launch_q(const StreamArgs &s, const uint16_t *sx, const uint16_t *sy, uint64
         if (ta.no_copy && !ta.tma) return QEXT_E_INVAL;  // the test needs the bulk-copy path
         ta.raw_periods = 0;
         size_t smem = size_t(nbuf) * 2 * T * s.wpb * 4;
+        ta.raw_prefetch = 0;
         if constexpr (B != 0) {
             nbuf = 1;
             ta.nbuf = 1;
@@ -285,9 +314,11 @@ int launch_q(const StreamArgs &s, const uint16_t *sx, const uint16_t *sy, uint64
             ta.T = T;
             ta.ntiles = (s.nblocks + T - 1) / T;
             ta.raw_periods = raw_periods;
-            smem = raw_periods ? size_t(2) * 16 * raw_periods : size_t(2) * T * s.wpb * 4;
+            ta.raw_prefetch = raw_periods && (flags & QEXT_F_RAW_PREFETCH) &&
+                              size_t(4) * 16 * raw_periods <= size_t(kSmemBudget);
+            smem = raw_periods ? size_t(ta.raw_prefetch ? 4 : 2) * 16 * raw_periods : size_t(2) * T * s.wpb * 4;
         }
-        const int ti = (T == 32 ? 0 : T == 64 ? 1 : 2) + 3 * int(nbuf - 1) + (B != 0 ? 6 : 0);
+        const int ti = (T == 32 ? 0 : T == 64 ? 1 : 2) + 3 * int(nbuf - 1) + (B != 0 ? 6 : 0) + 12 * ta.raw_prefetch;
         int &occ = cache.occ_tiled[ti];
         if (!occ) {
             if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, extract_tiled_kernel<Q, B>, int(T * TPB), smem) !=
@@ -368,6 +399,10 @@ int launch_extract_samples(const qext_plan *p, uint32_t b, const uint16_t *sx, c
     const StreamArgs s = stream_args(p, nullptr, nullptr, nblocks, out);
     if ((flags & QEXT_F_WARP_SPECIALIZED) && (p->q == 4 || p->q == 16))
         return launch_fused_samples(p->q, b, s, sx, sy, nsamples, stream);
+    if (!(flags & QEXT_F_CTA_TILES)) {
+        const int rc = launch_raw_samples(p->q, b, s, sx, sy, nsamples, stream, flags);
+        if (rc != QEXT_E_UNSUPPORTED) return rc;
+    }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     switch (b) {
         case 8: return launch_samples_b<8>(p, s, sx, sy, nsamples, st, flags);

@@ -50,6 +50,10 @@ int launch_extract_samples(const qext_plan *p, uint32_t b, const uint16_t *sx, c
                            uint32_t flags);
 int launch_fused_samples(uint32_t q, uint32_t b, const qxd::StreamArgs &s, const uint16_t *sx, const uint16_t *sy,
                          uint64_t nsamples, qext_cuda_stream stream);
+// Per-warp raw-sample kernel (q = 4, 16 with n_p = 64); QEXT_E_UNSUPPORTED for
+// other shapes.
+int launch_raw_samples(uint32_t q, uint32_t b, const qxd::StreamArgs &s, const uint16_t *sx, const uint16_t *sy,
+                       uint64_t nsamples, qext_cuda_stream stream, uint32_t flags);
 int launch_pack(uint32_t b, const uint16_t *samples, uint64_t nsamples, uint32_t *out, qext_cuda_stream stream);
 int read_device_status(int *status);
 // Device address of the status word of the current device (null if the

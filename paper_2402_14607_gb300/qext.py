@@ -32,6 +32,8 @@ QEXT_F_TILE32 = 0x4
 QEXT_F_TILE64 = 0x8
 QEXT_F_TEST_TIMEOUT = 0x10
 QEXT_F_WARP_SPECIALIZED = 0x20
+QEXT_F_RAW_PREFETCH = 0x40
+QEXT_F_CTA_TILES = 0x80
 
 _lib = None
 

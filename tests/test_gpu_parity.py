@@ -150,11 +150,16 @@ def test_config_large_single_stream_sampled():
         assert bits_at(got, l * 16, 16) == int(z[0]), "block %d" % l
 
 
+SAMPLE_FLAGS = [0, qext.QEXT_F_RAW_PREFETCH, qext.QEXT_F_CTA_TILES,
+                qext.QEXT_F_CTA_TILES | qext.QEXT_F_RAW_PREFETCH, qext.QEXT_F_WARP_SPECIALIZED]
+SAMPLE_FLAG_IDS = ["warp_pipelines", "warp_pipelines_2buf", "cta_tiles", "cta_tiles_2buf", "warp_specialized"]
+
+
 @pytest.mark.parametrize("q,b,nblocks,extra", [
     (16, 12, 1000, 0), (16, 12, 4133, 5), (16, 12, 129, 1), (4, 8, 4099, 0), (4, 12, 777, 3), (4, 16, 64, 0),
     (64, 12, 300, 1), (64, 16, 129, 0), (64, 8, 33, 2), (16, 8, 257, 0), (16, 16, 100, 7), (16, 12, 1, 0),
 ])
-@pytest.mark.parametrize("flags", [0, qext.QEXT_F_WARP_SPECIALIZED], ids=["tma_in_place", "warp_specialized"])
+@pytest.mark.parametrize("flags", SAMPLE_FLAGS, ids=SAMPLE_FLAG_IDS)
 def test_extract_samples_matches_oracle(q, b, nblocks, extra, flags):
     """Fused ingest + extraction from raw b-bit samples (garbage above b) against
     the oracle's packing followed by its extraction, every output bit."""
@@ -179,6 +184,28 @@ def test_extract_samples_matches_oracle(q, b, nblocks, extra, flags):
     assert (got[:nout] == want).all()
 
 
+@pytest.mark.parametrize("q,b,nblocks", [(16, 12, 200037), (4, 8, 600001), (16, 16, 150011)])
+@pytest.mark.parametrize("flags", SAMPLE_FLAGS, ids=SAMPLE_FLAG_IDS)
+def test_extract_samples_many_tiles_per_cta(q, b, nblocks, flags):
+    """Enough tiles that every persistent CTA walks several of them (buffer
+    reuse, raw-tile prefetch, the ragged last tile), every output bit."""
+    plan = plan_for(q, 64)
+    n = 64 * q
+    ns = -(-nblocks * n // b)
+    s_x = workloads.adc_samples(1000 + q + b, ns, b)
+    s_y = workloads.adc_samples(2000 + q + b, ns, b)
+    nout = -(-nblocks * q // 32)
+    out = torch.full((nout + 4,), -1, dtype=torch.int32, device="cuda")
+    qext.qext_extract_samples_ex(plan, b, torch.from_numpy(s_x.view(np.int16)).cuda(),
+                                 torch.from_numpy(s_y.view(np.int16)).cuda(), ns, nblocks, out, None, flags)
+    torch.cuda.synchronize()
+    got = host_words(out)
+    assert (got[nout:] == 0xFFFFFFFF).all()
+    words = nblocks * n // 32
+    want = oracle_extract(plan, oracle.pack_samples(b, s_x)[:words], oracle.pack_samples(b, s_y)[:words], nblocks)
+    assert (got[:nout] == want).all()
+
+
 def test_extract_samples_rejects_short_input():
     plan = plan_for(16, 64)
     with pytest.raises(qext.QextError) as e:
@@ -189,7 +216,8 @@ def test_extract_samples_rejects_short_input():
     assert e.value.code == qext.QEXT_E_UNSUPPORTED
 
 
-def test_config_large_single_stream_fused_sampled():
+@pytest.mark.parametrize("flags", SAMPLE_FLAGS[:4], ids=SAMPLE_FLAG_IDS[:4])
+def test_config_large_single_stream_fused_sampled(flags):
     """2^20 blocks x 1024 bits from 12-bit samples through the fused path
     (the benchmark's launch), checked on sampled blocks against the oracle."""
     spec = workloads.config_large_single()
@@ -197,8 +225,8 @@ def test_config_large_single_stream_fused_sampled():
     sx, sy = spec.samples("x"), spec.samples("y")
     out_words = spec.nblocks * 16 // 32
     out = torch.full((out_words + 4,), -1, dtype=torch.int32, device="cuda")
-    qext.qext_extract_samples(plan, 12, torch.from_numpy(sx.view(np.int16)).cuda(),
-                              torch.from_numpy(sy.view(np.int16)).cuda(), sx.size, spec.nblocks, out)
+    qext.qext_extract_samples_ex(plan, 12, torch.from_numpy(sx.view(np.int16)).cuda(),
+                                 torch.from_numpy(sy.view(np.int16)).cuda(), sx.size, spec.nblocks, out, None, flags)
     torch.cuda.synchronize()
     got = host_words(out)
     assert (got[out_words:] == 0xFFFFFFFF).all()
