@@ -48,19 +48,12 @@ struct Acc {
     // z (2q-1 bits) = parities of the Gram diagonals
     __device__ __forceinline__ uint64_t unreduced(const ShiftMuls &mu) {
         if constexpr (kKaratsuba) {
-            // z = A + x^16 B + x^8 (C - A - B), combined word-wise, then parity
-            const uint32_t *A = a, *B = a + 15, *C = a + 30;
-            uint32_t W[31];
-#pragma unroll
-            for (int k = 0; k < 31; ++k) W[k] = 0;
-#pragma unroll
-            for (int k = 0; k < 15; ++k) {
-                const uint32_t mid = lop_xor3(C[k], A[k], B[k]);
-                W[k] ^= A[k];
-                W[k + 16] ^= B[k];
-                W[k + 8] ^= mid;
-            }
-            return parity_bits32<31>(W, mu);
+            // z = A + x^16 B + x^8 (C - A - B) on the parities of the three
+            // 15-word products (parity is linear); each r holds its 15
+            // parity bits in bits 17..31
+            const uint32_t rA = parity_bits32_top<15>(a, mu), rB = parity_bits32_top<15>(a + 15, mu),
+                           rC = parity_bits32_top<15>(a + 30, mu);
+            return lop_xor3(rA >> 17, rB >> 1, lop_xor3(rA, rB, rC) >> 9);
         } else {
             return parity_bits64<2 * Q - 1>(a, mu);
         }

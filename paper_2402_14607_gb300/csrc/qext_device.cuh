@@ -139,53 +139,31 @@ __device__ __forceinline__ void gram_diagonals(const uint32_t *X, const uint32_t
         for (int l = 0; l < NY; ++l) acc[j + l] = lop_and_xor(X[j], Y[l], acc[j + l]);
 }
 
-// Parities of 32 words at once: after folding stages G = 16 .. 1 (each an
-// exchange followed by XOR of the pair), bit p of a[0] is the parity of the
-// original a[p].
-template <int G>
-__device__ __forceinline__ void parity_fold(uint32_t (&a)[32], const ShiftMuls &mu) {
-    if constexpr (G >= 1) {
+// Parities of K <= 32 words.  POPC runs on the XU pipe and the bits are put
+// together by IMADs on the FMA pipe, which leaves the ALU pipe (saturated by
+// the AND/XOR work) alone:
+//     r = (r >> 1) + (popc(acc[k]) << 31)        for k = 0 .. K-1
+// puts parity(acc[k]) in bit 32 - K + k (no carries: r >> 1 has bit 31
+// clear and popc << 31 keeps only the popcount's low bit).
+template <int K>
+__device__ __forceinline__ uint32_t parity_bits32_top(const uint32_t *acc, const ShiftMuls &mu) {
+    static_assert(K >= 1 && K <= 32, "1..32 words");
+    const uint32_t top = mu.hi[0];  // 2^31 at run time, so the multiplies stay IMADs
+    uint32_t r = 0;
 #pragma unroll
-        for (int i = 0; i < G; ++i) {
-            uint32_t u = a[i], v = a[i + G];
-            exchange<G>(u, v, mu);
-            a[i] = u ^ v;
-        }
-        parity_fold<G / 2>(a, mu);
-    }
+    for (int k = 0; k < K; ++k) r = __umulhi(r, top) + uint32_t(__popc(acc[k])) * top;
+    return r;
 }
 
-template <int N, int G>
-__device__ __forceinline__ void parity_fold_n(uint32_t (&a)[N], const ShiftMuls &mu) {
-    if constexpr (G >= 1) {
-#pragma unroll
-        for (int i = 0; i < G; ++i) {
-            uint32_t u = a[i], v = a[i + G];
-            exchange<G>(u, v, mu);
-            a[i] = u ^ v;
-        }
-        parity_fold_n<N, G / 2>(a, mu);
-    }
-}
-
-// bit k of the result = parity(acc[k]) for k < K (K <= 32).  With N = the
-// power of two >= K, stages G = N/2 .. 1 leave, in every N-bit segment of
-// a[0], bit p = parity of that segment of acc[p]; XORing the 32/N segments
-// together finishes the parities.
+// bit k of the result = parity(acc[k]) for k < K (K <= 32).
 template <int K>
 __device__ __forceinline__ uint32_t parity_bits32(const uint32_t *acc, const ShiftMuls &mu) {
-    constexpr int N = K <= 1 ? 1 : K <= 2 ? 2 : K <= 4 ? 4 : K <= 8 ? 8 : K <= 16 ? 16 : 32;
-    uint32_t a[N];
-#pragma unroll
-    for (int i = 0; i < N; ++i) a[i] = i < K ? acc[i] : 0u;
-    parity_fold_n<N, N / 2>(a, mu);
-    uint32_t r = a[0];
-    if constexpr (N <= 16) r ^= r >> 16;
-    if constexpr (N <= 8) r ^= r >> 8;
-    if constexpr (N <= 4) r ^= r >> 4;
-    if constexpr (N <= 2) r ^= r >> 2;
-    if constexpr (N <= 1) r ^= r >> 1;
-    return r & (N == 32 ? 0xFFFFFFFFu : ((1u << N) - 1u));
+    const uint32_t r = parity_bits32_top<K>(acc, mu);
+    if constexpr (K == 32) {
+        return r;
+    } else {
+        return r >> (32 - K);
+    }
 }
 
 template <int K>
