@@ -2,8 +2,9 @@
 // q = 4 and q = 16 with n_p = 64: Ext_IP (Definition 3.2) per block of
 // Algorithm 1, one block per thread, with per-warp copy pipelines.
 //
-// Every warp runs its own pipeline over sub-tiles of 32 consecutive blocks
-// (one block per lane).  Lane 0 copies the sub-tile's raw samples, as whole
+// Every warp runs its own pipeline over sub-tiles of R rows of 32 consecutive
+// blocks (one block per lane and row; R = 4 for q = 4 so that copies stay
+// large, else 1).  Lane 0 copies the sub-tile's raw samples, as whole
 // periods of 8 samples (16 bytes), into the warp's shared-memory buffer with
 // two 1-D TMA bulk copies that complete on the warp's mbarrier.  Each lane
 // then reads its own block's periods from shared memory and packs them into
@@ -48,8 +49,11 @@ struct RawLayout {
     static constexpr int NR = NPB >= 16 ? 16 : NPB >= 8 ? 8 : NPB >= 4 ? 4 : NPB >= 2 ? 2 : 1;
     static_assert(B != 12 || (WPB % 3 == 2 && 3 * NPG + 1 == Q), "b = 12 layout needs 2q = 2 mod 3");
     static_assert(B == 12 || WP * NPG == Q, "whole periods per group");
-    // raw periods per source and sub-tile of 32 blocks (capacity)
-    static constexpr uint32_t kCap = (32u * WPB + WP - 1) / WP + 1;
+    // rows of 32 blocks per sub-tile: small blocks take several rows so
+    // that each bulk copy stays large
+    static constexpr uint32_t kRows = Q == 4 ? 4 : 1;
+    // raw periods per source and sub-tile (buffer capacity)
+    static constexpr uint32_t kCap = (32u * kRows * WPB + WP - 1) / WP + 1;
 };
 
 struct RawArgs {
@@ -58,12 +62,13 @@ struct RawArgs {
     const uint16_t *sx;
     const uint16_t *sy;
     uint64_t nsamples;
-    uint64_t nsub;       // sub-tiles of 32 blocks
+    uint64_t nsub;       // sub-tiles of 32 * L::kRows blocks
     uint32_t nbuf;       // raw buffers per warp: 1 or 2
     uint32_t max_polls;  // bound of every mbarrier wait
 };
 
-// Sub-tile t: blocks [32t, min(32t+32, nblocks)), raw periods [p0, p0 + np).
+// Sub-tile t: blocks [32R t, min(32R (t+1), nblocks)) with R = kRows rows of
+// 32 blocks, raw periods [p0, p0 + np).
 template <int Q, int B>
 struct SubTile {
     uint64_t p0;
@@ -71,8 +76,9 @@ struct SubTile {
     bool tma;  // every period lies inside the sample arrays: bulk-copy it
     __device__ __forceinline__ SubTile(const RawArgs &a, uint64_t t) {
         using L = RawLayout<Q, B>;
-        const uint64_t b_end = 32 * t + 32 < a.s.nblocks ? 32 * t + 32 : a.s.nblocks;
-        p0 = 32 * t * L::WPB / L::WP;
+        const uint64_t b0 = 32 * L::kRows * t;
+        const uint64_t b_end = b0 + 32 * L::kRows < a.s.nblocks ? b0 + 32 * L::kRows : a.s.nblocks;
+        p0 = b0 * L::WPB / L::WP;
         np = uint32_t((b_end * L::WPB - 1) / L::WP - p0 + 1);
         tma = 8 * (p0 + np) <= a.nsamples;
     }
@@ -215,50 +221,58 @@ __global__ void __launch_bounds__(32 * kWarps) extract_raw_kernel(const RawArgs 
             __syncwarp();
         }
 
-        // this lane's block (lanes past the stream redo the last block, unstored)
-        const uint64_t blk = 32 * t + lane;
-        const uint64_t lb = blk < s.nblocks ? blk : s.nblocks - 1;
-        const uint64_t w0 = lb * L::WPB;
-        const uint32_t fp_rel = uint32_t((w0 + L::WP - 1) / L::WP - st.p0);  // first whole period
-        const uint32_t rot = lane_rotation<Q, B>(lane, fp_rel);
-        uint32_t ex1 = 0, ey1 = 0, ex2 = 0, ey2 = 0;
-        if constexpr (B == 12) {
-            const uint32_t off = uint32_t(w0 % 3);
-            const uint32_t hp = off ? fp_rel - 1 : fp_rel;                // head period (if any)
-            const uint32_t tp = off != 1 ? fp_rel + L::NPB : fp_rel;     // tail period (if any)
-            edge_words(bx[hp], bx[tp], off, ex1, ex2);
-            edge_words(by[hp], by[tp], off, ey1, ey2);
-        }
-        Acc<Q> acc;
-        {
-            uint32_t X[Q], Y[Q];
-            raw_group<Q, B, 0>(bx, by, fp_rel, rot, ex1, ey1, X, Y);
-            slice<Q>(X, a.mu);
-            slice<Q>(Y, a.mu);
-            acc.add(X, Y);
-        }
-        {
-            uint32_t X[Q], Y[Q];
-            raw_group<Q, B, 1>(bx, by, fp_rel, rot, ex2, ey2, X, Y);
-            // every lane has read its periods: the buffer may be refilled
-            __syncwarp();
-            if (a.nbuf == 1 && lane == 0) {
-                next_issued = false;
-                if (tn < a.nsub) {
-                    const SubTile<Q, B> sn(a, tn);
-                    if (sn.tma) {
-                        issue_sub(a, sn, buf0, buf0 + L::kCap, &full[warp][0]);
-                        next_issued = true;
+        // rows of 32 blocks, one block per lane (lanes past the stream redo
+        // the last block, unstored)
+        const uint64_t row0 = uint64_t(L::kRows) * t;
+        const uint64_t rows_left = (s.nblocks - 32 * row0 + 31) / 32;
+        const uint32_t nrows = rows_left < L::kRows ? uint32_t(rows_left) : L::kRows;
+        for (uint32_t r = 0; r < nrows; ++r) {
+            const uint64_t base = 32 * (row0 + r), blk = base + lane;
+            const uint64_t lb = blk < s.nblocks ? blk : s.nblocks - 1;
+            const uint64_t w0 = lb * L::WPB;
+            const uint32_t fp_rel = uint32_t((w0 + L::WP - 1) / L::WP - st.p0);  // first whole period
+            const uint32_t rot = lane_rotation<Q, B>(lane, fp_rel);
+            uint32_t ex1 = 0, ey1 = 0, ex2 = 0, ey2 = 0;
+            if constexpr (B == 12) {
+                const uint32_t off = uint32_t(w0 % 3);
+                const uint32_t hp = off ? fp_rel - 1 : fp_rel;             // head period (if any)
+                const uint32_t tp = off != 1 ? fp_rel + L::NPB : fp_rel;  // tail period (if any)
+                edge_words(bx[hp], bx[tp], off, ex1, ex2);
+                edge_words(by[hp], by[tp], off, ey1, ey2);
+            }
+            Acc<Q> acc;
+            {
+                uint32_t X[Q], Y[Q];
+                raw_group<Q, B, 0>(bx, by, fp_rel, rot, ex1, ey1, X, Y);
+                slice<Q>(X, a.mu);
+                slice<Q>(Y, a.mu);
+                acc.add(X, Y);
+            }
+            {
+                uint32_t X[Q], Y[Q];
+                raw_group<Q, B, 1>(bx, by, fp_rel, rot, ex2, ey2, X, Y);
+                if (r + 1 == nrows) {
+                    // every lane has read its periods: the buffer may be refilled
+                    __syncwarp();
+                    if (a.nbuf == 1 && lane == 0) {
+                        next_issued = false;
+                        if (tn < a.nsub) {
+                            const SubTile<Q, B> sn(a, tn);
+                            if (sn.tma) {
+                                issue_sub(a, sn, buf0, buf0 + L::kCap, &full[warp][0]);
+                                next_issued = true;
+                            }
+                        }
                     }
                 }
+                slice<Q>(X, a.mu);
+                slice<Q>(Y, a.mu);
+                acc.add(X, Y);
             }
-            slice<Q>(X, a.mu);
-            slice<Q>(Y, a.mu);
-            acc.add(X, Y);
+            uint64_t v = reduce_mod_p<Q>(acc.unreduced(a.mu), s) & mask_m(s.m);
+            if (blk >= s.nblocks) v = 0;
+            store_warp(v, base, s.nblocks, s.m, s.out);
         }
-        uint64_t v = reduce_mod_p<Q>(acc.unreduced(a.mu), s) & mask_m(s.m);
-        if (blk >= s.nblocks) v = 0;
-        store_warp(v, 32 * t, s.nblocks, s.m, s.out);
     }
     (void)next_issued;
 }
@@ -301,7 +315,7 @@ int launch_raw(const StreamArgs &s, const uint16_t *sx, const uint16_t *sy, uint
     a.sx = sx;
     a.sy = sy;
     a.nsamples = nsamples;
-    a.nsub = (s.nblocks + 31) / 32;
+    a.nsub = (s.nblocks + 32 * L::kRows - 1) / (32 * L::kRows);
     a.nbuf = nbuf;
     a.max_polls = kMaxPolls;
     const uint64_t ctas = (a.nsub + kWarps - 1) / kWarps, cap = uint64_t(c.sms) * occ;
