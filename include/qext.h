@@ -100,8 +100,11 @@ int qext_destroy(qext_plan *p);
  *   log2_eps_block     Theorem 3.1's per-block error, log2;
  *   poly_taps[4]       exponents of P below q, descending, then zeros
  *                      (the constant term 1 and x^q are implied);
- *   gpu_supported      1 if qext_extract has a kernel for this plan
- *                      (q in {1,2,4,8,16,32,64} and n a multiple of 32).
+ *   gpu_supported      1 if every GPU entry point has a kernel for this plan
+ *                      (q in {1,2,4,8,16,32,64} and n a multiple of 32);
+ *                      2 if only qext_extract and qext_extract_samples
+ *                      (b = 16) have one: q = 80, any n_p (Sec. 4.2's field);
+ *                      0 if none.
  * The error of a stream of L blocks is at most L * 2^log2_eps_block
  * (Theorem 3.3's sum with equal q).
  */
@@ -131,7 +134,8 @@ int qext_alg1_params(double N_samples, uint32_t b, double delta, double eps, uin
  *   stream CUDA stream the kernel is enqueued on (asynchronous).
  * The caller owns all three buffers.  nblocks = 0 enqueues nothing.
  * Errors: INVAL (null plan or pointer, misalignment), UNSUPPORTED (q has no
- * kernel: this build covers q in {1, 2, 4, 8, 16, 32, 64}), CUDA (launch).
+ * kernel: this build covers q in {1, 2, 4, 8, 16, 32, 64} with n a multiple
+ * of 32, and q = 80 with any n_p), CUDA (launch).
  */
 int qext_extract(const qext_plan *p, const uint32_t *x, const uint32_t *y, uint64_t nblocks, uint32_t *out,
                  qext_cuda_stream stream);
@@ -167,7 +171,8 @@ int qext_extract_ex(const qext_plan *p, const uint32_t *x, const uint32_t *y, ui
  *              aligned;
  *   nblocks    whole blocks to extract, nblocks * n <= nsamples * b;
  *   out        DEVICE pointer to ceil(nblocks*m/32) words, fully written.
- * Kernels exist for q in {4, 16, 64}; other q return UNSUPPORTED.
+ * Kernels exist for q in {4, 16, 64} (b = 8, 12, 16) and q = 80 (b = 16,
+ * where the samples are the packed stream); other q return UNSUPPORTED.
  * Asynchronous on stream.  Errors: INVAL, UNSUPPORTED, CUDA.
  */
 int qext_extract_samples(const qext_plan *p, uint32_t b, const uint16_t *x_samples, const uint16_t *y_samples,

@@ -16,10 +16,12 @@ int qext_extract_ex(const qext_plan *p, const uint32_t *x, const uint32_t *y, ui
     if (!p) return QEXT_E_INVAL;
     if (flags & ~uint32_t(QEXT_F_ALL)) return QEXT_E_INVAL;
     if ((flags & QEXT_F_TILE32) && (flags & QEXT_F_TILE64)) return QEXT_E_INVAL;
-    if (!p->gpu_supported) return QEXT_E_UNSUPPORTED;
+    if (!p->gpu_supported && !p->gpu_q80) return QEXT_E_UNSUPPORTED;
+    if (p->gpu_q80 && flags) return QEXT_E_INVAL;  // one kernel, no launch options
     if (nblocks == 0) return QEXT_OK;
     if (!x || !y || !out || !aligned(x, 4) || !aligned(y, 4) || !aligned(out, 4)) return QEXT_E_INVAL;
     if (nblocks > (UINT64_MAX / p->n)) return QEXT_E_INVAL;
+    if (p->gpu_q80) return qext::launch_extract_q80(p, x, y, nblocks, out, stream);
     return qext::launch_extract(p, x, y, nblocks, out, stream, flags);
 }
 
@@ -38,13 +40,17 @@ int qext_extract_samples_ex(const qext_plan *p, uint32_t b, const uint16_t *x_sa
                             uint32_t flags) {
     if (!p) return QEXT_E_INVAL;
     if (flags & ~uint32_t(QEXT_F_WARP_SPECIALIZED | QEXT_F_RAW_PREFETCH | QEXT_F_CTA_TILES)) return QEXT_E_INVAL;
-    if (!p->gpu_supported) return QEXT_E_UNSUPPORTED;
+    if (!p->gpu_supported && !p->gpu_q80) return QEXT_E_UNSUPPORTED;
     if (b != 8 && b != 12 && b != 16) return QEXT_E_UNSUPPORTED;
-    if (p->q != 4 && p->q != 16 && p->q != 64) return QEXT_E_UNSUPPORTED;
+    if (p->gpu_q80 ? b != 16 : (p->q != 4 && p->q != 16 && p->q != 64)) return QEXT_E_UNSUPPORTED;
+    if (p->gpu_q80 && flags) return QEXT_E_INVAL;
     if (nblocks == 0) return QEXT_OK;
     if (nsamples > UINT64_MAX / 16 || nblocks > (nsamples * b) / p->n) return QEXT_E_INVAL;
     if (!x_samples || !y_samples || !out || !aligned(x_samples, 16) || !aligned(y_samples, 16) || !aligned(out, 4))
         return QEXT_E_INVAL;
+    if (p->gpu_q80)  // 16-bit samples are the packed stream (sample s = bits [16s, 16s + 16))
+        return qext::launch_extract_q80(p, reinterpret_cast<const uint32_t *>(x_samples),
+                                        reinterpret_cast<const uint32_t *>(y_samples), nblocks, out, stream);
     return qext::launch_extract_samples(p, b, x_samples, y_samples, nsamples, nblocks, out, stream, flags);
 }
 

@@ -1,0 +1,290 @@
+// Extraction at the paper's own field size, q = 80 (Sec. 4.2: n_p = 71,
+// 5680-bit blocks of 16-bit samples), for any n_p: Ext_IP^{n_p,80}
+// (Definition 3.2) per block of Algorithm 1, one block per thread.
+//
+// Layout.  Block l is stream bits [l*n, (l+1)*n), n = 80 n_p, element i its
+// bits [80i, 80i+80).  Both l*n and 80i are multiples of 16, so every element
+// starts on a 16-bit boundary: its parts x0 (bits 0..31), x1 (32..63) and
+// x2 (64..79) are read from one or two stream words with one PRMT.
+//
+// Product.  Three-way Karatsuba over the parts (six products instead of
+// nine):  x*y = P00 + t^32 (P01 - P00 - P11) + t^64 (P02 - P00 - P22 + P11)
+//             + t^96 (P12 - P11 - P22) + t^128 P22,
+// with Pab = (xa + xb)(ya + yb), Paa = xa ya.  Each is accumulated over the
+// block's elements as sliced Gram-diagonal parities, 32 elements per group:
+// the 32-bit parts by a 32 x 32 transpose (element e in slot e) and
+// gram32_parities, x2 by slice<16> with elements k and k+16 in word k (which
+// also puts element e in slot e, so x0 + x2 is a slot-wise XOR of slices).
+// Parities are linear, so groups and Karatsuba parts combine after the
+// POPCs; the 159-bit sum is reduced mod P once per block.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "qext_block.cuh"
+#include "qext_internal.h"
+
+using namespace qxd;
+
+namespace {
+
+constexpr int kThreads80 = 128;
+constexpr int kMaxDevices80 = 64;
+
+struct Q80Args {
+    StreamArgs s;
+    ShiftMuls mu;
+    uint32_t n_p;
+    uint32_t zero;  // always 0 (see after())
+};
+
+// Raw operand of one product for elements 32g + e, e < 32 (element e in word
+// e): part A (0: bits 0..31, 1: bits 32..63), plus part 1 (kAdd1) and/or the
+// zero-extended x2 = bits 64..79 (kAddX2).  The block's bit 0 is bit 16*odd of
+// word w0; element e starts at bit 16 * ((odd + e) & 1) of its first word,
+// which sel[e & 1] undoes (PRMT 0x5432: from bit 16, 0x3210: from bit 0).
+// Elements past n_p read as 0.
+// Left alone, the compilers overlap the products of a group (loads and
+// slicing of the next product hoisted into the previous one: several hundred
+// registers).  Each product's operand addresses therefore depend on the
+// previous product's parity word through a run-time zero (`zero` = 0, a kernel
+// argument): w0 + (parity & zero) cannot be formed before that product ends.
+__device__ __forceinline__ uint64_t after(uint64_t w0, uint64_t done, uint32_t zero) {
+    return w0 + (uint32_t(done) & zero);
+}
+
+template <int A, bool kAdd1, bool kAddX2>
+__device__ __forceinline__ void load_operand(const uint32_t *__restrict__ w, uint64_t w0, uint32_t odd, uint32_t g,
+                                             uint32_t n_p, const uint32_t (&sel)[2], uint32_t (&R)[32]) {
+#pragma unroll
+    for (int e = 0; e < 32; ++e) {
+        const uint32_t elem = 32 * g + uint32_t(e);
+        const uint32_t in = elem < n_p;
+        const uint32_t bit = 16 * odd + 80 * (in ? elem : 0u);  // element start, from bit 0 of word w0
+        const uint64_t wi = w0 + (bit >> 5);
+        const uint32_t sh = (bit >> 4) & 1u;
+        // words wi .. wi+2 hold all three parts; with sh = 0 the PRMT takes
+        // the first operand whole, so reading word k + 1 costs no extra case
+        const uint32_t k0 = A, k1 = kAdd1 || kAddX2 ? 2 : A + 1;
+        uint32_t wd[3];
+#pragma unroll
+        for (uint32_t k = k0; k <= k1; ++k) wd[k] = __ldg(w + wi + k);
+        uint32_t v = __byte_perm(wd[A], wd[A + 1 <= k1 ? A + 1 : A], sel[e & 1]);
+        if constexpr (kAdd1) v ^= __byte_perm(wd[1], wd[2], sel[e & 1]);
+        if constexpr (kAddX2) v ^= __byte_perm(wd[2], wd[2], sel[e & 1]) & 0xFFFFu;
+        (void)sh;
+        R[e] = in ? v : 0u;
+    }
+}
+
+// x2 parts (bits 64..79) of elements 32g + k and 32g + k + 16 in word k.
+__device__ __forceinline__ void load_part16(const uint32_t *__restrict__ w, uint64_t w0, uint32_t odd, uint32_t g,
+                                            uint32_t n_p, const uint32_t (&sel)[2], uint32_t (&R)[16]) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        uint32_t v[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const uint32_t elem = 32 * g + uint32_t(k + 16 * h);
+            const uint32_t el = elem < n_p ? elem : 0u;
+            const uint32_t bit = 16 * odd + 80 * el + 64;
+            v[h] = elem < n_p ? __ldg(w + w0 + (bit >> 5)) : 0u;
+        }
+        // low half from element k, high half from element k + 16; both start
+        // at the same half-word position (80 * 16 = 0 mod 32)
+        R[k] = __byte_perm(v[0], v[1], sel[k & 1]);
+    }
+}
+
+// z (159 bits: z0 = bits 0..63, z1 = 64..127, z2 = 128..158) mod P, P = x^80 +
+// sum of taps (descending, last 0): two folds (2c - 2 < 80 checked at plan time).
+__device__ __forceinline__ void reduce_mod_p80(uint64_t z0, uint64_t z1, uint64_t z2, const StreamArgs &s,
+                                               uint64_t &r0, uint32_t &r1) {
+    // fold 1: H = z >> 80 (79 bits)
+    uint64_t h0 = (z1 >> 16) | (z2 << 48), h1 = z2 >> 16;
+    uint64_t l0 = z0, l1 = z1 & 0xFFFFull;
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+        if (t < int(s.ntaps)) {
+            const uint32_t c = s.taps[t];
+            l0 ^= h0 << c;
+            l1 ^= c ? (h1 << c) | (h0 >> (64 - c)) : h1;
+        }
+    // fold 2: bits 80 .. 80 + c of the result
+    const uint64_t g = l1 >> 16;
+    l1 &= 0xFFFFull;
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+        if (t < int(s.ntaps)) {
+            const uint32_t c = s.taps[t];
+            l0 ^= g << c;
+            l1 ^= c ? g >> (64 - c) : 0u;
+        }
+    r0 = l0;
+    r1 = uint32_t(l1);
+}
+
+// Bits [off, off + 32) of a value held as three words (v[2] holds its top bits).
+__device__ __forceinline__ uint32_t bits32(const uint32_t (&v)[3], uint32_t off) {
+    const uint32_t i = off >> 5, sh = off & 31u;
+    const uint32_t a = i == 0 ? v[0] : i == 1 ? v[1] : i == 2 ? v[2] : 0u;
+    const uint32_t b = i == 0 ? v[1] : i == 1 ? v[2] : 0u;
+    return sh ? __funnelshift_r(a, b, sh) : a;
+}
+
+// Output of 32 consecutive blocks base .. base+31 (one per lane, 32 < m <= 96
+// bits, value v truncated to m bits and 0 past nblocks): the warp owns exactly
+// m output words starting at word (base / 32) * m; with m > 32 a word holds
+// bits of at most two blocks.
+__device__ __forceinline__ void store_warp_wide(const uint32_t (&v)[3], uint64_t base, uint64_t nblocks, uint32_t m,
+                                                uint32_t *__restrict__ out) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t word0 = (base >> 5) * m;
+    const uint64_t total = (nblocks * m + 31) >> 5;
+    for (uint32_t r = 0; r * 32u < m; ++r) {
+        const uint32_t w = lane + 32u * r;            // the warp's output word w: bits [32w, 32w + 32)
+        const uint32_t first = w < m ? (32u * w) / m : 0u;
+        const uint32_t off = 32u * w - first * m;      // bit offset inside block `first`
+        uint32_t a[3], b[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            a[i] = __shfl_sync(0xffffffffu, v[i], int(first));
+            b[i] = __shfl_sync(0xffffffffu, v[i], int(first + 1 < 32u ? first + 1 : 31u));
+        }
+        if (w < m) {
+            uint32_t word = bits32(a, off);
+            if (off + 32u > m) {
+                const uint32_t keep = m - off;  // bits still from block `first` (1 .. 31)
+                word = (word & ((1u << keep) - 1u)) | (first + 1 < 32u ? b[0] << keep : 0u);
+            }
+            if (word0 + w < total) out[word0 + w] = word;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads80) extract_q80_kernel(const Q80Args a) {
+    const StreamArgs &s = a.s;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t warp = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
+    const uint64_t n = 80ull * a.n_p;
+    const uint32_t ngroups = (a.n_p + 31) / 32;
+    for (uint64_t base = warp * 32; base < s.nblocks; base += nwarps * 32) {
+        const uint64_t blk = base + lane;
+        const uint64_t lb = blk < s.nblocks ? blk : s.nblocks - 1;
+        const uint64_t bit0 = lb * n;
+        const uint64_t w0 = bit0 >> 5;
+        const uint32_t odd = uint32_t(bit0 >> 4) & 1u;  // block starts at bit 16 of w0
+        const uint32_t sel32[2] = {odd ? 0x5432u : 0x3210u, odd ? 0x3210u : 0x5432u};
+        // word k of the x2 slices: elements k, k + 16 (same alignment)
+        const uint32_t sel16[2] = {odd ? 0x7632u : 0x5410u, odd ? 0x5410u : 0x7632u};
+        uint64_t p00 = 0, p11 = 0, p01 = 0, p02 = 0, p12 = 0;
+        uint32_t p22 = 0;
+        for (uint32_t g = 0; g < ngroups; ++g) {
+            {
+                uint32_t X2[16], Y2[16];
+                const uint64_t wg = after(w0, p02, a.zero);  // after the previous group
+                load_part16(s.x, wg, odd, g, a.n_p, sel16, X2);
+                load_part16(s.y, wg, odd, g, a.n_p, sel16, Y2);
+                slice<16>(X2, a.mu);
+                slice<16>(Y2, a.mu);
+                p22 ^= diagonal_chain<16>(X2, Y2, a.mu.hi[0]) >> 1;
+            }
+            // the five 32 x 32 products, each sliced from its raw operand
+            // (slicing is linear, so sums of parts can be formed before it)
+            uint32_t X[32], Y[32];
+            uint64_t wp = after(w0, p22, a.zero);
+            load_operand<1, false, false>(s.x, wp, odd, g, a.n_p, sel32, X);
+            load_operand<1, false, false>(s.y, wp, odd, g, a.n_p, sel32, Y);
+            slice<32>(X, a.mu);
+            slice<32>(Y, a.mu);
+            p11 ^= gram32_parities(X, Y, a.mu);
+            wp = after(w0, p11, a.zero);
+            load_operand<1, false, true>(s.x, wp, odd, g, a.n_p, sel32, X);
+            load_operand<1, false, true>(s.y, wp, odd, g, a.n_p, sel32, Y);
+            slice<32>(X, a.mu);
+            slice<32>(Y, a.mu);
+            p12 ^= gram32_parities(X, Y, a.mu);
+            wp = after(w0, p12, a.zero);
+            load_operand<0, true, false>(s.x, wp, odd, g, a.n_p, sel32, X);
+            load_operand<0, true, false>(s.y, wp, odd, g, a.n_p, sel32, Y);
+            slice<32>(X, a.mu);
+            slice<32>(Y, a.mu);
+            p01 ^= gram32_parities(X, Y, a.mu);
+            wp = after(w0, p01, a.zero);
+            load_operand<0, false, false>(s.x, wp, odd, g, a.n_p, sel32, X);
+            load_operand<0, false, false>(s.y, wp, odd, g, a.n_p, sel32, Y);
+            slice<32>(X, a.mu);
+            slice<32>(Y, a.mu);
+            p00 ^= gram32_parities(X, Y, a.mu);
+            wp = after(w0, p00, a.zero);
+            load_operand<0, false, true>(s.x, wp, odd, g, a.n_p, sel32, X);
+            load_operand<0, false, true>(s.y, wp, odd, g, a.n_p, sel32, Y);
+            slice<32>(X, a.mu);
+            slice<32>(Y, a.mu);
+            p02 ^= gram32_parities(X, Y, a.mu);
+        }
+        // recombine the six products (63-bit parities; P22 31-bit)
+        const uint64_t t1 = p01 ^ p00 ^ p11, t2 = p02 ^ p00 ^ p11 ^ p22, t3 = p12 ^ p11 ^ p22;
+        const uint64_t z0 = p00 ^ (t1 << 32), z1 = (t1 >> 32) ^ t2 ^ (t3 << 32), z2 = (t3 >> 32) ^ p22;
+        uint64_t r0;
+        uint32_t r1;
+        reduce_mod_p80(z0, z1, z2, s, r0, r1);
+        // truncate to m bits
+        uint32_t v[3] = {uint32_t(r0), uint32_t(r0 >> 32), r1};
+        if (s.m < 64) {
+            v[2] = 0;
+            v[1] = s.m <= 32 ? 0u : v[1] & uint32_t(mask_m(s.m - 32));
+            if (s.m < 32) v[0] &= uint32_t(mask_m(s.m));
+        } else if (s.m < 80) {
+            v[2] &= uint32_t(mask_m(s.m - 64));
+        }
+        if (blk >= s.nblocks) v[0] = v[1] = v[2] = 0;
+        if (s.m <= 64)
+            store_warp(uint64_t(v[0]) | (uint64_t(v[1]) << 32), base, s.nblocks, s.m, s.out);
+        else
+            store_warp_wide(v, base, s.nblocks, s.m, s.out);
+    }
+}
+
+}  // namespace
+
+namespace qext {
+
+int launch_extract_q80(const qext_plan *p, const uint32_t *x, const uint32_t *y, uint64_t nblocks, uint32_t *out,
+                       qext_cuda_stream stream) {
+    if (p->q != 80) return QEXT_E_UNSUPPORTED;
+    if (nblocks == 0) return QEXT_OK;
+    static int grid_cap[kMaxDevices80] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices80) return QEXT_E_CUDA;
+    if (!grid_cap[dev]) {
+        int sms = 0, occ = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return QEXT_E_CUDA;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, extract_q80_kernel, kThreads80, 0) != cudaSuccess)
+            return QEXT_E_CUDA;
+        grid_cap[dev] = sms * (occ > 0 ? occ : 1);
+    }
+    Q80Args a;
+    a.s.x = x;
+    a.s.y = y;
+    a.s.out = out;
+    a.s.nblocks = nblocks;
+    a.s.wpb = 0;  // blocks need not be whole words
+    a.s.m = p->m;
+    a.s.ntaps = p->ntaps;
+    for (int i = 0; i < 4; ++i) {
+        a.s.taps[i] = p->taps[i];
+        a.s.tap_mul[i] = 0;
+    }
+    a.s.status = device_status_ptr();
+    a.mu = make_shift_muls();
+    a.n_p = p->n_p;
+    a.zero = 0;
+    const uint64_t ctas = (nblocks + kThreads80 - 1) / kThreads80;
+    const int grid = int(ctas < uint64_t(grid_cap[dev]) ? ctas : uint64_t(grid_cap[dev]));
+    extract_q80_kernel<<<grid, kThreads80, 0, reinterpret_cast<cudaStream_t>(stream)>>>(a);
+    return cudaGetLastError() == cudaSuccess ? QEXT_OK : QEXT_E_CUDA;
+}
+
+}  // namespace qext

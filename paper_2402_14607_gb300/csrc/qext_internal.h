@@ -17,7 +17,8 @@ struct qext_plan {
     double log2_eps;     // Theorem 3.1's per-block error, log2
     uint32_t ntaps;      // number of entries of taps[] used
     uint32_t taps[4];    // exponents of P(x) - x^q, descending, ending with 0
-    int gpu_supported;   // a kernel exists for this q
+    int gpu_supported;   // every GPU entry point has a kernel for this plan
+    int gpu_q80;         // q = 80: qext_extract / qext_extract_samples (b = 16) only
 };
 
 // Device-resident state of a stream (qext_stream.cu).
@@ -54,6 +55,9 @@ int launch_fused_samples(uint32_t q, uint32_t b, const qxd::StreamArgs &s, const
 // other shapes.
 int launch_raw_samples(uint32_t q, uint32_t b, const qxd::StreamArgs &s, const uint16_t *sx, const uint16_t *sy,
                        uint64_t nsamples, qext_cuda_stream stream, uint32_t flags);
+// q = 80 blocks (any n_p), packed words.
+int launch_extract_q80(const qext_plan *p, const uint32_t *x, const uint32_t *y, uint64_t nblocks, uint32_t *out,
+                       qext_cuda_stream stream);
 int launch_pack(uint32_t b, const uint16_t *samples, uint64_t nsamples, uint32_t *out, qext_cuda_stream stream);
 int read_device_status(int *status);
 // Device address of the status word of the current device (null if the

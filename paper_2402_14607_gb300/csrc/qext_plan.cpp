@@ -194,6 +194,7 @@ int qext_plan_create(uint32_t n, uint32_t m, double k, double eps, qext_plan **o
         }
         // two reduction folds suffice when the top tap c satisfies 2c - 2 < q
         p->gpu_supported = qext::gpu_q_supported(q) && n % 32 == 0 && (p->ntaps == 0 || 2 * p->taps[0] < q + 2);
+        p->gpu_q80 = q == 80 && 2 * p->taps[0] < q + 2;
         *out = p;
         return QEXT_OK;
     }
@@ -218,7 +219,7 @@ int qext_plan_info(const qext_plan *p, uint32_t *q, uint32_t *n_p, uint32_t *m, 
         for (uint32_t i = 0; i < p->ntaps; ++i)
             if (p->taps[i]) poly_taps[o++] = p->taps[i];
     }
-    if (gpu_supported) *gpu_supported = p->gpu_supported;
+    if (gpu_supported) *gpu_supported = p->gpu_supported ? 1 : p->gpu_q80 ? 2 : 0;
     return QEXT_OK;
 }
 

@@ -203,7 +203,7 @@ def qext_plan_info(plan: Plan) -> dict:
     _check(lib().qext_plan_info(plan.handle, ctypes.byref(q), ctypes.byref(n_p), ctypes.byref(m),
                                 ctypes.byref(le), taps, ctypes.byref(sup)), "qext_plan_info")
     return dict(q=q.value, n_p=n_p.value, n=q.value * n_p.value, m=m.value, log2_eps_block=le.value,
-                taps=tuple(int(t) for t in taps if t), gpu_supported=bool(sup.value))
+                taps=tuple(int(t) for t in taps if t), gpu_supported=int(sup.value))
 
 
 def qext_alg1_params(N_samples: float, b: int, delta: float, eps: float):

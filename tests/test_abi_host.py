@@ -61,7 +61,8 @@ def test_plan_matches_oracle(n, m, k, eps):
     assert (got["n_p"], got["q"], got["m"]) == (want["n_p"], want["q"], want["m"])
     assert abs(got["log2_eps_block"] - want["log2_eps"]) < 1e-9
     assert got["taps"] == want["taps"]
-    assert got["gpu_supported"] == (got["q"] in (1, 2, 4, 8, 16, 32, 64) and n % 32 == 0)
+    assert got["gpu_supported"] == (1 if got["q"] in (1, 2, 4, 8, 16, 32, 64) and n % 32 == 0
+                                    else 2 if got["q"] == 80 else 0)
 
 
 @pytest.mark.parametrize("n,m,k,eps,code", [
@@ -103,14 +104,28 @@ def test_alg1_params_worked_example():
     assert e.value.code == qext.QEXT_E_ENTROPY
 
 
-def test_paper_q80_plan_is_created_but_has_no_kernel():
+def test_paper_q80_plan_has_the_extract_kernels_only():
     p = qext.qext_plan_create(5680, 80, 0.67125 * 5680, 2.0 ** -30)
     info = p.info
-    assert (info["n_p"], info["q"]) == (71, 80) and not info["gpu_supported"]
+    # 2: qext_extract and qext_extract_samples (b = 16) only
+    assert (info["n_p"], info["q"], info["gpu_supported"]) == (71, 80, 2)
     assert info["log2_eps_block"] < math.log2(2.0 ** -30)
-    # qext_extract refuses before touching any pointer or device
+    # argument checks come before any device work
     with pytest.raises(qext.QextError) as e:
         qext.qext_extract(p, 0, 0, 1, 0, 0)
+    assert e.value.code == qext.QEXT_E_INVAL
+    with pytest.raises(qext.QextError) as e:
+        qext.qext_extract_ex(p, 16, 16, 1, 16, 0, qext.QEXT_F_DIRECT)
+    assert e.value.code == qext.QEXT_E_INVAL
+    # the other entry points have no q = 80 kernel and refuse the plan
+    with pytest.raises(qext.QextError) as e:
+        qext.qext_stream_create(p)
+    assert e.value.code == qext.QEXT_E_UNSUPPORTED
+    with pytest.raises(qext.QextError) as e:
+        qext.qext_pipeline_create(p, 16, 1024)
+    assert e.value.code == qext.QEXT_E_UNSUPPORTED
+    with pytest.raises(qext.QextError) as e:
+        qext.qext_extract_samples(p, 12, 16, 16, 10 ** 6, 1, 16, stream=0)
     assert e.value.code == qext.QEXT_E_UNSUPPORTED
 
 
