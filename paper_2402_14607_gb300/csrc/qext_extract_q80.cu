@@ -28,7 +28,7 @@ using namespace qxd;
 
 namespace {
 
-constexpr int kThreads80 = 128;
+constexpr int kThreads80 = 64;
 constexpr int kMaxDevices80 = 64;
 
 struct Q80Args {
@@ -53,26 +53,24 @@ __device__ __forceinline__ uint64_t after(uint64_t w0, uint64_t done, uint32_t z
     return w0 + (uint32_t(done) & zero);
 }
 
-template <int A, bool kAdd1, bool kAddX2>
-__device__ __forceinline__ void load_operand(const uint32_t *__restrict__ w, uint64_t w0, uint32_t odd, uint32_t g,
-                                             uint32_t n_p, const uint32_t (&sel)[2], uint32_t (&R)[32]) {
+// 32-bit part A (0: bits 0..31, 1: bits 32..63) of elements 32g + e, e < 32
+// (element e in word e).  The block's bit 0 is bit 16*odd of word w0; element
+// e starts at bit 16 * ((odd + e) & 1) of its first word, which sel[e & 1]
+// undoes (PRMT 0x5432: from bit 16, 0x3210: from bit 0).  Past n_p: 0.
+// Loads go in batches of 8 elements (16 in flight): each batch's addresses
+// wait for the previous batch's first value through the run-time zero.
+template <int A>
+__device__ __forceinline__ void load_part32(const uint32_t *__restrict__ w, uint64_t w0, uint32_t odd, uint32_t g,
+                                            uint32_t n_p, const uint32_t (&sel)[2], uint32_t zero,
+                                            uint32_t (&R)[32]) {
 #pragma unroll
     for (int e = 0; e < 32; ++e) {
+        if (e % 8 == 0 && e) w0 = after(w0, R[e - 8], zero);
         const uint32_t elem = 32 * g + uint32_t(e);
         const uint32_t in = elem < n_p;
-        const uint32_t bit = 16 * odd + 80 * (in ? elem : 0u);  // element start, from bit 0 of word w0
-        const uint64_t wi = w0 + (bit >> 5);
-        const uint32_t sh = (bit >> 4) & 1u;
-        // words wi .. wi+2 hold all three parts; with sh = 0 the PRMT takes
-        // the first operand whole, so reading word k + 1 costs no extra case
-        const uint32_t k0 = A, k1 = kAdd1 || kAddX2 ? 2 : A + 1;
-        uint32_t wd[3];
-#pragma unroll
-        for (uint32_t k = k0; k <= k1; ++k) wd[k] = __ldg(w + wi + k);
-        uint32_t v = __byte_perm(wd[A], wd[A + 1 <= k1 ? A + 1 : A], sel[e & 1]);
-        if constexpr (kAdd1) v ^= __byte_perm(wd[1], wd[2], sel[e & 1]);
-        if constexpr (kAddX2) v ^= __byte_perm(wd[2], wd[2], sel[e & 1]) & 0xFFFFu;
-        (void)sh;
+        const uint32_t bit = 16 * odd + 80 * (in ? elem : 0u) + 32 * A;
+        const uint32_t *p = w + w0 + (bit >> 5);
+        const uint32_t v = __byte_perm(__ldg(p), __ldg(p + 1), sel[e & 1]);
         R[e] = in ? v : 0u;
     }
 }
@@ -162,7 +160,11 @@ __device__ __forceinline__ void store_warp_wide(const uint32_t (&v)[3], uint64_t
     }
 }
 
-__global__ void __launch_bounds__(kThreads80) extract_q80_kernel(const Q80Args a) {
+__global__ void __launch_bounds__(kThreads80, 6) extract_q80_kernel(const Q80Args a) {
+    // per thread: 80 sliced words of each source, interleaved across threads
+    // (word k of thread t at k * kThreads80 + t: conflict-free)
+    __shared__ uint32_t slices[2 * 80 * kThreads80];
+    uint32_t *const sl = slices + threadIdx.x;
     const StreamArgs &s = a.s;
     const uint32_t lane = threadIdx.x & 31u;
     const uint64_t warp = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
@@ -181,48 +183,81 @@ __global__ void __launch_bounds__(kThreads80) extract_q80_kernel(const Q80Args a
         uint64_t p00 = 0, p11 = 0, p01 = 0, p02 = 0, p12 = 0;
         uint32_t p22 = 0;
         for (uint32_t g = 0; g < ngroups; ++g) {
+            // slice each part of both sources once into this thread's
+            // column of the shared array (word k at sl[k * nthreads]):
+            // S0 = slices 0..31, S1 = 32..63, S2 = 64..79 (x), +80 (y)
+            uint64_t dep = p02;  // after the previous group
+#pragma unroll 1
+            for (uint32_t src = 0; src < 2; ++src) {
+                const uint32_t *ws = src ? s.y : s.x;
+                uint32_t *const col = sl + src * 80 * kThreads80;
+                {
+                    uint32_t R[32];
+                    load_part32<0>(ws, after(w0, dep, a.zero), odd, g, a.n_p, sel32, a.zero, R);
+                    slice<32>(R, a.mu);
+#pragma unroll
+                    for (int k = 0; k < 32; ++k) col[k * kThreads80] = R[k];
+                    dep = R[31];
+                }
+                {
+                    uint32_t R[32];
+                    load_part32<1>(ws, after(w0, dep, a.zero), odd, g, a.n_p, sel32, a.zero, R);
+                    slice<32>(R, a.mu);
+#pragma unroll
+                    for (int k = 0; k < 32; ++k) col[(32 + k) * kThreads80] = R[k];
+                    dep = R[31];
+                }
+                {
+                    uint32_t R[16];
+                    load_part16(ws, after(w0, dep, a.zero), odd, g, a.n_p, sel16, R);
+                    slice<16>(R, a.mu);
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) col[(64 + k) * kThreads80] = R[k];
+                    dep = R[15];
+                }
+            }
+            const uint32_t *const cx = sl, *const cy = sl + 80 * kThreads80;
             {
                 uint32_t X2[16], Y2[16];
-                const uint64_t wg = after(w0, p02, a.zero);  // after the previous group
-                load_part16(s.x, wg, odd, g, a.n_p, sel16, X2);
-                load_part16(s.y, wg, odd, g, a.n_p, sel16, Y2);
-                slice<16>(X2, a.mu);
-                slice<16>(Y2, a.mu);
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    X2[k] = cx[(64 + k) * kThreads80];
+                    Y2[k] = cy[(64 + k) * kThreads80];
+                }
                 p22 ^= diagonal_chain<16>(X2, Y2, a.mu.hi[0]) >> 1;
             }
-            // the five 32 x 32 products, each sliced from its raw operand
-            // (slicing is linear, so sums of parts can be formed before it)
-            uint32_t X[32], Y[32];
-            uint64_t wp = after(w0, p22, a.zero);
-            load_operand<1, false, false>(s.x, wp, odd, g, a.n_p, sel32, X);
-            load_operand<1, false, false>(s.y, wp, odd, g, a.n_p, sel32, Y);
-            slice<32>(X, a.mu);
-            slice<32>(Y, a.mu);
-            p11 ^= gram32_parities(X, Y, a.mu);
-            wp = after(w0, p11, a.zero);
-            load_operand<1, false, true>(s.x, wp, odd, g, a.n_p, sel32, X);
-            load_operand<1, false, true>(s.y, wp, odd, g, a.n_p, sel32, Y);
-            slice<32>(X, a.mu);
-            slice<32>(Y, a.mu);
-            p12 ^= gram32_parities(X, Y, a.mu);
-            wp = after(w0, p12, a.zero);
-            load_operand<0, true, false>(s.x, wp, odd, g, a.n_p, sel32, X);
-            load_operand<0, true, false>(s.y, wp, odd, g, a.n_p, sel32, Y);
-            slice<32>(X, a.mu);
-            slice<32>(Y, a.mu);
-            p01 ^= gram32_parities(X, Y, a.mu);
-            wp = after(w0, p01, a.zero);
-            load_operand<0, false, false>(s.x, wp, odd, g, a.n_p, sel32, X);
-            load_operand<0, false, false>(s.y, wp, odd, g, a.n_p, sel32, Y);
-            slice<32>(X, a.mu);
-            slice<32>(Y, a.mu);
-            p00 ^= gram32_parities(X, Y, a.mu);
-            wp = after(w0, p00, a.zero);
-            load_operand<0, false, true>(s.x, wp, odd, g, a.n_p, sel32, X);
-            load_operand<0, false, true>(s.y, wp, odd, g, a.n_p, sel32, Y);
-            slice<32>(X, a.mu);
-            slice<32>(Y, a.mu);
-            p02 ^= gram32_parities(X, Y, a.mu);
+            // the five 32 x 32 products; operands are XORs of slices (slicing
+            // is linear):  pr 0: S1 (P11), 1: S1 + S2 (P12), 2: S0 + S1 (P01),
+            // 3: S0 (P00), 4: S0 + S2 (P02), S2 covering slices 0..15
+#pragma unroll 1
+            for (uint32_t pr = 0; pr < 5; ++pr) {
+                uint32_t X[32], Y[32];
+                const uint32_t first = pr <= 2 ? 32u : 0u;  // S1 or S0
+#pragma unroll
+                for (int k = 0; k < 32; ++k) {
+                    X[k] = cx[(first + k) * kThreads80];
+                    Y[k] = cy[(first + k) * kThreads80];
+                }
+                if (pr == 2) {
+#pragma unroll
+                    for (int k = 0; k < 32; ++k) {
+                        X[k] ^= cx[k * kThreads80];
+                        Y[k] ^= cy[k * kThreads80];
+                    }
+                } else if (pr == 1 || pr == 4) {
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) {
+                        X[k] ^= cx[(64 + k) * kThreads80];
+                        Y[k] ^= cy[(64 + k) * kThreads80];
+                    }
+                }
+                const uint64_t r = gram32_parities(X, Y, a.mu);
+                p11 ^= pr == 0 ? r : 0;
+                p12 ^= pr == 1 ? r : 0;
+                p01 ^= pr == 2 ? r : 0;
+                p00 ^= pr == 3 ? r : 0;
+                p02 ^= pr == 4 ? r : 0;
+            }
         }
         // recombine the six products (63-bit parities; P22 31-bit)
         const uint64_t t1 = p01 ^ p00 ^ p11, t2 = p02 ^ p00 ^ p11 ^ p22, t3 = p12 ^ p11 ^ p22;
