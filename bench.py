@@ -239,6 +239,41 @@ def measure_batched(args, dev):
             "outputs_equal_plain": same, "launches_per_run": 1}
 
 
+def measure_paper_params(args, dev):
+    """The paper's own parameterisation (Sec. 4.2: 16-bit samples, delta =
+    10.74/16, n_p = 71, q = 80, 5680-bit blocks): 2^18 block pairs of seeded
+    16-bit samples through qext_extract_samples, CUDA events, inputs larger
+    than L2.  Context for the paper's simulated FPGA figure (64 Gbps)."""
+    import numpy as np
+    import torch
+
+    from paper_2402_14607_gb300 import qext, workloads
+    plan = qext.qext_plan_create(5680, 80, 0.67125 * 5680, 2.0 ** -30)
+    info = plan.info
+    nb = 1 << 18
+    ns = nb * 5680 // 16
+    sx = torch.from_numpy(workloads.adc_samples(51, ns, 16).view(np.int16)).to(dev)
+    sy = torch.from_numpy(workloads.adc_samples(52, ns, 16).view(np.int16)).to(dev)
+    out = torch.empty(nb * 80 // 32, dtype=torch.int32, device=dev)
+    for _ in range(3):
+        qext.qext_extract_samples(plan, 16, sx, sy, ns, nb, out)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(10):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        qext.qext_extract_samples(plan, 16, sx, sy, ns, nb, out)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) * 1e-3)
+    t = statistics.median(times)
+    return {"workload": "2^18 block pairs x 5680 bits (n_p = 71, q = 80), 16-bit samples, seeds 51/52",
+            "q": info["q"], "n_p": info["n_p"], "m": info["m"], "log2_eps_block": round(info["log2_eps_block"], 2),
+            "extracted_gbps": round(nb * 80 / t / 1e9, 2), "ms": round(t * 1e3, 4),
+            "input_gbps": round(2 * nb * 5680 / t / 1e9, 1),
+            "paper_fpga_estimate_gbps": 64.0}
+
+
 def measure_serving(args, dev):
     """Poisson arrivals at 2000 requests/s from 256 channels, 2^10..2^18
     block pairs per request (rounded to multiples of 3 so requests hold whole
@@ -468,6 +503,8 @@ def run_gpu(args):
         extra["batched"] = measure_batched(args, dev)
         torch.cuda.empty_cache()
         extra["serving"] = measure_serving(args, dev)
+        torch.cuda.empty_cache()
+        extra["paper_params"] = measure_paper_params(args, dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
