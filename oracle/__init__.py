@@ -86,6 +86,10 @@ def _configure(lib):
     lib.orc_alg1_params.argtypes = [ctypes.c_double, ctypes.c_uint32, ctypes.c_double, ctypes.c_double,
                                     u32p, u32p]
     lib.orc_alg1_params.restype = ctypes.c_int
+    lib.orc_extract_alg2.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, u32p, u32p, u32p]
+    lib.orc_extract_alg2.restype = ctypes.c_int
+    lib.orc_alg2_log2_error.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.orc_alg2_log2_error.restype = ctypes.c_double
     lib.orc_pack_samples.argtypes = [ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint16), ctypes.c_uint64, u32p]
     lib.orc_pack_samples.restype = None
     lib.orc_max_q.restype = ctypes.c_int
@@ -176,6 +180,29 @@ def extract(q: int, n_p: int, m: int, poly: int, x: np.ndarray, y: np.ndarray, n
     if rc != 0:
         raise ValueError("orc_extract rejected its arguments (rc=%d)" % rc)
     return out[: (nblocks * m + 31) // 32]
+
+
+def extract_alg2(n_p: int, q1: int, dq: int, nblocks: int, x: np.ndarray, y: np.ndarray) -> np.ndarray:
+    """Algorithm 2 (Sec. 3.3) over its first ``nblocks`` blocks: block l has
+    q_l = q1 + l*dq (dq = Delta*b) and takes the next q_l*n_p stream bits of
+    each packed uint32 stream; returns the concatenated outputs (sum q_l bits)
+    as uint32 words."""
+    lib = _load()
+    x = np.ascontiguousarray(x, dtype=np.uint32)
+    y = np.ascontiguousarray(y, dtype=np.uint32)
+    qs = [q1 + l * dq for l in range(nblocks)]
+    need = (n_p * sum(qs) + 31) // 32
+    if x.size < need or y.size < need:
+        raise ValueError("streams shorter than nblocks blocks")
+    out = np.zeros(max(1, (sum(qs) + 31) // 32), dtype=np.uint32)
+    if lib.orc_extract_alg2(n_p, q1, dq, nblocks, _u32(x), _u32(y), _u32(out)) != 0:
+        raise ValueError("bad Algorithm 2 parameters")
+    return out
+
+
+def alg2_log2_error(n_p: int, delta: float, q1: int, dq: int, nblocks: int) -> float:
+    """log2 of Theorem 3.3's bound for the first nblocks outputs of Algorithm 2."""
+    return _load().orc_alg2_log2_error(n_p, delta, q1, dq, nblocks)
 
 
 def log2_eps_block(n: int, k: float, q: int) -> float:

@@ -290,6 +290,68 @@ int orc_extract(int q, int n_p, int m, const uint64_t *poly, const uint32_t *x, 
 }
 
 /*
+ * Algorithm 2 (Ext_bs^neq, Sec. 3.3) over its first nblocks blocks.
+ * Parameters q_1 = q1 and the step dq = Delta * b; n = n_p elements per
+ * block.  Following the algorithm: the cursor i starts at the first sample;
+ * block l takes the window I_l = [i, i - 1 + q_l n / b] of each source,
+ * computes Z^(l) = Ext_IP^{n, q_l}(X_{I_l}, Y_{I_l}) in GF(2^{q_l}) (with
+ * that degree's field polynomial, chosen as for Algorithm 1), outputs it, then
+ * i := i + q_l n / b and q_{l+1} := q_l + Delta b.  In stream bits the window
+ * is the next q_l * n bits and the outputs are concatenated, q_l bits each.
+ * out must hold ceil(sum q_l / 32) words and is fully overwritten.
+ * Returns 0, or -1 on bad arguments (some q_l outside 1..ORC_MAXQ).
+ */
+int orc_extract_alg2(int n_p, int q1, int dq, int nblocks, const uint32_t *x, const uint32_t *y, uint32_t *out)
+{
+    if (n_p < 1 || q1 < 1 || dq < 0 || nblocks < 0) return -1;
+    if ((int64_t)q1 + (int64_t)dq * (nblocks > 0 ? nblocks - 1 : 0) > ORC_MAXQ) return -1;
+    uint64_t total = 0;
+    for (int l = 0; l < nblocks; ++l) total += (uint64_t)(q1 + l * dq);
+    memset(out, 0, sizeof(uint32_t) * ((total + 31) / 32));
+    uint64_t i = 0;   /* the cursor, in stream bits */
+    uint64_t o = 0;   /* output bits so far */
+    int ql = q1;      /* q_l */
+    for (int l = 0; l < nblocks; ++l) {
+        uint64_t poly[ORC_W], z[ORC_W];
+        int taps[3];
+        if (!orc_select_poly(ql, poly, taps)) return -1;
+        int ew = (ql + 63) / 64;
+        uint64_t *xs = (uint64_t *)calloc((size_t)n_p * ew, sizeof(uint64_t));
+        uint64_t *ys = (uint64_t *)calloc((size_t)n_p * ew, sizeof(uint64_t));
+        for (int e = 0; e < n_p; ++e)               /* X_{I_l}: n elements of q_l bits */
+            for (int j = 0; j < ql; ++j) {
+                uint64_t t = i + (uint64_t)e * ql + j;
+                if (sbit(x, t)) pset(xs + (size_t)e * ew, j);
+                if (sbit(y, t)) pset(ys + (size_t)e * ew, j);
+            }
+        orc_ext_ip(ql, n_p, poly, xs, ys, z);     /* Z^(l) */
+        free(xs);
+        free(ys);
+        for (int j = 0; j < ql; ++j)                /* output Z^(l) */
+            if (pbit(z, j)) out[(o + j) >> 5] |= (uint32_t)1 << ((o + j) & 31);
+        i += (uint64_t)ql * (uint64_t)n_p;         /* i := i + q_l n / b (in bits: q_l n) */
+        o += (uint64_t)ql;
+        ql += dq;                                   /* q_{l+1} := q_l + Delta b */
+    }
+    return 0;
+}
+
+/*
+ * log2 of Theorem 3.3's bound on the error of the first nblocks outputs of
+ * Algorithm 2 (rate delta, n = n_p):
+ *   sqrt(3) * sum_l 2^(-1/4 - (delta/4 - 1/8) q_l n + 2 q_l).
+ */
+double orc_alg2_log2_error(int n_p, double delta, int q1, int dq, int nblocks)
+{
+    double sum = 0.0;
+    for (int l = 0; l < nblocks; ++l) {
+        double ql = (double)(q1 + l * dq);
+        sum += pow(2.0, -0.25 - (delta / 4.0 - 0.125) * ql * (double)n_p + 2.0 * ql);
+    }
+    return 0.5 * log2(3.0) + log2(sum);
+}
+
+/*
  * log2 of the per-block error of Theorem 3.1 for an n-bit block (n = q*n_p)
  * of min-entropy k bits (k = delta*q*n_p):
  *   eps_blk = sqrt(3) * 2^(-1/4 - (delta/4 - 1/8) q n_p + 2q)

@@ -10,6 +10,7 @@ import subprocess
 import pytest
 
 import oracle
+import tests.test_oracle_alg2 as alg2
 import tests.test_oracle_pins as pins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "qext_oracle.c")
@@ -26,7 +27,10 @@ MUTATIONS = {
     "nmin_off_by_one": ("while ((double)dmin * gap < 24.0 * (double)n) ++dmin;",
                         "while ((double)dmin * gap <= 24.0 * (double)n) ++dmin;"),
     "eps_sign": ("- (k / 4.0 - (double)n / 8.0)", "+ (k / 4.0 - (double)n / 8.0)"),
-    "y_for_x": ("if (sbit(y, t)) pset(ys", "if (sbit(x, t)) pset(ys"),
+    "y_for_x": ("if (sbit(y, t)) pset(ys + (size_t)i * ew", "if (sbit(x, t)) pset(ys + (size_t)i * ew"),
+    "alg2_cursor_by_first_block": ("i += (uint64_t)ql * (uint64_t)n_p;", "i += (uint64_t)q1 * (uint64_t)n_p;"),
+    "alg2_output_by_first_block": ("o += (uint64_t)ql;", "o += (uint64_t)q1;"),
+    "alg2_q_step_once": ("ql += dq;", "ql = q1 + dq;"),
 }
 
 # fast pins, each a (function, kwargs) pair from test_oracle_pins
@@ -42,6 +46,7 @@ CHECKS = [
     (pins.test_plan_rejections_and_exact_ceiling, {}),
     (pins.test_theorem31_constant_chain, {}),
     (pins.test_exact_uniformity, {"q": 2, "n_p": 4}),
+    (alg2.test_blocks_are_ext_ip_on_closed_form_windows, {"n_p": 27, "q1": 8, "dq": 8, "nb": 6}),
 ]
 
 
@@ -64,6 +69,7 @@ def _mutant(name, tmp_path):
 def test_pins_reject_planted_mistake(name, tmp_path, monkeypatch):
     mod = _mutant(name, tmp_path)
     monkeypatch.setattr(pins, "oracle", mod)
+    monkeypatch.setattr(alg2, "oracle", mod)
     caught = []
     for fn, kw in CHECKS:
         try:
