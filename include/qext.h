@@ -461,6 +461,50 @@ int qext_pipeline_run(qext_pipeline *pp, const void *x_host, const void *y_host,
  */
 int qext_device_status(int *status);
 
+/* ------------------------------------------------------------------------
+ * Algorithm 2 (Ext_bs^neq, Sec. 3.3; error: Theorem 3.3): block sizes grow
+ * with the block index, q_l = q_1 + l * Delta * b (l = 0, 1, ...), so that a
+ * stream of unknown length can be extracted.  n = ceil(24 / (2 delta - 1))
+ * elements per block (Algorithm 2's n); block l takes the next q_l * n bits of
+ * each stream (the paper's cursor advances by q_l n / b samples), computes
+ * Z^(l) = Ext_IP^{n, q_l} in GF(2^{q_l}) with that degree's field polynomial
+ * (the convention of qext_plan_create) and outputs its q_l bits, concatenated
+ * in block order.  With Delta = 0 this is Algorithm 1.
+ * ------------------------------------------------------------------------ */
+typedef struct qext_alg2_plan qext_alg2_plan;
+
+/*
+ * qext_alg2_plan_create -- the first max_blocks blocks of Algorithm 2 for
+ * b-bit samples (1 <= b <= 16) of min-entropy rate delta.  q1 and Delta * b
+ * must be multiples of 16 (the GPU works on 16-bit units), and
+ * q1 + (max_blocks - 1) * Delta * b <= 256 (the largest field built),
+ * else UNSUPPORTED.  Holds the per-block polynomials and a device table of
+ * them (allocated on the current device).  Caller owns *out.
+ * Errors: INVAL, ENTROPY (delta <= 1/2), UNSUPPORTED, PARAM, CUDA.
+ */
+int qext_alg2_plan_create(double delta, uint32_t b, uint32_t q1, uint32_t Delta, uint32_t max_blocks,
+                          qext_alg2_plan **out);
+/* n_p (Algorithm 2's n), max_blocks, and log2 of Theorem 3.3's bound
+ * sqrt(3) sum_l 2^(-1/4 - (delta/4 - 1/8) q_l n + 2 q_l) over the plan's
+ * blocks.  Any output pointer may be NULL.  Errors: INVAL. */
+int qext_alg2_plan_info(const qext_alg2_plan *p, uint32_t *n_p, uint32_t *max_blocks, double *log2_error_bound);
+/* Block l's q_l, window start (stream bit), output offset (bit) and
+ * polynomial taps (as qext_plan_info); l = max_blocks gives the end of the
+ * last block (q_l = 0).  Errors: INVAL. */
+int qext_alg2_block_info(const qext_alg2_plan *p, uint32_t l, uint32_t *q_l, uint64_t *in_bit, uint64_t *out_bit,
+                         uint64_t poly_taps[4]);
+/*
+ * qext_alg2_extract -- Z^(0) .. Z^(nblocks-1), nblocks <= max_blocks.
+ *   x, y  DEVICE pointers to the streams as 16-bit units (unit u = stream
+ *         bits [16u, 16u + 16), LSB first; for b = 16 the samples
+ *         themselves), 2-byte aligned, at least in_bit(nblocks) / 16 units;
+ *   out   DEVICE pointer to out_bit(nblocks) / 16 units, fully written.
+ * One CTA per block.  Asynchronous on stream.  Errors: INVAL, CUDA.
+ */
+int qext_alg2_extract(const qext_alg2_plan *p, const uint16_t *x, const uint16_t *y, uint32_t nblocks, uint16_t *out,
+                      qext_cuda_stream stream);
+int qext_alg2_destroy(qext_alg2_plan *p);
+
 #ifdef __cplusplus
 }
 #endif

@@ -42,6 +42,12 @@ namespace qext {
 
 // Field degrees with a GPU kernel.
 bool gpu_q_supported(uint32_t q);
+// The field polynomial of degree q (minimum weight, lexicographically first;
+// taps descending, ending with 0), q <= max_field_degree().
+bool field_poly(uint32_t q, uint32_t taps[4], uint32_t *ntaps);
+// Theorem 3.1's per-block error, log2, for an n-bit block of min-entropy k.
+double log2_eps_block(uint32_t n, double k, uint32_t q);
+uint32_t max_field_degree();
 
 // Ingest and extraction launchers (defined in the .cu files).
 int launch_extract(const qext_plan *p, const uint32_t *x, const uint32_t *y, uint64_t nblocks, uint32_t *out,

@@ -138,6 +138,14 @@ bool gpu_q_supported(uint32_t q) {
     return q == 1 || q == 2 || q == 4 || q == 8 || q == 16 || q == 32 || q == 64;
 }
 
+bool field_poly(uint32_t q, uint32_t taps[4], uint32_t *ntaps) {
+    return q >= 1 && q <= uint32_t(kMaxQ) && choose_field_poly(int(q), taps, ntaps);
+}
+
+double log2_eps_block(uint32_t n, double k, uint32_t q) { return theorem31_log2_eps(n, k, q); }
+
+uint32_t max_field_degree() { return uint32_t(kMaxQ); }
+
 }  // namespace qext
 
 extern "C" {

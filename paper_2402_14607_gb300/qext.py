@@ -122,6 +122,11 @@ def lib():
     L.qext_pipeline_info.argtypes = [vp, P(u64)]
     L.qext_pipeline_destroy.argtypes = [vp]
     L.qext_pipeline_run.argtypes = [vp, vp, vp, u64, u64, vp]
+    L.qext_alg2_plan_create.argtypes = [dbl, u32, u32, u32, u32, P(vp)]
+    L.qext_alg2_plan_info.argtypes = [vp, P(u32), P(u32), P(dbl)]
+    L.qext_alg2_block_info.argtypes = [vp, u32, P(u32), P(u64), P(u64), P(u64)]
+    L.qext_alg2_extract.argtypes = [vp, vp, vp, u32, vp, vp]
+    L.qext_alg2_destroy.argtypes = [vp]
     for name in ["qext_plan_create", "qext_destroy", "qext_plan_info", "qext_alg1_params", "qext_extract",
                  "qext_extract_ex", "qext_extract_samples", "qext_extract_samples_ex",
                  "qext_pack_samples", "qext_device_status", "qext_stream_create", "qext_stream_destroy",
@@ -131,7 +136,8 @@ def lib():
                  "qext_batch_autotune", "qext_batch_run_noalloc", "qext_server_create", "qext_server_destroy",
                  "qext_server_add_channel", "qext_server_submit", "qext_server_poll", "qext_server_drain",
                  "qext_server_get_stats", "qext_pipeline_create", "qext_pipeline_info", "qext_pipeline_destroy",
-                 "qext_pipeline_run"]:
+                 "qext_pipeline_run", "qext_alg2_plan_create", "qext_alg2_plan_info", "qext_alg2_block_info",
+                 "qext_alg2_extract", "qext_alg2_destroy"]:
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -494,3 +500,58 @@ def qext_pipeline_destroy(pp: Pipeline) -> None:
 def qext_pipeline_run(pp: Pipeline, x_host, y_host, count: int, nblocks: int, out_host) -> None:
     _check(lib().qext_pipeline_run(pp.handle, _ptr(x_host), _ptr(y_host), count, nblocks, _ptr(out_host)),
            "qext_pipeline_run")
+
+
+class Alg2Plan:
+    """Owns a qext_alg2_plan handle (Algorithm 2, growing q_l)."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+
+    def close(self):
+        if self.handle:
+            lib().qext_alg2_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def info(self):
+        return qext_alg2_plan_info(self)
+
+    def block(self, l: int) -> dict:
+        return qext_alg2_block_info(self, l)
+
+
+def qext_alg2_plan_create(delta: float, b: int, q1: int, Delta: int, max_blocks: int) -> Alg2Plan:
+    h = ctypes.c_void_p()
+    _check(lib().qext_alg2_plan_create(delta, b, q1, Delta, max_blocks, ctypes.byref(h)), "qext_alg2_plan_create")
+    return Alg2Plan(h.value)
+
+
+def qext_alg2_plan_info(p: Alg2Plan) -> dict:
+    n_p, nb, le = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_double()
+    _check(lib().qext_alg2_plan_info(p.handle, ctypes.byref(n_p), ctypes.byref(nb), ctypes.byref(le)),
+           "qext_alg2_plan_info")
+    return dict(n_p=n_p.value, max_blocks=nb.value, log2_error_bound=le.value)
+
+
+def qext_alg2_block_info(p: Alg2Plan, l: int) -> dict:
+    q, ib, ob = ctypes.c_uint32(), ctypes.c_uint64(), ctypes.c_uint64()
+    taps = (ctypes.c_uint64 * 4)()
+    _check(lib().qext_alg2_block_info(p.handle, l, ctypes.byref(q), ctypes.byref(ib), ctypes.byref(ob), taps),
+           "qext_alg2_block_info")
+    return dict(q=q.value, in_bit=ib.value, out_bit=ob.value, taps=tuple(int(t) for t in taps if t))
+
+
+def qext_alg2_extract(p: Alg2Plan, x, y, nblocks: int, out, stream=None) -> None:
+    _check(lib().qext_alg2_extract(p.handle, _ptr(x), _ptr(y), nblocks, _ptr(out), _stream(stream)),
+           "qext_alg2_extract")
+
+
+def qext_alg2_destroy(p: Alg2Plan) -> None:
+    p.close()

@@ -139,3 +139,19 @@ def test_extract_argument_checks_without_gpu():
     with pytest.raises(qext.QextError) as e:
         qext.qext_pack_samples(17, 16, 4, 16, stream=0)
     assert e.value.code == qext.QEXT_E_INVAL
+
+
+def test_alg2_plan_checks_without_gpu():
+    """Algorithm 2 plans: argument checks before any device work."""
+    with pytest.raises(qext.QextError) as e:
+        qext.qext_alg2_plan_create(0.5, 16, 16, 1, 4)
+    assert e.value.code == qext.QEXT_E_ENTROPY
+    with pytest.raises(qext.QextError) as e:
+        qext.qext_alg2_plan_create(0.8, 12, 24, 1, 4)     # q_l not multiples of 16
+    assert e.value.code == qext.QEXT_E_UNSUPPORTED
+    with pytest.raises(qext.QextError) as e:
+        qext.qext_alg2_plan_create(0.8, 16, 16, 1, 17)    # q_16 = 272 > 256
+    assert e.value.code == qext.QEXT_E_UNSUPPORTED
+    with pytest.raises(qext.QextError) as e:
+        qext.qext_alg2_plan_create(0.8, 16, 0, 1, 4)
+    assert e.value.code == qext.QEXT_E_INVAL
