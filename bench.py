@@ -274,6 +274,40 @@ def measure_paper_params(args, dev):
             "paper_fpga_estimate_gbps": 64.0}
 
 
+def measure_alg2(args, dev):
+    """Algorithm 2 at the paper's rate (delta = 10.74/16, b = 16) with q_1 = 16,
+    Delta = 1: its first 16 blocks (q_l = 16 .. 256, the largest field built;
+    n = 71), seeded 16-bit samples, one launch (one CTA per block), CUDA events."""
+    import numpy as np
+    import torch
+
+    from paper_2402_14607_gb300 import qext, workloads
+    p = qext.qext_alg2_plan_create(10.74 / 16, 16, 16, 1, 16)
+    info = p.info
+    end = p.block(16)
+    nunits = end["in_bit"] // 16
+    sx = torch.from_numpy(workloads.adc_samples(61, nunits, 16).view(np.int16)).to(dev)
+    sy = torch.from_numpy(workloads.adc_samples(62, nunits, 16).view(np.int16)).to(dev)
+    out = torch.empty(end["out_bit"] // 16, dtype=torch.int16, device=dev)
+    for _ in range(3):
+        qext.qext_alg2_extract(p, sx, sy, 16, out)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(20):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        qext.qext_alg2_extract(p, sx, sy, 16, out)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) * 1e-3)
+    t = statistics.median(times)
+    return {"workload": "Algorithm 2, delta = 10.74/16, b = 16, q_1 = 16, Delta = 1: 16 blocks, q_l = 16..256, "
+                        "n = 71 (2 x %d input bits)" % end["in_bit"],
+            "blocks": 16, "n_p": info["n_p"], "output_bits": end["out_bit"], "us": round(t * 1e6, 2),
+            "extracted_gbps": round(end["out_bit"] / t / 1e9, 4),
+            "log2_error_bound": round(info["log2_error_bound"], 2)}
+
+
 def measure_serving(args, dev):
     """Poisson arrivals at 2000 requests/s from 256 channels, 2^10..2^18
     block pairs per request (rounded to multiples of 3 so requests hold whole
@@ -505,6 +539,7 @@ def run_gpu(args):
         extra["serving"] = measure_serving(args, dev)
         torch.cuda.empty_cache()
         extra["paper_params"] = measure_paper_params(args, dev)
+        extra["alg2"] = measure_alg2(args, dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
