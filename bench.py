@@ -308,6 +308,55 @@ def measure_alg2(args, dev):
             "log2_error_bound": round(info["log2_error_bound"], 2)}
 
 
+def measure_sustained(args, dev):
+    """The sustained workload's shape: n = 4096 (q = 64) stream pairs pushed
+    through qext_stream_push in 256 MiB chunks (2^31 bits = 2^19 blocks per
+    source), state carried on the device, 16 chunks (4 GiB per source) cycling
+    over two chunk buffers of 12-bit ADC samples (sigma drifting +-5 %) packed
+    on the device by qext_pack_samples (not timed); CUDA events around the 16
+    pushes.  Inputs larger than L2 (512 MiB per push)."""
+    import numpy as np
+    import torch
+
+    from paper_2402_14607_gb300 import qext, workloads
+    spec = workloads.config_sustained(total_bits=1 << 32)
+    plan = qext.qext_plan_create(spec.n, 0, spec.k, spec.eps)
+    info = plan.info
+    chunk_bits = 1 << 31
+    bufs = []
+    for c in range(2):
+        nsamp = chunk_bits // 12 + 1
+        sx = workloads.adc_samples(spec.seed_x + 100 * c, nsamp, 12, drift_amp=0.05, drift_period=float(nsamp))
+        sy = workloads.adc_samples(spec.seed_y + 100 * c, nsamp, 12, drift_amp=0.05, drift_period=float(nsamp))
+        px = torch.empty(-(-nsamp * 12 // 32), dtype=torch.int32, device=dev)
+        py = torch.empty_like(px)
+        qext.qext_pack_samples(12, torch.from_numpy(sx.view(np.int16)).to(dev), nsamp, px)
+        qext.qext_pack_samples(12, torch.from_numpy(sy.view(np.int16)).to(dev), nsamp, py)
+        bufs.append((px, py))
+    out_words = chunk_bits // 4096 * info["m"] // 32
+    out = torch.empty(out_words, dtype=torch.int32, device=dev)
+    s = qext.qext_stream_create(plan)
+    for c in range(2):  # warm-up pushes
+        qext.qext_stream_push(s, bufs[c][0], bufs[c][1], chunk_bits, out, out_words)
+    torch.cuda.synchronize()
+    nchunks = 16
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for c in range(nchunks):
+        qext.qext_stream_push(s, bufs[c % 2][0], bufs[c % 2][1], chunk_bits, out, out_words)
+    e1.record()
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) * 1e-3
+    done = qext.qext_stream_info(s)["blocks_done"]
+    s.close()
+    return {"workload": "n = 4096 (q = %d), 16 pushes of 2^31-bit chunks (4 GiB per source), 12-bit ADC with "
+                        "sigma drifting +-5 %%, packed words in HBM, state carried" % info["q"],
+            "chunks": nchunks, "blocks": done, "ms": round(t * 1e3, 3),
+            "extracted_gbps": round(nchunks * (chunk_bits // 4096) * info["m"] / t / 1e9, 2),
+            "input_tbit_per_s": round(2 * nchunks * chunk_bits / t / 1e12, 2),
+            "hbm_frac_of_measured": round(2 * nchunks * chunk_bits / 8 / t / 1e9 / measured_peaks()[0], 4)}
+
+
 def measure_serving(args, dev):
     """Poisson arrivals at 2000 requests/s from 256 channels, 2^10..2^18
     block pairs per request (rounded to multiples of 3 so requests hold whole
@@ -540,6 +589,8 @@ def run_gpu(args):
         torch.cuda.empty_cache()
         extra["paper_params"] = measure_paper_params(args, dev)
         extra["alg2"] = measure_alg2(args, dev)
+        torch.cuda.empty_cache()
+        extra["sustained"] = measure_sustained(args, dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
