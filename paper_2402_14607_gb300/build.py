@@ -19,7 +19,7 @@ LIB = os.path.join(BUILD, "libqext.so")
 SOURCES = ["qext_plan.cpp", "qext_api.cpp", "qext_extract.cu", "qext_extract_raw.cu", "qext_extract_q80.cu", "qext_fused.cu", "qext_ingest.cu", "qext_stream.cu",
            "qext_batch.cu", "qext_server.cu", "qext_pipeline.cu", "qext_alg2.cu"]
 HEADERS = [os.path.join(CSRC, "qext_internal.h"), os.path.join(CSRC, "qext_device.cuh"),
-           os.path.join(CSRC, "qext_block.cuh"),
+           os.path.join(CSRC, "qext_block.cuh"), os.path.join(CSRC, "qext_wide.cuh"),
            os.path.join(ROOT, "include", "qext.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

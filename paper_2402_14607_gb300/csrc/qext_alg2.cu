@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "qext_block.cuh"
+#include "qext_wide.cuh"
 #include "qext_internal.h"
 
 using namespace qxd;

@@ -160,98 +160,6 @@ __device__ __forceinline__ uint64_t block_small_q(const uint32_t *xs, const uint
 }
 
 // ---------------------------------------------------------------------------
-// q = 64 (elements are word pairs: low word = bits 0..31, high = 32..63).
-// One Karatsuba level over the halves: z = A + x^64 B + x^32 (C - A - B) with
-// A = sum lo*lo, B = sum hi*hi, C = sum (lo^hi)*(lo^hi), each a sliced 32x32
-// Gram product over groups of 32 elements (itself split once more, see
-// gram32_parities).  Transposition is linear, so C's
-// operands are sliced from the XOR of the raw halves.  The thread handles the
-// groups g_first, g_first + g_step, ... of its block.
-// ---------------------------------------------------------------------------
-// Parity chain of the 2H-1 Gram diagonals of X[0..H) x Y[0..H), one diagonal
-// at a time (one live accumulator): bit 32 - (2H-1) + d of the result is
-// parity(XOR_{j+l=d} X[j] & Y[l]) (see parity_bits32_top).
-template <int H>
-__device__ __forceinline__ uint32_t diagonal_chain(const uint32_t *X, const uint32_t *Y, uint32_t top) {
-    static_assert(2 * H - 1 <= 32, "one word of parities");
-    uint32_t c = 0;
-#pragma unroll
-    for (int d = 0; d < 2 * H - 1; ++d) {
-        uint32_t acc = 0;
-#pragma unroll
-        for (int j = d < H ? 0 : d - H + 1; j <= (d < H ? d : H - 1); ++j) acc = lop_and_xor(X[j], Y[d - j], acc);
-        c = __umulhi(c, top) + uint32_t(__popc(acc)) * top;
-    }
-    return c;
-}
-
-// Parities of the 63 diagonals of a sliced 32 x 32 Gram product, by one
-// Karatsuba level over the slice index (low 16 / high 16 / their sums) and
-// diagonal chains; X and Y are overwritten.  Bit d of the result = parity of
-// diagonal d.
-__device__ __forceinline__ uint64_t gram32_parities(uint32_t (&X)[32], uint32_t (&Y)[32], const ShiftMuls &mu) {
-    const uint32_t top = mu.hi[0];  // 2^31 at run time
-    const uint32_t a = diagonal_chain<16>(X, Y, top);  // diagonal d at bit d + 1
-    const uint32_t b = diagonal_chain<16>(X + 16, Y + 16, top);
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-        X[j] ^= X[j + 16];
-        Y[j] ^= Y[j + 16];
-    }
-    const uint32_t c = diagonal_chain<16>(X, Y, top);
-    const uint64_t A = a >> 1, B = b >> 1, M = lop_xor3(a, b, c) >> 1;
-    return A ^ (M << 16) ^ (B << 32);
-}
-
-template <int PART>
-__device__ __forceinline__ uint32_t pick64(uint32_t lo, uint32_t hi) {
-    return PART == 0 ? lo : PART == 1 ? hi : (lo ^ hi);
-}
-
-template <int PART>
-__device__ __forceinline__ uint64_t half_product64(const uint32_t *xs, const uint32_t *ys, uint32_t wpb, int vec,
-                                                   uint32_t rot, uint32_t g_first, uint32_t g_step,
-                                                   const ShiftMuls &mu) {
-    uint64_t z = 0;  // parities are linear: XOR of the groups' parities
-    for (uint32_t g0 = 64 * g_first; g0 < wpb; g0 += 64 * g_step) {
-        uint32_t X[32], Y[32];
-        if (vec) {
-            // 16 chunks of 2 elements each, rotated within the group
-#pragma unroll
-            for (int c = 0; c < 16; ++c) {
-                const uint32_t w = g0 + 4 * ((uint32_t(c) + rot) & 15u);
-                uint4 vx = make_uint4(0, 0, 0, 0), vy = vx;
-                if (w < wpb) {
-                    vx = lds4(xs + w);
-                    vy = lds4(ys + w);
-                }
-                X[2 * c] = pick64<PART>(vx.x, vx.y);
-                X[2 * c + 1] = pick64<PART>(vx.z, vx.w);
-                Y[2 * c] = pick64<PART>(vy.x, vy.y);
-                Y[2 * c + 1] = pick64<PART>(vy.z, vy.w);
-            }
-        } else {
-#pragma unroll
-            for (int e = 0; e < 32; ++e) {
-                const uint32_t w = g0 + 2 * e;
-                const bool in = w < wpb;
-                X[e] = in ? pick64<PART>(xs[w], xs[w + 1]) : 0u;
-                Y[e] = in ? pick64<PART>(ys[w], ys[w + 1]) : 0u;
-            }
-        }
-        slice<32>(X, mu);
-        slice<32>(Y, mu);
-        z ^= gram32_parities(X, Y, mu);
-    }
-    return z;
-}
-
-__device__ __forceinline__ uint64_t combine_q64(uint64_t A, uint64_t B, uint64_t C, const StreamArgs &s) {
-    const uint64_t M = C ^ A ^ B;  // middle term, degree <= 62
-    return reduce_mod_p64(A ^ (M << 32), B ^ (M >> 32), s);
-}
-
-// ---------------------------------------------------------------------------
 // Fused ingest: pack the raw b-bit samples behind stream words [w0, w0 + nw)
 // straight into shared memory (sample s at stream bits [s*b, (s+1)*b), LSB
 // first; samples past nsamples read as 0).  One period per thread and step:

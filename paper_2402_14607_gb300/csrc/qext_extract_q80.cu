@@ -22,6 +22,7 @@
 #include <cstdint>
 
 #include "qext_block.cuh"
+#include "qext_wide.cuh"
 #include "qext_internal.h"
 
 using namespace qxd;

@@ -1,0 +1,119 @@
+// Device helpers of the wide fields: q = 64 (elements are word pairs) and
+// the 32 x 32 / 16 x 16 sliced Gram products by Karatsuba levels and POPC
+// diagonal chains that q = 64 and q = 80 share.
+#pragma once
+
+#include "qext_block.cuh"
+
+namespace qxd {
+
+// ---------------------------------------------------------------------------
+// q = 64 (elements are word pairs: low word = bits 0..31, high = 32..63).
+// One Karatsuba level over the halves: z = A + x^64 B + x^32 (C - A - B) with
+// A = sum lo*lo, B = sum hi*hi, C = sum (lo^hi)*(lo^hi), each a sliced 32x32
+// Gram product over groups of 32 elements (itself split once more, see
+// gram32_parities).  Transposition is linear, so C's
+// operands are sliced from the XOR of the raw halves.  The thread handles the
+// groups g_first, g_first + g_step, ... of its block.
+// ---------------------------------------------------------------------------
+// Parity chain of the 2H-1 Gram diagonals of X[0..H) x Y[0..H), one diagonal
+// at a time (one live accumulator): bit 32 - (2H-1) + d of the result is
+// parity(XOR_{j+l=d} X[j] & Y[l]) (see parity_bits32_top).
+template <int H>
+__device__ __forceinline__ uint32_t diagonal_chain(const uint32_t *X, const uint32_t *Y, uint32_t top) {
+    static_assert(2 * H - 1 <= 32, "one word of parities");
+    uint32_t c = 0;
+#pragma unroll
+    for (int d = 0; d < 2 * H - 1; ++d) {
+        uint32_t acc = 0;
+#pragma unroll
+        for (int j = d < H ? 0 : d - H + 1; j <= (d < H ? d : H - 1); ++j) acc = lop_and_xor(X[j], Y[d - j], acc);
+        c = __umulhi(c, top) + uint32_t(__popc(acc)) * top;
+    }
+    return c;
+}
+
+// Parities of the 31 diagonals of a sliced 16 x 16 Gram product by one
+// Karatsuba level (8 + 8): bit d of the result = parity of diagonal d.  X and
+// Y are overwritten (their low halves become the halves' sums).
+__device__ __forceinline__ uint32_t gram16_parities(uint32_t *X, uint32_t *Y, uint32_t top) {
+    const uint32_t a = diagonal_chain<8>(X, Y, top);  // 15 parities in bits 17..31
+    const uint32_t b = diagonal_chain<8>(X + 8, Y + 8, top);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        X[j] ^= X[j + 8];
+        Y[j] ^= Y[j + 8];
+    }
+    const uint32_t c = diagonal_chain<8>(X, Y, top);
+    return lop_xor3(a >> 17, b >> 1, lop_xor3(a, b, c) >> 9);
+}
+
+// Parities of the 63 diagonals of a sliced 32 x 32 Gram product, by two
+// Karatsuba levels over the slice index (32 -> 16 + 16 -> 8 + 8) and diagonal
+// chains: nine 8 x 8 products instead of one 32 x 32.  X and Y are
+// overwritten.  Bit d of the result = parity of diagonal d.
+__device__ __forceinline__ uint64_t gram32_parities(uint32_t (&X)[32], uint32_t (&Y)[32], const ShiftMuls &mu) {
+    const uint32_t top = mu.hi[0];  // 2^31 at run time
+    // sums of the halves first (gram16_parities overwrites its operands)
+    uint32_t XS[16], YS[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        XS[j] = X[j] ^ X[j + 16];
+        YS[j] = Y[j] ^ Y[j + 16];
+    }
+    const uint64_t A = gram16_parities(X, Y, top);
+    const uint64_t B = gram16_parities(X + 16, Y + 16, top);
+    const uint64_t C = gram16_parities(XS, YS, top);
+    const uint64_t M = A ^ B ^ C;
+    return A ^ (M << 16) ^ (B << 32);
+}
+
+template <int PART>
+__device__ __forceinline__ uint32_t pick64(uint32_t lo, uint32_t hi) {
+    return PART == 0 ? lo : PART == 1 ? hi : (lo ^ hi);
+}
+
+template <int PART>
+__device__ __forceinline__ uint64_t half_product64(const uint32_t *xs, const uint32_t *ys, uint32_t wpb, int vec,
+                                                   uint32_t rot, uint32_t g_first, uint32_t g_step,
+                                                   const ShiftMuls &mu) {
+    uint64_t z = 0;  // parities are linear: XOR of the groups' parities
+    for (uint32_t g0 = 64 * g_first; g0 < wpb; g0 += 64 * g_step) {
+        uint32_t X[32], Y[32];
+        if (vec) {
+            // 16 chunks of 2 elements each, rotated within the group
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+                const uint32_t w = g0 + 4 * ((uint32_t(c) + rot) & 15u);
+                uint4 vx = make_uint4(0, 0, 0, 0), vy = vx;
+                if (w < wpb) {
+                    vx = lds4(xs + w);
+                    vy = lds4(ys + w);
+                }
+                X[2 * c] = pick64<PART>(vx.x, vx.y);
+                X[2 * c + 1] = pick64<PART>(vx.z, vx.w);
+                Y[2 * c] = pick64<PART>(vy.x, vy.y);
+                Y[2 * c + 1] = pick64<PART>(vy.z, vy.w);
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+                const uint32_t w = g0 + 2 * e;
+                const bool in = w < wpb;
+                X[e] = in ? pick64<PART>(xs[w], xs[w + 1]) : 0u;
+                Y[e] = in ? pick64<PART>(ys[w], ys[w + 1]) : 0u;
+            }
+        }
+        slice<32>(X, mu);
+        slice<32>(Y, mu);
+        z ^= gram32_parities(X, Y, mu);
+    }
+    return z;
+}
+
+__device__ __forceinline__ uint64_t combine_q64(uint64_t A, uint64_t B, uint64_t C, const StreamArgs &s) {
+    const uint64_t M = C ^ A ^ B;  // middle term, degree <= 62
+    return reduce_mod_p64(A ^ (M << 32), B ^ (M >> 32), s);
+}
+
+}  // namespace qxd
