@@ -71,14 +71,18 @@ struct RawArgs {
 // 32 blocks, raw periods [p0, p0 + np).
 template <int Q, int B>
 struct SubTile {
+    uint64_t b0;  // first block
     uint64_t p0;
     uint32_t np;
-    bool tma;  // every period lies inside the sample arrays: bulk-copy it
+    uint32_t r0;  // words of period p0 before the sub-tile's first word
+    bool tma;     // every period lies inside the sample arrays: bulk-copy it
     __device__ __forceinline__ SubTile(const RawArgs &a, uint64_t t) {
         using L = RawLayout<Q, B>;
-        const uint64_t b0 = 32 * L::kRows * t;
+        b0 = 32 * L::kRows * t;
         const uint64_t b_end = b0 + 32 * L::kRows < a.s.nblocks ? b0 + 32 * L::kRows : a.s.nblocks;
-        p0 = b0 * L::WPB / L::WP;
+        const uint64_t w = b0 * L::WPB;
+        p0 = w / L::WP;
+        r0 = uint32_t(w - p0 * L::WP);
         np = uint32_t((b_end * L::WPB - 1) / L::WP - p0 + 1);
         tma = 8 * (p0 + np) <= a.nsamples;
     }
@@ -229,12 +233,13 @@ __global__ void __launch_bounds__(32 * kWarps) extract_raw_kernel(const RawArgs 
         for (uint32_t r = 0; r < nrows; ++r) {
             const uint64_t base = 32 * (row0 + r), blk = base + lane;
             const uint64_t lb = blk < s.nblocks ? blk : s.nblocks - 1;
-            const uint64_t w0 = lb * L::WPB;
-            const uint32_t fp_rel = uint32_t((w0 + L::WP - 1) / L::WP - st.p0);  // first whole period
+            // the block's first word, counted from the start of period p0
+            const uint32_t w_rel = st.r0 + uint32_t(lb - st.b0) * uint32_t(L::WPB);
+            const uint32_t fp_rel = (w_rel + L::WP - 1) / L::WP;  // first whole period
             const uint32_t rot = lane_rotation<Q, B>(lane, fp_rel);
             uint32_t ex1 = 0, ey1 = 0, ex2 = 0, ey2 = 0;
             if constexpr (B == 12) {
-                const uint32_t off = uint32_t(w0 % 3);
+                const uint32_t off = w_rel % 3;
                 const uint32_t hp = off ? fp_rel - 1 : fp_rel;             // head period (if any)
                 const uint32_t tp = off != 1 ? fp_rel + L::NPB : fp_rel;  // tail period (if any)
                 edge_words(bx[hp], bx[tp], off, ex1, ex2);
