@@ -521,7 +521,7 @@ def run_gpu(args):
             dom = {"kernel": "pack_kernel_vec<12>", "bytes": pack_bytes, "t": pack_s, "traffic": None}
         per_kernel = {"pack_x_plus_y": round(statistics.mean(pack_ms), 4), "extract": round(statistics.mean(ext_ms), 4)}
     else:
-        # the fused kernel reads both sample arrays once and writes the output
+        # the step kernel reads both sample arrays once and writes the output
         dom = {"kernel": "extract_raw_kernel<16,12> (per-warp TMA pipelines, samples packed in registers)",
                "bytes": 2 * ns * 2 + out_words * 4, "t": ext_s,
                "traffic": measured_traffic("raw_ingest_q16_b12_large_single_stream",

@@ -436,7 +436,7 @@ typedef struct qext_pipeline qext_pipeline; /* opaque, holds device buffers and 
  * blocks (rounded up so that a chunk holds whole samples and whole output
  * words; qext_pipeline_info reports the value used).
  *   b   0: input is packed uint32 words; 8, 12 or 16: raw samples in uint16
- *       containers, extracted by the fused kernel (q in {4, 16, 64}).
+ *       containers, extracted by qext_extract_samples (q in {4, 16, 64}).
  * Errors: INVAL, UNSUPPORTED, CUDA.
  */
 int qext_pipeline_create(const qext_plan *p, uint32_t b, uint64_t chunk_blocks, qext_pipeline **out);

@@ -1,7 +1,7 @@
 // Device primitives of the extraction kernels (sm_103a): register bit-matrix
 // transposes, the sliced GF(2) Gram-diagonal accumulation of Ext_IP
-// (Definition 3.2), parity folding, reduction mod P, output assembly, and the
-// TMA bulk-copy / mbarrier helpers with bounded waits.
+// (Definition 3.2), parities by POPC, reduction mod P, output assembly, and
+// the TMA bulk-copy / mbarrier helpers with bounded waits.
 //
 // Formulation.  For one block, Z = sum_i x_i * y_i in GF(2^q).  Reduction
 // mod P is F_2-linear, so the unreduced sum of carry-less products

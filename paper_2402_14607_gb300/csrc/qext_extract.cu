@@ -2,14 +2,17 @@
 // block loop, for GB300 (sm_103a).  See qext_device.cuh for the sliced GF(2)
 // formulation.
 //
-// Tiled kernel (the main path).  A persistent CTA walks tiles of T
-// consecutive blocks.  Each tile of x and y arrives in shared memory by two
+// Tiled kernel (qext_extract's path; with B != 0 the CTA-tile variant of
+// qext_extract_samples, whose default for q = 4, 16 is the per-warp kernel
+// of qext_extract_raw.cu).  A persistent CTA walks tiles of T consecutive
+// blocks.  Each tile of x and y arrives in shared memory by two
 // 1-D TMA bulk copies (cp.async.bulk, completion on an mbarrier); the copy of
 // the next tile is issued before the current one is computed (two buffers).
 // Each thread (two for q = 64) computes one block from shared memory, reading
 // its 16-byte chunks in a lane-rotated order so that eight consecutive lanes
 // hit eight different bank groups.  Block values go to shared memory and warps
-// assemble m-bit outputs of 32 consecutive blocks into whole words.
+// assemble m-bit outputs of 32 consecutive blocks into whole words.  From raw
+// samples (B != 0) the tile's samples arrive by TMA and are packed in place.
 //
 // Direct kernel (fallback for blocks too long to stage): each thread loads its
 // own block from global memory.
