@@ -80,9 +80,7 @@ __device__ __forceinline__ void compute_tile(const StreamArgs &s, uint64_t first
             if (lb < nb) {
                 const uint32_t *xb = xs + lb * s.wpb, *yb = ys + lb * s.wpb;
                 const int vec = s.wpb % 4 == 0;
-                A = half_product64<0>(xb, yb, s.wpb, vec, tid, part, 2, mu);
-                B = half_product64<1>(xb, yb, s.wpb, vec, tid, part, 2, mu);
-                C = half_product64<2>(xb, yb, s.wpb, vec, tid, part, 2, mu);
+                half_products64(xb, yb, s.wpb, vec, tid, part, 2, mu, A, B, C);
             }
             A ^= __shfl_xor_sync(0xffffffffu, A, 1);
             B ^= __shfl_xor_sync(0xffffffffu, B, 1);

@@ -195,9 +195,7 @@ __global__ void __launch_bounds__(kThreads) extract_tiled_kernel(const TileArgs 
             uint64_t A = 0, Bm = 0, C = 0;
             if (blk < s.nblocks) {
                 const uint32_t *xb = xs + lb * s.wpb, *yb = ys + lb * s.wpb;
-                A = half_product64<0>(xb, yb, s.wpb, ta.vec, tid, part, TPB, ta.mu);
-                Bm = half_product64<1>(xb, yb, s.wpb, ta.vec, tid, part, TPB, ta.mu);
-                C = half_product64<2>(xb, yb, s.wpb, ta.vec, tid, part, TPB, ta.mu);
+                half_products64(xb, yb, s.wpb, ta.vec, tid, part, TPB, ta.mu, A, Bm, C);
             }
             A ^= __shfl_xor_sync(0xffffffffu, A, 1);
             Bm ^= __shfl_xor_sync(0xffffffffu, Bm, 1);
@@ -233,6 +231,7 @@ __global__ void __launch_bounds__(kThreads) extract_direct_kernel(const StreamAr
         if (blk < s.nblocks) {
             const uint32_t *xb = s.x + blk * s.wpb, *yb = s.y + blk * s.wpb;
             if constexpr (Q == 64) {
+                // scalar loads here: the per-part templates beat the one-copy loop
                 const uint64_t A = half_product64<0>(xb, yb, s.wpb, 0, 0, 0, 1, mu);
                 const uint64_t B = half_product64<1>(xb, yb, s.wpb, 0, 0, 0, 1, mu);
                 const uint64_t C = half_product64<2>(xb, yb, s.wpb, 0, 0, 0, 1, mu);

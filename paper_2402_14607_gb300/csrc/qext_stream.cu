@@ -74,9 +74,8 @@ __global__ void __launch_bounds__(kStreamThreads) stream_general_kernel(const Ge
         }
         uint64_t v;
         if constexpr (Q == 64) {
-            const uint64_t A = half_product64<0>(xs, ys, s.wpb, 0, 0, 0, 1, g.mu);
-            const uint64_t B = half_product64<1>(xs, ys, s.wpb, 0, 0, 0, 1, g.mu);
-            const uint64_t C = half_product64<2>(xs, ys, s.wpb, 0, 0, 0, 1, g.mu);
+            uint64_t A = 0, B = 0, C = 0;
+            half_products64(xs, ys, s.wpb, 0, 0, 0, 1, g.mu, A, B, C);
             v = combine_q64(A, B, C, s);
         } else {
             v = block_small_q<Q>(xs, ys, s.wpb, 0, 0, g.mu, s);

@@ -68,15 +68,21 @@ __device__ __forceinline__ uint64_t gram32_parities(uint32_t (&X)[32], uint32_t 
     return A ^ (M << 16) ^ (B << 32);
 }
 
+// The part's word of an element: PART 0 = lo, 1 = hi, 2 = lo ^ hi; PART -1
+// picks at run time, lo or hi by the PRMT selector sel (0x3210 / 0x7654) plus
+// hi & mask (mask = ~0 for lo ^ hi): one code path for several parts keeps
+// the kernels within the instruction cache.
 template <int PART>
-__device__ __forceinline__ uint32_t pick64(uint32_t lo, uint32_t hi) {
+__device__ __forceinline__ uint32_t pick64(uint32_t lo, uint32_t hi, uint32_t sel, uint32_t mask) {
+    if constexpr (PART < 0) return lop_and_xor(hi, mask, __byte_perm(lo, hi, sel));
     return PART == 0 ? lo : PART == 1 ? hi : (lo ^ hi);
 }
 
 template <int PART>
 __device__ __forceinline__ uint64_t half_product64(const uint32_t *xs, const uint32_t *ys, uint32_t wpb, int vec,
                                                    uint32_t rot, uint32_t g_first, uint32_t g_step,
-                                                   const ShiftMuls &mu) {
+                                                   const ShiftMuls &mu, uint32_t sel = 0x3210u,
+                                                   uint32_t mask = 0) {
     uint64_t z = 0;  // parities are linear: XOR of the groups' parities
     for (uint32_t g0 = 64 * g_first; g0 < wpb; g0 += 64 * g_step) {
         uint32_t X[32], Y[32];
@@ -90,18 +96,18 @@ __device__ __forceinline__ uint64_t half_product64(const uint32_t *xs, const uin
                     vx = lds4(xs + w);
                     vy = lds4(ys + w);
                 }
-                X[2 * c] = pick64<PART>(vx.x, vx.y);
-                X[2 * c + 1] = pick64<PART>(vx.z, vx.w);
-                Y[2 * c] = pick64<PART>(vy.x, vy.y);
-                Y[2 * c + 1] = pick64<PART>(vy.z, vy.w);
+                X[2 * c] = pick64<PART>(vx.x, vx.y, sel, mask);
+                X[2 * c + 1] = pick64<PART>(vx.z, vx.w, sel, mask);
+                Y[2 * c] = pick64<PART>(vy.x, vy.y, sel, mask);
+                Y[2 * c + 1] = pick64<PART>(vy.z, vy.w, sel, mask);
             }
         } else {
 #pragma unroll
             for (int e = 0; e < 32; ++e) {
                 const uint32_t w = g0 + 2 * e;
                 const bool in = w < wpb;
-                X[e] = in ? pick64<PART>(xs[w], xs[w + 1]) : 0u;
-                Y[e] = in ? pick64<PART>(ys[w], ys[w + 1]) : 0u;
+                X[e] = in ? pick64<PART>(xs[w], xs[w + 1], sel, mask) : 0u;
+                Y[e] = in ? pick64<PART>(ys[w], ys[w + 1], sel, mask) : 0u;
             }
         }
         slice<32>(X, mu);
@@ -109,6 +115,21 @@ __device__ __forceinline__ uint64_t half_product64(const uint32_t *xs, const uin
         z ^= gram32_parities(X, Y, mu);
     }
     return z;
+}
+
+// A, B and C of one thread's groups with a single copy of half_product64
+// (a run-time loop over the parts).
+__device__ __forceinline__ void half_products64(const uint32_t *xs, const uint32_t *ys, uint32_t wpb, int vec,
+                                                uint32_t rot, uint32_t g_first, uint32_t g_step, const ShiftMuls &mu,
+                                                uint64_t &A, uint64_t &B, uint64_t &C) {
+#pragma unroll 1
+    for (uint32_t part = 0; part < 3; ++part) {
+        const uint64_t r = half_product64<-1>(xs, ys, wpb, vec, rot, g_first, g_step, mu,
+                                              part == 1 ? 0x7654u : 0x3210u, part == 2 ? ~0u : 0u);
+        A = part == 0 ? r : A;
+        B = part == 1 ? r : B;
+        C = part == 2 ? r : C;
+    }
 }
 
 __device__ __forceinline__ uint64_t combine_q64(uint64_t A, uint64_t B, uint64_t C, const StreamArgs &s) {
