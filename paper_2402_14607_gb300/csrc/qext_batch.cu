@@ -248,22 +248,21 @@ extern "C" {
 int qext_batch_create(const qext_batch_item *items, uint32_t nitems, qext_batch **out) {
     if (!out || (nitems && !items)) return QEXT_E_INVAL;
     *out = nullptr;
-    static bool attr = false;
-    if (!attr) {
-        if (cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) !=
-            cudaSuccess)
-            return QEXT_E_CUDA;
-        attr = true;
-    }
+    static qext::DeviceSlots attr_set;
+    const int dev = qext::current_device();
+    if (dev < 0 || attr_set.get(dev, [] {
+            return cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) ==
+                           cudaSuccess ? 1 : 0;
+        }) <= 0)
+        return QEXT_E_CUDA;
     qext_batch *b = new (std::nothrow) qext_batch();
     if (!b) return QEXT_E_INVAL;
     b->cfg.blocks_per_thread_small = 4;
     b->cfg.blocks_per_thread_mid = 1;
     b->cfg.ctas_per_sm = 3;
     b->cfg.order = 0;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev) !=
-                                                  cudaSuccess) {
+    b->sms = qext::sm_count(dev);
+    if (b->sms <= 0) {
         delete b;
         return QEXT_E_CUDA;
     }
@@ -599,13 +598,13 @@ size_t batch_table_bytes() { return sizeof(NoallocScratch); }
 int batch_launch_tables(const qext_batch_item *items, uint32_t nitems, void *d_table, void *h_stage,
                         qext_cuda_stream stream) {
     if (nitems > QEXT_NOALLOC_MAX_ITEMS) return QEXT_E_LIMIT;
-    static bool attr = false;
-    if (!attr) {
-        if (cudaFuncSetAttribute(batch_noalloc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) !=
-            cudaSuccess)
-            return QEXT_E_CUDA;
-        attr = true;
-    }
+    static qext::DeviceSlots attr_set;
+    const int dev = qext::current_device();
+    if (dev < 0 || attr_set.get(dev, [] {
+            return cudaFuncSetAttribute(batch_noalloc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        kSmemBytes) == cudaSuccess ? 1 : 0;
+        }) <= 0)
+        return QEXT_E_CUDA;
     NoallocScratch *h = static_cast<NoallocScratch *>(h_stage);
     h->counter = 0;
     h->nitems = nitems;
@@ -641,10 +640,8 @@ int batch_launch_tables(const qext_batch_item *items, uint32_t nitems, void *d_t
     const size_t bytes = offsetof(NoallocScratch, items) + sizeof(BatchStreamDev) * nitems;
     if (cudaMemcpyAsync(d_table, h_stage, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return QEXT_E_CUDA;
     if (!tiles) return QEXT_OK;
-    int dev = 0, sms = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-        return QEXT_E_CUDA;
+    const int sms = qext::sm_count(dev);
+    if (sms <= 0) return QEXT_E_CUDA;
     const uint64_t cap = uint64_t(sms) * cfg.ctas_per_sm;
     const int grid = int(tiles < cap ? tiles : cap);
     batch_noalloc_kernel<<<grid, kThreads, kSmemBytes, st>>>(static_cast<NoallocScratch *>(d_table),

@@ -245,12 +245,6 @@ __global__ void __launch_bounds__(kThreads) extract_direct_kernel(const StreamAr
     }
 }
 
-struct LaunchCache {
-    int sms = 0;
-    int occ_tiled[24] = {};  // by T (32, 64, 128), buffers (1, 2), fused ingest, raw prefetch
-    int occ_direct = 0;
-    bool attr = false;
-};
 
 template <int Q, int B>
 int launch_q(const StreamArgs &s, const uint16_t *sx, const uint16_t *sy, uint64_t nsamples, cudaStream_t st,
@@ -258,14 +252,13 @@ int launch_q(const StreamArgs &s, const uint16_t *sx, const uint16_t *sy, uint64
     const bool force_direct = B == 0 && (flags & QEXT_F_DIRECT) && !(flags & QEXT_F_TEST_TIMEOUT);
     const uint32_t t_max = (flags & QEXT_F_TILE32) ? 32u : (flags & QEXT_F_TILE64) ? 64u : 128u;
     const uint32_t nb_max = (flags & QEXT_F_NBUF1) ? 1u : 2u;
-    static LaunchCache cache;
+    // per device: SM count, "attribute set", occupancies by tile shape
+    static qext::DeviceSlots attr_set, occ_tiled[24], occ_direct;
     const ShiftMuls mu = make_shift_muls();
-    if (!cache.sms) {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess) return QEXT_E_CUDA;
-        if (cudaDeviceGetAttribute(&cache.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-            return QEXT_E_CUDA;
-    }
+    const int dev = qext::current_device();
+    if (dev < 0) return QEXT_E_CUDA;
+    const int sms = qext::sm_count(dev);
+    if (sms <= 0) return QEXT_E_CUDA;
     constexpr int TPB = QTraits<Q>::TPB;
     // tile size: the largest T (multiple of 32, T * TPB <= kThreads) whose
     // buffers fit the per-CTA budget, double-buffered if possible; the fused
@@ -286,12 +279,11 @@ int launch_q(const StreamArgs &s, const uint16_t *sx, const uint16_t *sy, uint64
                 nbuf = nb;
             }
     if (T && !force_direct) {
-        if (!cache.attr) {
-            if (cudaFuncSetAttribute(extract_tiled_kernel<Q, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     kSmemBudget) != cudaSuccess)
-                return QEXT_E_CUDA;
-            cache.attr = true;
-        }
+        if (attr_set.get(dev, [] {
+                return cudaFuncSetAttribute(extract_tiled_kernel<Q, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            kSmemBudget) == cudaSuccess ? 1 : 0;
+            }) <= 0)
+            return QEXT_E_CUDA;
         TileArgs ta;
         ta.s = s;
         ta.sx = sx;
@@ -322,26 +314,28 @@ int launch_q(const StreamArgs &s, const uint16_t *sx, const uint16_t *sy, uint64
             smem = raw_periods ? size_t(ta.raw_prefetch ? 4 : 2) * 16 * raw_periods : size_t(2) * T * s.wpb * 4;
         }
         const int ti = (T == 32 ? 0 : T == 64 ? 1 : 2) + 3 * int(nbuf - 1) + (B != 0 ? 6 : 0) + 12 * ta.raw_prefetch;
-        int &occ = cache.occ_tiled[ti];
-        if (!occ) {
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, extract_tiled_kernel<Q, B>, int(T * TPB), smem) !=
+        const int occ = occ_tiled[ti].get(dev, [&] {
+            int o = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, extract_tiled_kernel<Q, B>, int(T * TPB), smem) !=
                 cudaSuccess)
-                return QEXT_E_CUDA;
-            if (occ < 1) occ = 1;
-        }
-        const uint64_t cap = uint64_t(cache.sms) * occ;
+                return 0;
+            return o < 1 ? 1 : o;
+        });
+        if (occ <= 0) return QEXT_E_CUDA;
+        const uint64_t cap = uint64_t(sms) * occ;
         const int grid = int(ta.ntiles < cap ? ta.ntiles : cap);
         extract_tiled_kernel<Q, B><<<grid, T * TPB, smem, st>>>(ta);
     } else {
         if (B != 0) return QEXT_E_UNSUPPORTED;  // fused ingest needs a staged tile
-        if (!cache.occ_direct) {
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cache.occ_direct, extract_direct_kernel<Q>, kThreads,
-                                                              0) != cudaSuccess)
-                return QEXT_E_CUDA;
-            if (cache.occ_direct < 1) cache.occ_direct = 1;
-        }
+        const int occd = occ_direct.get(dev, [] {
+            int o = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, extract_direct_kernel<Q>, kThreads, 0) != cudaSuccess)
+                return 0;
+            return o < 1 ? 1 : o;
+        });
+        if (occd <= 0) return QEXT_E_CUDA;
         const uint64_t ctas = (s.nblocks + kThreads - 1) / kThreads;
-        const uint64_t cap = uint64_t(cache.sms) * cache.occ_direct;
+        const uint64_t cap = uint64_t(sms) * occd;
         const int grid = int(ctas < cap ? ctas : cap);
         extract_direct_kernel<Q><<<grid, kThreads, 0, st>>>(s, mu);
     }

@@ -30,7 +30,6 @@ using namespace qxd;
 namespace {
 
 constexpr int kThreads80 = 64;
-constexpr int kMaxDevices80 = 64;
 
 struct Q80Args {
     StreamArgs s;
@@ -291,16 +290,18 @@ int launch_extract_q80(const qext_plan *p, const uint32_t *x, const uint32_t *y,
                        qext_cuda_stream stream) {
     if (p->q != 80) return QEXT_E_UNSUPPORTED;
     if (nblocks == 0) return QEXT_OK;
-    static int grid_cap[kMaxDevices80] = {};
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices80) return QEXT_E_CUDA;
-    if (!grid_cap[dev]) {
-        int sms = 0, occ = 0;
-        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return QEXT_E_CUDA;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, extract_q80_kernel, kThreads80, 0) != cudaSuccess)
-            return QEXT_E_CUDA;
-        grid_cap[dev] = sms * (occ > 0 ? occ : 1);
-    }
+    static DeviceSlots grid_caps;
+    const int dev = current_device();
+    if (dev < 0) return QEXT_E_CUDA;
+    const int grid_cap = grid_caps.get(dev, [dev] {
+        int occ = 0;
+        const int sms = sm_count(dev);
+        if (sms <= 0 || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, extract_q80_kernel, kThreads80, 0) !=
+                            cudaSuccess)
+            return 0;
+        return sms * (occ > 0 ? occ : 1);
+    });
+    if (grid_cap <= 0) return QEXT_E_CUDA;
     Q80Args a;
     a.s.x = x;
     a.s.y = y;
@@ -318,7 +319,7 @@ int launch_extract_q80(const qext_plan *p, const uint32_t *x, const uint32_t *y,
     a.n_p = p->n_p;
     a.zero = 0;
     const uint64_t ctas = (nblocks + kThreads80 - 1) / kThreads80;
-    const int grid = int(ctas < uint64_t(grid_cap[dev]) ? ctas : uint64_t(grid_cap[dev]));
+    const int grid = int(ctas < uint64_t(grid_cap) ? ctas : uint64_t(grid_cap));
     extract_q80_kernel<<<grid, kThreads80, 0, reinterpret_cast<cudaStream_t>(stream)>>>(a);
     return cudaGetLastError() == cudaSuccess ? QEXT_OK : QEXT_E_CUDA;
 }

@@ -37,7 +37,6 @@ using namespace qxd;
 namespace {
 
 constexpr int kWarps = 4;  // warps per CTA, each an independent pipeline
-constexpr int kMaxDevices = 64;
 
 template <int Q, int B>
 struct RawLayout {
@@ -282,38 +281,31 @@ __global__ void __launch_bounds__(32 * kWarps) extract_raw_kernel(const RawArgs 
     (void)next_issued;
 }
 
-struct RawCache {
-    int sms = 0;
-    int occ[2] = {0, 0};  // by buffers per warp
-    bool attr = false;
-};
-
 template <int Q, int B>
 int launch_raw(const StreamArgs &s, const uint16_t *sx, const uint16_t *sy, uint64_t nsamples, cudaStream_t st,
                uint32_t flags) {
     using L = RawLayout<Q, B>;
     if (s.wpb != uint32_t(L::WPB)) return QEXT_E_UNSUPPORTED;
-    static RawCache caches[kMaxDevices];
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return QEXT_E_CUDA;
-    RawCache &c = caches[dev];
+    static qext::DeviceSlots attr_set, occ[2];  // per device; occupancy by buffers per warp
+    const int dev = qext::current_device();
+    if (dev < 0) return QEXT_E_CUDA;
+    const int sms = qext::sm_count(dev);
+    if (sms <= 0) return QEXT_E_CUDA;
     const uint32_t nbuf = (flags & QEXT_F_RAW_PREFETCH) ? 2u : 1u;
     const size_t smem = size_t(kWarps) * nbuf * 2 * L::kCap * sizeof(uint4);
-    if (!c.sms && cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    if (attr_set.get(dev, [] {
+            return cudaFuncSetAttribute(extract_raw_kernel<Q, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        int(size_t(kWarps) * 2 * 2 * L::kCap * sizeof(uint4))) == cudaSuccess ? 1 : 0;
+        }) <= 0)
         return QEXT_E_CUDA;
-    if (!c.attr) {
-        if (cudaFuncSetAttribute(extract_raw_kernel<Q, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 int(size_t(kWarps) * 2 * 2 * L::kCap * sizeof(uint4))) != cudaSuccess)
-            return QEXT_E_CUDA;
-        c.attr = true;
-    }
-    int &occ = c.occ[nbuf - 1];
-    if (!occ) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, extract_raw_kernel<Q, B>, 32 * kWarps, smem) !=
+    const int o = occ[nbuf - 1].get(dev, [&] {
+        int v = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, extract_raw_kernel<Q, B>, 32 * kWarps, smem) !=
             cudaSuccess)
-            return QEXT_E_CUDA;
-        if (occ < 1) occ = 1;
-    }
+            return 0;
+        return v < 1 ? 1 : v;
+    });
+    if (o <= 0) return QEXT_E_CUDA;
     RawArgs a;
     a.s = s;
     a.mu = make_shift_muls();
@@ -323,7 +315,7 @@ int launch_raw(const StreamArgs &s, const uint16_t *sx, const uint16_t *sy, uint
     a.nsub = (s.nblocks + 32 * L::kRows - 1) / (32 * L::kRows);
     a.nbuf = nbuf;
     a.max_polls = kMaxPolls;
-    const uint64_t ctas = (a.nsub + kWarps - 1) / kWarps, cap = uint64_t(c.sms) * occ;
+    const uint64_t ctas = (a.nsub + kWarps - 1) / kWarps, cap = uint64_t(sms) * o;
     const int grid = int(ctas < cap ? ctas : cap);
     extract_raw_kernel<Q, B><<<grid, 32 * kWarps, smem, st>>>(a);
     return cudaGetLastError() == cudaSuccess ? QEXT_OK : QEXT_E_CUDA;

@@ -93,21 +93,23 @@ __global__ void __launch_bounds__(kConsumers + kProducers) extract_fused_kernel(
 template <int Q, int B>
 int launch_fused(const StreamArgs &s, const uint16_t *sx, const uint16_t *sy, uint64_t nsamples,
                  cudaStream_t st) {
-    static int grid_cap = 0;
+    static qext::DeviceSlots grid_caps;
     const size_t smem = size_t(2) * 2 * kTile * s.wpb * 4;
     if (smem > 200 * 1024) return QEXT_E_UNSUPPORTED;
-    if (!grid_cap) {
-        int dev = 0, sms = 0, occ = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess) return QEXT_E_CUDA;
-        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return QEXT_E_CUDA;
-        if (cudaFuncSetAttribute(extract_fused_kernel<Q, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 200 * 1024) != cudaSuccess)
-            return QEXT_E_CUDA;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, extract_fused_kernel<Q, B>,
+    const int dev = qext::current_device();
+    if (dev < 0) return QEXT_E_CUDA;
+    const int grid_cap = grid_caps.get(dev, [&] {
+        int occ = 0;
+        const int sms = qext::sm_count(dev);
+        if (sms <= 0 ||
+            cudaFuncSetAttribute(extract_fused_kernel<Q, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 200 * 1024) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, extract_fused_kernel<Q, B>,
                                                           int(kConsumers + kProducers), smem) != cudaSuccess)
-            return QEXT_E_CUDA;
-        grid_cap = sms * (occ > 0 ? occ : 1);
-    }
+            return 0;
+        return sms * (occ > 0 ? occ : 1);
+    });
+    if (grid_cap <= 0) return QEXT_E_CUDA;
     FusedArgs fa;
     fa.s = s;
     fa.sx = sx;

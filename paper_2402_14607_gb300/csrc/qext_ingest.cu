@@ -120,13 +120,11 @@ int launch_pack(uint32_t b, const uint16_t *samples, uint64_t nsamples, uint32_t
     const uint32_t S = 32 / g, L = b / g;
     const uint64_t nwords = (nsamples * b + 31) / 32;
     const uint64_t nperiods = (nsamples + S - 1) / S;
-    static int grid_cap = 0;
-    if (!grid_cap) {
-        int dev = 0, sms = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess) return QEXT_E_CUDA;
-        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return QEXT_E_CUDA;
-        grid_cap = sms * 8;
-    }
+    const int dev = current_device();
+    if (dev < 0) return QEXT_E_CUDA;
+    const int sms = sm_count(dev);
+    if (sms <= 0) return QEXT_E_CUDA;
+    const int grid_cap = sms * 8;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const bool a16 = reinterpret_cast<uintptr_t>(samples) % 16 == 0;
     const bool o16 = reinterpret_cast<uintptr_t>(out) % 16 == 0;
@@ -149,16 +147,26 @@ int launch_pack(uint32_t b, const uint16_t *samples, uint64_t nsamples, uint32_t
     return cudaGetLastError() == cudaSuccess ? QEXT_OK : QEXT_E_CUDA;
 }
 
+int sm_count(int dev) {
+    static DeviceSlots sms;
+    return sms.get(dev, [dev] {
+        int v = 0;
+        return cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess ? v : 0;
+    });
+}
+
 int *device_status_ptr() {
-    static int *ptrs[64];
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-    if (!ptrs[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, qext_device_status_word) != cudaSuccess) return nullptr;
-        ptrs[dev] = static_cast<int *>(p);
+    static std::atomic<int *> ptrs[kMaxDevices];  // zero-initialised; races store the same address
+    const int dev = current_device();
+    if (dev < 0) return nullptr;
+    int *p = ptrs[dev].load(std::memory_order_relaxed);
+    if (!p) {
+        void *a = nullptr;
+        if (cudaGetSymbolAddress(&a, qext_device_status_word) != cudaSuccess) return nullptr;
+        p = static_cast<int *>(a);
+        ptrs[dev].store(p, std::memory_order_relaxed);
     }
-    return ptrs[dev];
+    return p;
 }
 
 int read_device_status(int *status) {

@@ -1,6 +1,9 @@
 // Internal declarations shared by the translation units of libqext.
 #pragma once
 
+#include <cuda_runtime.h>
+
+#include <atomic>
 #include <cstdint>
 
 #include "../../include/qext.h"
@@ -39,6 +42,35 @@ struct StreamArgs;
 }
 
 namespace qext {
+
+constexpr int kMaxDevices = 64;
+
+// The current device, or -1 (error, or beyond kMaxDevices).
+inline int current_device() {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return -1;
+    return dev;
+}
+
+// A launch fact of one device (SM count, occupancy, "attribute set"),
+// computed on first use and kept for the process.  0 means not yet known;
+// host threads that race on a slot compute and store the same value, so
+// relaxed atomics suffice.  Static instances are zero-initialised.
+struct DeviceSlots {
+    std::atomic<int> v[kMaxDevices];
+    // the slot's value, computing it with f() (> 0 on success) on first use
+    template <typename F>
+    int get(int dev, F f) {
+        int x = v[dev].load(std::memory_order_relaxed);
+        if (x > 0) return x;
+        x = f();
+        if (x > 0) v[dev].store(x, std::memory_order_relaxed);
+        return x;
+    }
+};
+
+// Multiprocessor count of device dev (cached), or 0 on error.
+int sm_count(int dev);
 
 // Field degrees with a GPU kernel.
 bool gpu_q_supported(uint32_t q);

@@ -122,13 +122,13 @@ __global__ void save_pending_kernel(const uint32_t *out, uint64_t word, uint32_t
 template <int Q>
 int launch_general(const GeneralArgs &g, cudaStream_t st) {
     const size_t smem = size_t(kStreamThreads) * 2 * g.s.wpb * 4;
-    static bool attr = false;
-    if (!attr) {
-        if (cudaFuncSetAttribute(stream_general_kernel<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kStreamThreads * 2 * kMaxGeneralWpb * 4) != cudaSuccess)
-            return QEXT_E_CUDA;
-        attr = true;
-    }
+    static qext::DeviceSlots attr_set;
+    const int dev = qext::current_device();
+    if (dev < 0 || attr_set.get(dev, [] {
+            return cudaFuncSetAttribute(stream_general_kernel<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        kStreamThreads * 2 * kMaxGeneralWpb * 4) == cudaSuccess ? 1 : 0;
+        }) <= 0)
+        return QEXT_E_CUDA;
     uint64_t ctas = (g.s.nblocks + kStreamThreads - 1) / kStreamThreads;
     if (ctas > 4096) ctas = 4096;
     stream_general_kernel<Q><<<int(ctas), kStreamThreads, smem, st>>>(g);
