@@ -24,7 +24,7 @@ NVML_CLOCK_SM = 1
 
 
 class ClockSampler:
-    def __init__(self, index: int = 0, period_s: float = 0.002):
+    def __init__(self, index: int = 0, period_s: float = 0.00025):
         self.index = index
         self.period = period_s
         self.samples = []          # (sm_mhz, reasons_mask)
