@@ -90,6 +90,10 @@ def _configure(lib):
     lib.orc_extract_alg2.restype = ctypes.c_int
     lib.orc_alg2_log2_error.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     lib.orc_alg2_log2_error.restype = ctypes.c_double
+    lib.orc_sample_histogram.argtypes = [ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint16), ctypes.c_uint64, u64p]
+    lib.orc_sample_histogram.restype = None
+    lib.orc_min_entropy_estimate.argtypes = [ctypes.c_uint32, u64p]
+    lib.orc_min_entropy_estimate.restype = ctypes.c_double
     lib.orc_pack_samples.argtypes = [ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint16), ctypes.c_uint64, u32p]
     lib.orc_pack_samples.restype = None
     lib.orc_max_q.restype = ctypes.c_int
@@ -203,6 +207,20 @@ def extract_alg2(n_p: int, q1: int, dq: int, nblocks: int, x: np.ndarray, y: np.
 def alg2_log2_error(n_p: int, delta: float, q1: int, dq: int, nblocks: int) -> float:
     """log2 of Theorem 3.3's bound for the first nblocks outputs of Algorithm 2."""
     return _load().orc_alg2_log2_error(n_p, delta, q1, dq, nblocks)
+
+
+def sample_histogram(b: int, samples: np.ndarray, counts: np.ndarray | None = None) -> np.ndarray:
+    """counts[v] += #samples whose low b bits equal v (2^b uint64 counts)."""
+    lib = _load()
+    s = np.ascontiguousarray(samples, dtype=np.uint16)
+    c = np.zeros(1 << b, dtype=np.uint64) if counts is None else counts
+    lib.orc_sample_histogram(b, s.ctypes.data_as(ctypes.POINTER(ctypes.c_uint16)), s.size, _u64(c))
+    return c
+
+
+def min_entropy_estimate(b: int, counts: np.ndarray) -> float:
+    """Plug-in min-entropy -log2(max count / total) of a sample histogram."""
+    return _load().orc_min_entropy_estimate(b, _u64(np.ascontiguousarray(counts, dtype=np.uint64)))
 
 
 def log2_eps_block(n: int, k: float, q: int) -> float:

@@ -431,6 +431,30 @@ void orc_pack_samples(uint32_t b, const uint16_t *samples, uint64_t nsamples, ui
             }
 }
 
+/*
+ * Min-entropy monitoring of the raw samples (Sec. 2: the sources' min-entropy
+ * H_min(X) = -log2 max_x P(X = x) is the quantity the extractor's parameters
+ * rest on).  counts[v] += the number of samples s with (samples[s] & (2^b - 1))
+ * == v, for v < 2^b (bits above b ignored, as for the ingest).
+ */
+void orc_sample_histogram(uint32_t b, const uint16_t *samples, uint64_t nsamples, uint64_t *counts)
+{
+    uint32_t mask = (uint32_t)((1u << b) - 1u);
+    for (uint64_t s = 0; s < nsamples; ++s) counts[samples[s] & mask] += 1;
+}
+
+/* The plug-in estimate -log2(max_v counts[v] / sum_v counts[v]); -1 if empty. */
+double orc_min_entropy_estimate(uint32_t b, const uint64_t *counts)
+{
+    uint64_t total = 0, top = 0;
+    for (uint64_t v = 0; v < ((uint64_t)1 << b); ++v) {
+        total += counts[v];
+        if (counts[v] > top) top = counts[v];
+    }
+    if (!total) return -1.0;
+    return -log2((double)top / (double)total);
+}
+
 int orc_max_q(void) { return ORC_MAXQ; }
 
 int orc_has_openmp(void)
