@@ -357,6 +357,44 @@ def measure_sustained(args, dev):
             "hbm_frac_of_measured": round(2 * nchunks * chunk_bits / 8 / t / 1e9 / measured_peaks()[0], 4)}
 
 
+def measure_monitor(args, dev):
+    """Min-entropy monitoring: qext_sample_histogram over one 2^31-bit chunk of
+    12-bit samples (179M samples, 358 MB, larger than L2; CUDA events over 10
+    launches), and the plug-in estimate per chunk along a stream whose noise
+    level drifts sinusoidally by +-5 % over 8 chunks of 2^24 samples."""
+    import numpy as np
+    import torch
+
+    from paper_2402_14607_gb300 import qext, workloads
+    n = (1 << 31) // 12
+    s = torch.from_numpy(workloads.adc_samples(71, n, 12).view(np.int16)).to(dev)
+    counts = torch.zeros(4096, dtype=torch.int64, device=dev)
+    for _ in range(3):
+        qext.qext_sample_histogram(12, s, n, counts)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(10):
+        qext.qext_sample_histogram(12, s, n, counts)
+    e1.record()
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) * 1e-3 / 10
+    del s
+    chunk, nch = 1 << 24, 8
+    est = []
+    drift = workloads.adc_samples(72, chunk * nch, 12, drift_amp=0.05)
+    d = torch.from_numpy(drift.view(np.int16)).to(dev)
+    for c in range(nch):
+        counts.zero_()
+        qext.qext_sample_histogram(12, d[c * chunk:], chunk, counts)
+        est.append(round(qext.qext_min_entropy_estimate(12, counts.cpu().numpy().view(np.uint64)), 3))
+    return {"workload": "qext_sample_histogram, 12-bit samples: one 2^31-bit chunk (358 MB); drift: 8 chunks of "
+                        "2^24 samples, sigma(t) = 1 + 0.05 sin(2 pi t / T)",
+            "us": round(t * 1e6, 2), "gb_per_s": round(2 * n / t / 1e9, 1),
+            "hbm_frac_of_measured": round(2 * n / t / 1e9 / measured_peaks()[0], 4),
+            "h_min_per_chunk_bits": est, "h_min_analytic_sigma1_bits": round(workloads.adc_min_entropy(12), 3)}
+
+
 def measure_serving(args, dev):
     """Poisson arrivals at 2000 requests/s from 256 channels, 2^10..2^18
     block pairs per request (rounded to multiples of 3 so requests hold whole
@@ -591,6 +629,8 @@ def run_gpu(args):
         extra["alg2"] = measure_alg2(args, dev)
         torch.cuda.empty_cache()
         extra["sustained"] = measure_sustained(args, dev)
+        torch.cuda.empty_cache()
+        extra["monitor"] = measure_monitor(args, dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -462,6 +462,28 @@ int qext_pipeline_run(qext_pipeline *pp, const void *x_host, const void *y_host,
 int qext_device_status(int *status);
 
 /* ------------------------------------------------------------------------
+ * Min-entropy monitoring.  The guarantees rest on the sources' min-entropy
+ * H_min(X) = -log2 max_x P(X = x) (Sec. 2; the rate delta of Algorithms 1 and
+ * 2); a stream whose sources drift is watched through the histogram of its
+ * sample values.
+ * ------------------------------------------------------------------------ */
+/*
+ * qext_sample_histogram -- counts[v] += the number of samples whose low b
+ * bits equal v, for v < 2^b (bits above b ignored, as in the ingest).
+ *   b        1 .. 16;
+ *   samples  DEVICE pointer to nsamples uint16, 2-byte aligned (16-byte
+ *            alignment enables vector loads);
+ *   counts   DEVICE pointer to 2^b uint64, 8-byte aligned; the caller zeroes
+ *            it to start and successive calls accumulate (e.g. per chunk).
+ * Asynchronous on stream.  Errors: INVAL, CUDA.
+ */
+int qext_sample_histogram(uint32_t b, const uint16_t *samples, uint64_t nsamples, uint64_t *counts,
+                          qext_cuda_stream stream);
+/* The plug-in estimate -log2(max_v counts[v] / sum_v counts[v]) of a HOST copy
+ * of such a histogram (2^b entries); -1 if it is empty or b is out of range. */
+double qext_min_entropy_estimate(uint32_t b, const uint64_t *counts_host);
+
+/* ------------------------------------------------------------------------
  * Algorithm 2 (Ext_bs^neq, Sec. 3.3; error: Theorem 3.3): block sizes grow
  * with the block index, q_l = q_1 + l * Delta * b (l = 0, 1, ...), so that a
  * stream of unknown length can be extracted.  n = ceil(24 / (2 delta - 1))

@@ -127,6 +127,9 @@ def lib():
     L.qext_alg2_block_info.argtypes = [vp, u32, P(u32), P(u64), P(u64), P(u64)]
     L.qext_alg2_extract.argtypes = [vp, vp, vp, u32, vp, vp]
     L.qext_alg2_destroy.argtypes = [vp]
+    L.qext_sample_histogram.argtypes = [u32, vp, u64, vp, vp]
+    L.qext_min_entropy_estimate.argtypes = [u32, P(u64)]
+    L.qext_min_entropy_estimate.restype = dbl
     for name in ["qext_plan_create", "qext_destroy", "qext_plan_info", "qext_alg1_params", "qext_extract",
                  "qext_extract_ex", "qext_extract_samples", "qext_extract_samples_ex",
                  "qext_pack_samples", "qext_device_status", "qext_stream_create", "qext_stream_destroy",
@@ -137,7 +140,7 @@ def lib():
                  "qext_server_add_channel", "qext_server_submit", "qext_server_poll", "qext_server_drain",
                  "qext_server_get_stats", "qext_pipeline_create", "qext_pipeline_info", "qext_pipeline_destroy",
                  "qext_pipeline_run", "qext_alg2_plan_create", "qext_alg2_plan_info", "qext_alg2_block_info",
-                 "qext_alg2_extract", "qext_alg2_destroy"]:
+                 "qext_alg2_extract", "qext_alg2_destroy", "qext_sample_histogram"]:
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -555,3 +558,14 @@ def qext_alg2_extract(p: Alg2Plan, x, y, nblocks: int, out, stream=None) -> None
 
 def qext_alg2_destroy(p: Alg2Plan) -> None:
     p.close()
+
+
+def qext_sample_histogram(b: int, samples, nsamples: int, counts, stream=None) -> None:
+    _check(lib().qext_sample_histogram(b, _ptr(samples), nsamples, _ptr(counts), _stream(stream)),
+           "qext_sample_histogram")
+
+
+def qext_min_entropy_estimate(b: int, counts_host) -> float:
+    import numpy as np
+    c = np.ascontiguousarray(counts_host, dtype=np.uint64)
+    return lib().qext_min_entropy_estimate(b, c.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)))
