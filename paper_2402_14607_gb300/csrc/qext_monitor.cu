@@ -4,9 +4,10 @@
 // noise level, an offset) is watched through the histogram of its b-bit
 // sample values and the plug-in estimate -log2(max count / total).
 //
-// Kernel: persistent CTAs; for b <= 13 each CTA counts into a shared-memory
-// histogram (32-bit bins, shared atomics) over a grid-stride walk of 16-byte
-// chunks (8 samples), then adds its non-zero bins to the 64-bit global counts;
+// Kernel: persistent CTAs; for b <= 13 each CTA counts into shared-memory
+// histograms (32-bit bins, shared atomics; 2^13 / 2^b copies, up to one per
+// warp) over a grid-stride walk of 16-byte chunks (8 samples), then adds the
+// non-zero sums of its copies to the 64-bit global counts;
 // wider samples count straight into global memory.  Bits above b are ignored,
 // as in the ingest.
 #include <cuda_runtime.h>
@@ -27,13 +28,17 @@ __global__ void __launch_bounds__(kMonThreads)
                      unsigned long long *__restrict__ counts, int vec) {
     extern __shared__ uint32_t bins[];
     const uint32_t nbins = 1u << b, mask = nbins - 1u;
+    // several copies of the bins (warp w counts into copy w % copies) spread
+    // the shared atomics of the few hot values a noise distribution has
+    const uint32_t copies = kShared ? min(kMonThreads / 32u, (1u << kMaxSmemBits) >> b) : 1u;
+    uint32_t *const mine = bins + ((threadIdx.x >> 5) % copies) * nbins;
     if constexpr (kShared) {
-        for (uint32_t v = threadIdx.x; v < nbins; v += blockDim.x) bins[v] = 0;
+        for (uint32_t v = threadIdx.x; v < copies * nbins; v += blockDim.x) bins[v] = 0;
         __syncthreads();
     }
     auto add = [&](uint32_t v) {
         if constexpr (kShared)
-            atomicAdd(&bins[v & mask], 1u);
+            atomicAdd(&mine[v & mask], 1u);
         else
             atomicAdd(&counts[v & mask], 1ull);
     };
@@ -57,8 +62,11 @@ __global__ void __launch_bounds__(kMonThreads)
     for (uint64_t s = done + tid; s < nsamples; s += stride) add(samples[s]);
     if constexpr (kShared) {
         __syncthreads();
-        for (uint32_t v = threadIdx.x; v < nbins; v += blockDim.x)
-            if (bins[v]) atomicAdd(&counts[v], (unsigned long long)bins[v]);
+        for (uint32_t v = threadIdx.x; v < nbins; v += blockDim.x) {
+            uint32_t total = 0;
+            for (uint32_t c = 0; c < copies; ++c) total += bins[c * nbins + v];
+            if (total) atomicAdd(&counts[v], (unsigned long long)total);
+        }
     }
 }
 
@@ -76,7 +84,7 @@ int qext_sample_histogram(uint32_t b, const uint16_t *samples, uint64_t nsamples
     const int dev = qext::current_device();
     if (dev < 0) return QEXT_E_CUDA;
     const bool shared = b <= kMaxSmemBits;
-    const size_t smem = shared ? (size_t(4) << b) : 0;
+    const size_t smem = shared ? size_t(4) << kMaxSmemBits : 0;  // all copies of the bins
     const int cap = grid_caps[shared].get(dev, [&] {
         int occ = 0;
         const int sms = qext::sm_count(dev);
