@@ -148,7 +148,9 @@ int qext_extract(const qext_plan *p, const uint32_t *x, const uint32_t *y, uint6
 #define QEXT_F_TEST_TIMEOUT 0x10u /* test of failure detection: every CTA arms its tile barrier but issues no
                                    copy, gives up its bounded wait after a few polls, records QEXT_E_TIMEOUT
                                    (qext_device_status) and returns; outputs are not written.  Needs 16-byte
-                                   aligned x, y and a staged tile (else INVAL). */
+                                   aligned x, y and a staged tile (else INVAL).  qext_extract_samples_ex
+                                   accepts it for its per-warp kernel (q = 4, 16 with n_p = 64): every
+                                   warp arms its barrier without a copy (else INVAL). */
 #define QEXT_F_ALL 0x1Fu
 
 /*

@@ -39,7 +39,10 @@ int qext_extract_samples_ex(const qext_plan *p, uint32_t b, const uint16_t *x_sa
                             uint64_t nsamples, uint64_t nblocks, uint32_t *out, qext_cuda_stream stream,
                             uint32_t flags) {
     if (!p) return QEXT_E_INVAL;
-    if (flags & ~uint32_t(QEXT_F_WARP_SPECIALIZED | QEXT_F_RAW_PREFETCH | QEXT_F_CTA_TILES)) return QEXT_E_INVAL;
+    if (flags & ~uint32_t(QEXT_F_WARP_SPECIALIZED | QEXT_F_RAW_PREFETCH | QEXT_F_CTA_TILES | QEXT_F_TEST_TIMEOUT))
+        return QEXT_E_INVAL;
+    // the test of failure detection exists for the per-warp kernel only
+    if ((flags & QEXT_F_TEST_TIMEOUT) && (flags & (QEXT_F_WARP_SPECIALIZED | QEXT_F_CTA_TILES))) return QEXT_E_INVAL;
     if (!p->gpu_supported && !p->gpu_q80) return QEXT_E_UNSUPPORTED;
     if (b != 8 && b != 12 && b != 16) return QEXT_E_UNSUPPORTED;
     if (p->gpu_q80 ? b != 16 : (p->q != 4 && p->q != 16 && p->q != 64)) return QEXT_E_UNSUPPORTED;

@@ -399,6 +399,7 @@ int launch_extract_samples(const qext_plan *p, uint32_t b, const uint16_t *sx, c
     if (!(flags & QEXT_F_CTA_TILES)) {
         const int rc = launch_raw_samples(p->q, b, s, sx, sy, nsamples, stream, flags);
         if (rc != QEXT_E_UNSUPPORTED) return rc;
+        if (flags & QEXT_F_TEST_TIMEOUT) return QEXT_E_INVAL;  // no per-warp kernel for this shape
     }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     switch (b) {

@@ -294,3 +294,33 @@ def test_bounded_wait_times_out_and_context_survives():
     assert qext.qext_device_status() == qext.QEXT_OK          # read clears it
     assert (gpu_extract(plan, x, y, nb) == oracle_extract(plan, x, y, nb)).all()
     assert qext.qext_device_status() == qext.QEXT_OK
+
+
+def test_per_warp_bounded_wait_times_out_and_context_survives():
+    """The same failure detection in the per-warp raw-sample kernel (the
+    default of qext_extract_samples): each warp arms its barrier without a
+    copy, gives up, records QEXT_E_TIMEOUT and returns; the next extraction on
+    the same context is correct."""
+    plan = plan_for(16, 64)
+    nb = 6000
+    ns = -(-nb * 1024 // 12)
+    sx = workloads.adc_samples(81, ns, 12)
+    sy = workloads.adc_samples(82, ns, 12)
+    gx = torch.from_numpy(sx.view(np.int16)).cuda()
+    gy = torch.from_numpy(sy.view(np.int16)).cuda()
+    out = torch.zeros(nb // 2, dtype=torch.int32, device="cuda")
+    assert qext.qext_device_status() == qext.QEXT_OK
+    qext.qext_extract_samples_ex(plan, 12, gx, gy, ns, nb, out, None, qext.QEXT_F_TEST_TIMEOUT)
+    torch.cuda.synchronize()
+    assert qext.qext_device_status() == qext.QEXT_E_TIMEOUT
+    assert qext.qext_device_status() == qext.QEXT_OK
+    with pytest.raises(qext.QextError) as e:   # only the per-warp kernel has the test mode
+        qext.qext_extract_samples_ex(plan, 12, gx, gy, ns, nb, out, None,
+                                     qext.QEXT_F_TEST_TIMEOUT | qext.QEXT_F_CTA_TILES)
+    assert e.value.code == qext.QEXT_E_INVAL
+    qext.qext_extract_samples(plan, 12, gx, gy, ns, nb, out)
+    torch.cuda.synchronize()
+    words = nb * 32
+    want = oracle_extract(plan, oracle.pack_samples(12, sx)[:words], oracle.pack_samples(12, sy)[:words], nb)
+    assert (host_words(out) == want).all()
+    assert qext.qext_device_status() == qext.QEXT_OK
