@@ -676,7 +676,7 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["qext", "reference"], default="qext")
     ap.add_argument("--nblocks", type=int, default=1 << 20, help="block pairs per step per GPU")
     ap.add_argument("--cpu-sample-blocks", type=int, default=1 << 20)
-    ap.add_argument("--ref-sample-blocks", type=int, default=1 << 17)
+    ap.add_argument("--ref-sample-blocks", type=int, default=1 << 15)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched and serving measurements")
     ap.add_argument("--e2e-chunk-blocks", type=int, default=1 << 17)
