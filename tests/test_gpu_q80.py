@@ -72,22 +72,13 @@ def test_samples_b16_match_oracle():
     assert e.value.code == qext.QEXT_E_UNSUPPORTED
 
 
-def test_large_launch_sampled():
-    """2^16 blocks (one launch covering every SM several times), sampled
-    blocks checked against the oracle one by one."""
-    plan = paper_plan()
-    nblocks = 1 << 16
-    words = nblocks * 5680 // 32
-    x = workloads.random_words(5, words)
-    y = workloads.random_words(6, words)
-    out = torch.empty(nblocks * 80 // 32, dtype=torch.int32, device="cuda")
-    qext.qext_extract(plan, dev_words(x), dev_words(y), nblocks, out)
-    torch.cuda.synchronize()
-    got = host_words(out)
-    rng = np.random.Generator(np.random.PCG64(3))
+def check_sampled(plan, x, y, got, nblocks, seed):
+    """Blocks drawn at random (plus both ends), each recomputed by the oracle
+    alone from its own 5680 bits, re-based on a word boundary."""
+    rng = np.random.Generator(np.random.PCG64(seed))
     for l in np.unique(np.concatenate([rng.integers(0, nblocks, 200), [0, 1, nblocks - 2, nblocks - 1]])):
         l = int(l)
-        # block l is bits [5680 l, 5680 (l+1)): re-base it on a word boundary
+        # block l is bits [5680 l, 5680 (l+1))
         bits0 = 5680 * l
         w0, sh = bits0 // 32, bits0 % 32
         def blockwords(a):
@@ -102,3 +93,37 @@ def test_large_launch_sampled():
             have |= int(got[(80 * l) // 32 + i]) << (32 * i) if (80 * l) // 32 + i < got.size else 0
         have = (have >> ((80 * l) % 32)) & ((1 << 80) - 1)
         assert have == want, l
+
+
+def test_large_launch_sampled():
+    """2^16 blocks (one launch covering every SM several times), sampled
+    blocks checked against the oracle one by one."""
+    plan = paper_plan()
+    nblocks = 1 << 16
+    words = nblocks * 5680 // 32
+    x = workloads.random_words(5, words)
+    y = workloads.random_words(6, words)
+    out = torch.empty(nblocks * 80 // 32, dtype=torch.int32, device="cuda")
+    qext.qext_extract(plan, dev_words(x), dev_words(y), nblocks, out)
+    torch.cuda.synchronize()
+    check_sampled(plan, x, y, host_words(out), nblocks, 3)
+
+
+def test_paper_workload_full_size_sampled():
+    """The paper's parameters at the size and in the launch the benchmark
+    times: 2^18 block pairs of seeded 16-bit ADC samples (seeds 51 / 52)
+    through qext_extract_samples; the packed stream of 16-bit samples is the
+    samples' little-endian words."""
+    plan = qext.qext_plan_create(5680, 80, 0.67125 * 5680, 2.0 ** -30)
+    assert (plan.info["q"], plan.info["n_p"], plan.info["m"]) == (80, 71, 80)
+    nb = 1 << 18
+    ns = nb * 5680 // 16
+    sx = workloads.adc_samples(51, ns, 16)
+    sy = workloads.adc_samples(52, ns, 16)
+    out = torch.full((nb * 80 // 32 + 1,), -1, dtype=torch.int32, device="cuda")
+    qext.qext_extract_samples(plan, 16, torch.from_numpy(sx.view(np.int16)).cuda(),
+                              torch.from_numpy(sy.view(np.int16)).cuda(), ns, nb, out)
+    torch.cuda.synchronize()
+    got = host_words(out)
+    assert got[-1] == 0xFFFFFFFF, "wrote past the output"
+    check_sampled(plan, oracle.pack_samples(16, sx), oracle.pack_samples(16, sy), got[:-1], nb, 5)
