@@ -12,10 +12,16 @@ __device__ __forceinline__ uint4 lds4(const uint32_t *p) { return *reinterpret_c
 // ---------------------------------------------------------------------------
 // Accumulator of one block's sliced Gram diagonals, q <= 32.
 // ---------------------------------------------------------------------------
+// q = 16: one Karatsuba level over the element bits, with low half L (bits
+// 0..7), high half H (8..15) and sum S = L + H of each element:
+//     x y = A + t^8 (A + B + C) + t^16 B,   A = LxLy, B = HxHy, C = SxSy,
+//         = D + t^8 D + t^8 C,             D = A + t^8 B.
+// So A and B accumulate into one array D (A at offset 0, B at offset 8; 23
+// diagonals) and C into its own (15): 38 accumulators and parities.
 template <int Q>
 struct Acc {
     static constexpr bool kKaratsuba = Q == 16;
-    static constexpr int NA = kKaratsuba ? 45 : 2 * Q - 1;
+    static constexpr int NA = kKaratsuba ? 38 : 2 * Q - 1;
     uint32_t a[NA];
     __device__ __forceinline__ Acc() {
 #pragma unroll
@@ -24,9 +30,7 @@ struct Acc {
     // Sliced group of 32 elements: X[j], Y[j] = bit j of the 32 elements.
     __device__ __forceinline__ void add(uint32_t (&X)[Q], uint32_t (&Y)[Q]) {
         if constexpr (kKaratsuba) {
-            // one Karatsuba level over the element bits: low half L (bits
-            // 0..7), high half H (8..15), sum S = L + H
-            uint32_t *A = a, *B = a + 15, *C = a + 30;
+            uint32_t *D = a, *C = a + 23;
             uint32_t XS[8], YS[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
@@ -37,8 +41,8 @@ struct Acc {
             for (int j = 0; j < 8; ++j)
 #pragma unroll
                 for (int l = 0; l < 8; ++l) {
-                    A[j + l] = lop_and_xor(X[j], Y[l], A[j + l]);
-                    B[j + l] = lop_and_xor(X[j + 8], Y[l + 8], B[j + l]);
+                    D[j + l] = lop_and_xor(X[j], Y[l], D[j + l]);
+                    D[j + l + 8] = lop_and_xor(X[j + 8], Y[l + 8], D[j + l + 8]);
                     C[j + l] = lop_and_xor(XS[j], YS[l], C[j + l]);
                 }
         } else {
@@ -46,16 +50,14 @@ struct Acc {
         }
     }
     // z (2q-1 bits) = parities of the Gram diagonals
-    __device__ __forceinline__ uint64_t unreduced(const ShiftMuls &mu) {
+    __device__ __forceinline__ uint64_t unreduced() {
         if constexpr (kKaratsuba) {
-            // z = A + x^16 B + x^8 (C - A - B) on the parities of the three
-            // 15-word products (parity is linear); each r holds its 15
-            // parity bits in bits 17..31
-            const uint32_t rA = parity_bits32_top<15>(a, mu), rB = parity_bits32_top<15>(a + 15, mu),
-                           rC = parity_bits32_top<15>(a + 30, mu);
-            return lop_xor3(rA >> 17, rB >> 1, lop_xor3(rA, rB, rC) >> 9);
+            // z = D + t^8 D + t^8 C on the parities (parity is linear): rD
+            // holds D's 23 parity bits in bits 9..31, rC C's 15 in bits 17..31
+            const uint32_t rD = parity_bits32_top<23>(a), rC = parity_bits32_top<15>(a + 23);
+            return lop_xor3(rD >> 9, rD >> 1, rC >> 9);
         } else {
-            return parity_bits64<2 * Q - 1>(a, mu);
+            return parity_bits64<2 * Q - 1>(a);
         }
     }
 };
@@ -91,7 +93,7 @@ __device__ __forceinline__ uint64_t block_small_q(const uint32_t *xs, const uint
                 slice<Q>(Y, mu);
                 acc.add(X, Y);
             }
-            return reduce_mod_p<Q>(acc.unreduced(mu), s);
+            return reduce_mod_p<Q>(acc.unreduced(), s);
         }
     }
     if (vec) {
@@ -156,7 +158,7 @@ __device__ __forceinline__ uint64_t block_small_q(const uint32_t *xs, const uint
             acc.add(X, Y);
         }
     }
-    return reduce_mod_p<Q>(acc.unreduced(mu), s);
+    return reduce_mod_p<Q>(acc.unreduced(), s);
 }
 
 // ---------------------------------------------------------------------------

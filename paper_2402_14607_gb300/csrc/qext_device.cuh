@@ -23,9 +23,10 @@
 
 namespace qxd {
 
-// 2^G and 2^(32-G) for G = 1, 2, 4 (index log2 G).  Passed at run time so the
-// shifts of the transpose stages issue as IMAD / IMAD.HI on the FMA pipe
-// instead of SHF on the ALU pipe, which the AND/XOR work already saturates.
+// 2^G and 2^(32-G) for G = 1, 2, 4 (index log2 G).  Passed at run time so
+// that shifts written as multiplies stay IMAD / IMAD.HI on the FMA pipe.  The
+// q = 80 kernel (latency-bound) slices that way; elsewhere plain shifts, which
+// the compiler places itself, measured faster.
 struct ShiftMuls {
     uint32_t lo[3];  // 2^G
     uint32_t hi[3];  // 2^(32-G): umulhi(a, 2^(32-G)) = a >> G
@@ -89,8 +90,9 @@ __device__ __forceinline__ uint32_t lop_xor3(uint32_t a, uint32_t b, uint32_t c)
 
 // One exchange stage of a recursive bit transpose between words a and b:
 // in every 2G-bit lane, a keeps its low G bits and receives b's low G bits
-// on top; b receives a's high G bits below its own high G bits.
-template <int G>
+// on top; b receives a's high G bits below its own high G bits.  kMul: the
+// shifts as run-time multiplies (see ShiftMuls).
+template <int G, bool kMul>
 __device__ __forceinline__ void exchange(uint32_t &a, uint32_t &b, const ShiftMuls &mu) {
     if constexpr (G == 16) {
         const uint32_t na = __byte_perm(a, b, 0x5410), nb = __byte_perm(a, b, 0x7632);
@@ -102,8 +104,8 @@ __device__ __forceinline__ void exchange(uint32_t &a, uint32_t &b, const ShiftMu
         b = nb;
     } else {
         constexpr uint32_t M = low_mask<G>();
-        const uint32_t up = b * mu.lo[log2_of<G>()];           // b << G   (IMAD)
-        const uint32_t dn = __umulhi(a, mu.hi[log2_of<G>()]);  // a >> G   (IMAD.HI)
+        const uint32_t up = kMul ? b * mu.lo[log2_of<G>()] : b << G;           // b << G
+        const uint32_t dn = kMul ? __umulhi(a, mu.hi[log2_of<G>()]) : a >> G;  // a >> G
         const uint32_t na = lop_select(a, up, M);
         const uint32_t nb = lop_select(dn, b, M);
         a = na;
@@ -114,19 +116,19 @@ __device__ __forceinline__ void exchange(uint32_t &a, uint32_t &b, const ShiftMu
 // Transpose stages G = N/2 .. 1 over N words.  With N = Q <= 32 and Q-bit
 // elements packed 32/Q per word, word j afterwards holds bit j of every
 // element; with N = 32 it is the full 32x32 bit transpose.
-template <int N, int G>
+template <int N, int G, bool kMul>
 __device__ __forceinline__ void slice_stages(uint32_t (&w)[N], const ShiftMuls &mu) {
     if constexpr (G >= 1) {
 #pragma unroll
         for (int i = 0; i < N; ++i)
-            if ((i & G) == 0) exchange<G>(w[i], w[i + G], mu);
-        slice_stages<N, G / 2>(w, mu);
+            if ((i & G) == 0) exchange<G, kMul>(w[i], w[i + G], mu);
+        slice_stages<N, G / 2, kMul>(w, mu);
     }
 }
 
-template <int N>
+template <int N, bool kMul = false>
 __device__ __forceinline__ void slice(uint32_t (&w)[N], const ShiftMuls &mu) {
-    if constexpr (N > 1) slice_stages<N, N / 2>(w, mu);
+    if constexpr (N > 1) slice_stages<N, N / 2, kMul>(w, mu);
 }
 
 // acc[j + l] ^= X[j] & Y[l] for j < NX, l < NY (offsets into the arrays).
@@ -139,26 +141,23 @@ __device__ __forceinline__ void gram_diagonals(const uint32_t *X, const uint32_t
         for (int l = 0; l < NY; ++l) acc[j + l] = lop_and_xor(X[j], Y[l], acc[j + l]);
 }
 
-// Parities of K <= 32 words.  POPC runs on the XU pipe and the bits are put
-// together by IMADs on the FMA pipe, which leaves the ALU pipe (saturated by
-// the AND/XOR work) alone:
+// Parities of K <= 32 words, one POPC each:
 //     r = (r >> 1) + (popc(acc[k]) << 31)        for k = 0 .. K-1
 // puts parity(acc[k]) in bit 32 - K + k (no carries: r >> 1 has bit 31
 // clear and popc << 31 keeps only the popcount's low bit).
 template <int K>
-__device__ __forceinline__ uint32_t parity_bits32_top(const uint32_t *acc, const ShiftMuls &mu) {
+__device__ __forceinline__ uint32_t parity_bits32_top(const uint32_t *acc) {
     static_assert(K >= 1 && K <= 32, "1..32 words");
-    const uint32_t top = mu.hi[0];  // 2^31 at run time, so the multiplies stay IMADs
     uint32_t r = 0;
 #pragma unroll
-    for (int k = 0; k < K; ++k) r = __umulhi(r, top) + uint32_t(__popc(acc[k])) * top;
+    for (int k = 0; k < K; ++k) r = (r >> 1) + (uint32_t(__popc(acc[k])) << 31);
     return r;
 }
 
 // bit k of the result = parity(acc[k]) for k < K (K <= 32).
 template <int K>
-__device__ __forceinline__ uint32_t parity_bits32(const uint32_t *acc, const ShiftMuls &mu) {
-    const uint32_t r = parity_bits32_top<K>(acc, mu);
+__device__ __forceinline__ uint32_t parity_bits32(const uint32_t *acc) {
+    const uint32_t r = parity_bits32_top<K>(acc);
     if constexpr (K == 32) {
         return r;
     } else {
@@ -167,11 +166,11 @@ __device__ __forceinline__ uint32_t parity_bits32(const uint32_t *acc, const Shi
 }
 
 template <int K>
-__device__ __forceinline__ uint64_t parity_bits64(const uint32_t *acc, const ShiftMuls &mu) {
+__device__ __forceinline__ uint64_t parity_bits64(const uint32_t *acc) {
     if constexpr (K <= 32) {
-        return parity_bits32<K>(acc, mu);
+        return parity_bits32<K>(acc);
     } else {
-        return uint64_t(parity_bits32<32>(acc, mu)) | (uint64_t(parity_bits32<K - 32>(acc + 32, mu)) << 32);
+        return uint64_t(parity_bits32<32>(acc)) | (uint64_t(parity_bits32<K - 32>(acc + 32)) << 32);
     }
 }
 

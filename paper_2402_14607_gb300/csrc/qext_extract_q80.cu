@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(kThreads80, 6) extract_q80_kernel(const Q80Arg
                 {
                     uint32_t R[32];
                     load_part32<0>(ws, after(w0, dep, a.zero), odd, g, a.n_p, sel32, a.zero, R);
-                    slice<32>(R, a.mu);
+                    slice<32, true>(R, a.mu);
 #pragma unroll
                     for (int k = 0; k < 32; ++k) col[k * kThreads80] = R[k];
                     dep = R[31];
@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(kThreads80, 6) extract_q80_kernel(const Q80Arg
                 {
                     uint32_t R[32];
                     load_part32<1>(ws, after(w0, dep, a.zero), odd, g, a.n_p, sel32, a.zero, R);
-                    slice<32>(R, a.mu);
+                    slice<32, true>(R, a.mu);
 #pragma unroll
                     for (int k = 0; k < 32; ++k) col[(32 + k) * kThreads80] = R[k];
                     dep = R[31];
@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(kThreads80, 6) extract_q80_kernel(const Q80Arg
                 {
                     uint32_t R[16];
                     load_part16(ws, after(w0, dep, a.zero), odd, g, a.n_p, sel16, R);
-                    slice<16>(R, a.mu);
+                    slice<16, true>(R, a.mu);
 #pragma unroll
                     for (int k = 0; k < 16; ++k) col[(64 + k) * kThreads80] = R[k];
                     dep = R[15];

@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(32 * kWarps) extract_raw_kernel(const RawArgs 
                 slice<Q>(Y, a.mu);
                 acc.add(X, Y);
             }
-            uint64_t v = reduce_mod_p<Q>(acc.unreduced(a.mu), s) & mask_m(s.m);
+            uint64_t v = reduce_mod_p<Q>(acc.unreduced(), s) & mask_m(s.m);
             if (blk >= s.nblocks) v = 0;
             store_warp(v, base, s.nblocks, s.m, s.out);
         }
