@@ -680,7 +680,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched and serving measurements")
     ap.add_argument("--e2e-chunk-blocks", type=int, default=1 << 17)
-    ap.add_argument("--serving-requests", type=int, default=300)
+    ap.add_argument("--serving-requests", type=int, default=1000)
     ap.add_argument("--unfused", action="store_true",
                     help="step = qext_pack_samples x2 + qext_extract instead of the fused qext_extract_samples")
     ap.add_argument("--traffic", type=float, default=None,

@@ -189,17 +189,19 @@ struct PeriodOf {
     static constexpr int kWords = B == 12 ? 3 : B == 8 ? 2 : 4;
 };
 
+// 12-bit sample pair q = s | t << 16 -> bits 0..23 of s | t << 12: bits
+// 0..11 from q, bits 12..23 from q >> 4.  The bits of s and t above 12 fall
+// outside bits 0..23 (t's land in byte 3), which the byte permutes below
+// never take.
+__device__ __forceinline__ uint32_t pack_pair12(uint32_t q) {
+    return lop_select(q, __umulhi(q, 1u << 28), 0x00000FFFu);
+}
+
 template <int B>
 __device__ __forceinline__ void pack_period8(const uint4 v, uint32_t (&w)[PeriodOf<B>::kWords]) {
     if constexpr (B == 12) {
-        // each sample pair q = s | t << 16 -> bits 0..23 of P = s | t << 12:
-        // bits 0..11 from q, bits 12..23 from q >> 4.  The bits of s and t
-        // above 12 fall outside bits 0..23 (t's land in byte 3), and the byte
-        // permutes below take bytes 0..2 of each P only.
-        const uint32_t q[4] = {v.x, v.y, v.z, v.w};
-        uint32_t P[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) P[j] = lop_select(q[j], __umulhi(q[j], 1u << 28), 0x00000FFFu);
+        // word j = bytes of the packed pairs P_j, P_j+1 (bytes 0..2 of each)
+        const uint32_t P[4] = {pack_pair12(v.x), pack_pair12(v.y), pack_pair12(v.z), pack_pair12(v.w)};
         w[0] = __byte_perm(P[0], P[1], 0x4210);
         w[1] = __byte_perm(P[1], P[2], 0x5421);
         w[2] = __byte_perm(P[2], P[3], 0x6542);

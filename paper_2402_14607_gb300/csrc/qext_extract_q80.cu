@@ -13,7 +13,7 @@
 // with Pab = (xa + xb)(ya + yb), Paa = xa ya.  Each is accumulated over the
 // block's elements as sliced Gram-diagonal parities, 32 elements per group:
 // the 32-bit parts by a 32 x 32 transpose (element e in slot e) and
-// gram32_parities, x2 by slice<16> with elements k and k+16 in word k (which
+// gram32_parities_3x16, x2 by slice<16> with elements k and k+16 in word k (which
 // also puts element e in slot e, so x0 + x2 is a slot-wise XOR of slices).
 // Parities are linear, so groups and Karatsuba parts combine after the
 // POPCs; the 159-bit sum is reduced mod P once per block.
@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(kThreads80, 6) extract_q80_kernel(const Q80Arg
                         Y[k] ^= cy[(64 + k) * kThreads80];
                     }
                 }
-                const uint64_t r = gram32_parities(X, Y, a.mu);
+                const uint64_t r = gram32_parities_3x16(X, Y, a.mu);
                 p11 ^= pr == 0 ? r : 0;
                 p12 ^= pr == 1 ? r : 0;
                 p01 ^= pr == 2 ? r : 0;

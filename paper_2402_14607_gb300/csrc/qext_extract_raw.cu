@@ -147,12 +147,23 @@ __device__ __forceinline__ void raw_group(const uint4 *bx, const uint4 *by, uint
 // b = 12 edge words: off = (first word of the block) mod 3.
 //   off 0: no head word, tail words T0, T1;  off 1: head H1, H2, no tail;
 //   off 2: head H2, tail T0.
-__device__ __forceinline__ void edge_words(uint4 h, uint4 t, uint32_t off, uint32_t &e1, uint32_t &e2) {
-    uint32_t H[3], T[3];
-    pack_period8<12>(h, H);
-    pack_period8<12>(t, T);
-    e1 = off == 0 ? T[0] : off == 1 ? H[1] : H[2];
-    e2 = off == 0 ? T[1] : off == 1 ? H[2] : T[0];
+// Word w of a period is a byte permute of its packed sample pairs w and w+1
+// (pack_period8), so the four sample pairs behind the two edge words are
+// picked first and only they are packed.
+struct EdgeSel {
+    uint32_t off, s1, s2;  // off, and the byte-permute selectors of the two edge words
+    __device__ __forceinline__ explicit EdgeSel(uint32_t o)
+        : off(o), s1(o == 0 ? 0x4210u : o == 1 ? 0x5421u : 0x6542u), s2(o == 0 ? 0x5421u : o == 1 ? 0x6542u : 0x4210u) {}
+};
+
+__device__ __forceinline__ void edge_words(uint4 h, uint4 t, const EdgeSel &es, uint32_t &e1, uint32_t &e2) {
+    const uint32_t off = es.off;
+    const uint32_t u0 = off == 0 ? t.x : off == 1 ? h.y : h.z;
+    const uint32_t u1 = off == 0 ? t.y : off == 1 ? h.z : h.w;
+    const uint32_t u2 = off == 0 ? t.y : off == 1 ? h.z : t.x;
+    const uint32_t u3 = off == 0 ? t.z : off == 1 ? h.w : t.y;
+    e1 = __byte_perm(pack_pair12(u0), pack_pair12(u1), es.s1);
+    e2 = __byte_perm(pack_pair12(u2), pack_pair12(u3), es.s2);
 }
 
 template <int Q, int B>
@@ -243,8 +254,9 @@ __global__ void __launch_bounds__(32 * kWarps) extract_raw_kernel(const RawArgs 
                 const uint32_t off = w_rel % 3;
                 const uint32_t hp = off ? fp_rel - 1 : fp_rel;             // head period (if any)
                 const uint32_t tp = off != 1 ? fp_rel + L::NPB : fp_rel;  // tail period (if any)
-                edge_words(bx[hp], bx[tp], off, ex1, ex2);
-                edge_words(by[hp], by[tp], off, ey1, ey2);
+                const EdgeSel es(off);
+                edge_words(bx[hp], bx[tp], es, ex1, ex2);
+                edge_words(by[hp], by[tp], es, ey1, ey2);
             }
             Acc<Q> acc;
             {

@@ -50,9 +50,11 @@ __device__ __forceinline__ uint32_t gram16_parities(uint32_t *X, uint32_t *Y, ui
 
 // Parities of the 63 diagonals of a sliced 32 x 32 Gram product, by two
 // Karatsuba levels over the slice index (32 -> 16 + 16 -> 8 + 8) and diagonal
-// chains: nine 8 x 8 products instead of one 32 x 32.  X and Y are
+// chains: nine 8 x 8 products instead of one 32 x 32, combined as three
+// 16 x 16 products (135 diagonal parities; the q = 80 kernel, latency-bound,
+// measured faster with this form than with gram32_parities).  X and Y are
 // overwritten.  Bit d of the result = parity of diagonal d.
-__device__ __forceinline__ uint64_t gram32_parities(uint32_t (&X)[32], uint32_t (&Y)[32], const ShiftMuls &mu) {
+__device__ __forceinline__ uint64_t gram32_parities_3x16(uint32_t (&X)[32], uint32_t (&Y)[32], const ShiftMuls &mu) {
     const uint32_t top = mu.hi[0];  // 2^31 at run time
     // sums of the halves first (gram16_parities overwrites its operands)
     uint32_t XS[16], YS[16];
@@ -66,6 +68,70 @@ __device__ __forceinline__ uint64_t gram32_parities(uint32_t (&X)[32], uint32_t 
     const uint64_t C = gram16_parities(XS, YS, top);
     const uint64_t M = A ^ B ^ C;
     return A ^ (M << 16) ^ (B << 32);
+}
+
+
+// Parity chain of the diagonals D0 .. D1-1 of sum_b t^(S b) (X_b x Y_b),
+// where X_b = X[O0 + OSTEP b .. + 8) and likewise Y_b: diagonal d takes the
+// pairs j + l = d - S b of block b.  One live accumulator; bit
+// 32 - (D1 - D0) + (d - D0) of the result is the parity of diagonal d.
+template <int NB, int O0, int OSTEP, int S, int D0, int D1>
+__device__ __forceinline__ uint32_t block_chain(const uint32_t *X, const uint32_t *Y, uint32_t top) {
+    static_assert(D1 - D0 >= 1 && D1 - D0 <= 32, "one word of parities");
+    uint32_t c = 0;
+#pragma unroll
+    for (int d = D0; d < D1; ++d) {
+        uint32_t acc = 0;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const int k = d - S * b, o = O0 + OSTEP * b;
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (k - j >= 0 && k - j < 8) acc = lop_and_xor(X[o + j], Y[o + k - j], acc);
+        }
+        c = __umulhi(c, top) + uint32_t(__popc(acc)) * top;
+    }
+    return c;
+}
+
+// Parities of the 63 diagonals of a sliced 32 x 32 Gram product by two
+// Karatsuba levels over the slice index (32 -> 16 + 16 -> 8 + 8), nine 8 x 8
+// products.  With halves L, H and sum S at each level,
+//     u v = A + t^h (A + B + C) + t^2h B = D (1 + t^h) + t^h C,  D = A + t^h B,
+// so products whose results are added at a fixed shift share one chain:
+//     R = E (1 + t^8)(1 + t^16) + t^8 F (1 + t^16) + t^16 DC (1 + t^8) + t^24 SC
+// with E = A_LL + t^8 A_HH + t^16 B_LL + t^24 B_HH (the four diagonal 8 x 8
+// blocks), F = A_SS + t^16 B_SS, DC = C_LL + t^8 C_HH, SC = C_SS (A, B, C
+// the 16 x 16 products of the outer level): 107 diagonal parities instead
+// of 135.  X and Y are overwritten.  Bit d of the result = parity of
+// diagonal d.
+__device__ __forceinline__ uint64_t gram32_parities(uint32_t (&X)[32], uint32_t (&Y)[32], const ShiftMuls &mu) {
+    const uint32_t top = mu.hi[0];  // 2^31 at run time
+    const uint64_t E = uint64_t(block_chain<4, 0, 8, 8, 0, 32>(X, Y, top)) |
+                       (uint64_t(block_chain<4, 0, 8, 8, 32, 39>(X, Y, top) >> 25) << 32);
+    // inner sums of A's and B's halves (words 8.. and 24..)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        X[8 + j] ^= X[j];
+        Y[8 + j] ^= Y[j];
+        X[24 + j] ^= X[16 + j];
+        Y[24 + j] ^= Y[16 + j];
+    }
+    const uint64_t F = uint64_t(block_chain<1, 8, 0, 0, 0, 15>(X, Y, top) >> 17) |
+                       (uint64_t(block_chain<1, 24, 0, 0, 0, 15>(X, Y, top) >> 17) << 16);
+    // outer sum (words 0..15) and its inner half sum (words 24..31)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        X[j] ^= X[16 + j];
+        Y[j] ^= Y[16 + j];
+        X[24 + j] ^= X[8 + j];
+        Y[24 + j] ^= Y[8 + j];
+        X[8 + j] = X[24 + j] ^ X[j];
+        Y[8 + j] = Y[24 + j] ^ Y[j];
+    }
+    const uint64_t DC = block_chain<2, 0, 8, 8, 0, 23>(X, Y, top) >> 9;
+    const uint64_t SC = block_chain<1, 24, 0, 0, 0, 15>(X, Y, top) >> 17;
+    return E ^ ((E ^ F) << 8) ^ ((E ^ DC) << 16) ^ ((E ^ F ^ DC ^ SC) << 24);
 }
 
 // The part's word of an element: PART 0 = lo, 1 = hi, 2 = lo ^ hi; PART -1
