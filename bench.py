@@ -579,6 +579,13 @@ def run_gpu(args):
                 "peak_source": ("measured hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured"
                                 else "fallback 6.8 TB/s"),
                 "per_kernel_ms": per_kernel,
+                # the same step counted by the packed-stream figure per block,
+                # 2 n / 8 bytes in + m / 8 out (the ingest's raw uint16 samples
+                # left out): the scale on which the packed-input kernels sit
+                "packed_bits_view": {
+                    "bytes_per_block": 2 * spec.n // 8 + info["m"] / 8,
+                    "achieved": round((2 * spec.n // 8 + info["m"] / 8) * spec.nblocks / ext_s / 1e9, 1),
+                    "frac": round((2 * spec.n // 8 + info["m"] / 8) * spec.nblocks / ext_s / 1e9 / peak, 4)},
                 "kernel_time": ("per-kernel CUDA events in the timed region" if args.unfused else
                                 "timed region / K on the launching stream (one kernel per step)")}
 
