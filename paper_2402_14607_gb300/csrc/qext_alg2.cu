@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(kAlg2Threads)
                 const uint32_t c = eb < n_p ? s[uint64_t(eb) * k] : 0u;
                 w[i] = a | (c << 16);
             }
-            slice<16>(w, mu);
+            slice<16>(w);
 #pragma unroll
             for (int i = 0; i < 16; ++i) S[src][u][i] = w[i];
         }

@@ -89,7 +89,7 @@ __device__ __forceinline__ void compute_tile(const StreamArgs &s, uint64_t first
         }
     } else {
         for (uint32_t lb = tid; lb < nb; lb += kThreads)
-            vals[lb] = block_small_q<Q>(xs + lb * s.wpb, ys + lb * s.wpb, s.wpb, s.wpb % 4 == 0, tid, mu, s) &
+            vals[lb] = block_small_q<Q>(xs + lb * s.wpb, ys + lb * s.wpb, s.wpb, s.wpb % 4 == 0, tid, s) &
                        mask_m(s.m);
     }
 }

@@ -66,7 +66,7 @@ struct Acc {
 // With vec, the block's 16-byte chunks are read starting at chunk rot.
 template <int Q>
 __device__ __forceinline__ uint64_t block_small_q(const uint32_t *xs, const uint32_t *ys, uint32_t wpb, int vec,
-                                                  uint32_t rot, const ShiftMuls &mu, const StreamArgs &s) {
+                                                  uint32_t rot, const StreamArgs &s) {
     Acc<Q> acc;
     if constexpr (Q >= 4) {
         if (vec && wpb == 2 * Q) {
@@ -89,8 +89,8 @@ __device__ __forceinline__ uint64_t block_small_q(const uint32_t *xs, const uint
                     Y[4 * c + 2] = vy.z;
                     Y[4 * c + 3] = vy.w;
                 }
-                slice<Q>(X, mu);
-                slice<Q>(Y, mu);
+                slice<Q>(X);
+                slice<Q>(Y);
                 acc.add(X, Y);
             }
             return reduce_mod_p<Q>(acc.unreduced(), s);
@@ -121,8 +121,8 @@ __device__ __forceinline__ uint64_t block_small_q(const uint32_t *xs, const uint
                     Y[4 * c + 2] = vy.z;
                     Y[4 * c + 3] = vy.w;
                 }
-                slice<Q>(X, mu);
-                slice<Q>(Y, mu);
+                slice<Q>(X);
+                slice<Q>(Y);
                 acc.add(X, Y);
             }
         } else {
@@ -139,8 +139,8 @@ __device__ __forceinline__ uint64_t block_small_q(const uint32_t *xs, const uint
                         X[i] = wx[g * Q + i];
                         Y[i] = wy[g * Q + i];
                     }
-                    slice<Q>(X, mu);
-                    slice<Q>(Y, mu);
+                    slice<Q>(X);
+                    slice<Q>(Y);
                     acc.add(X, Y);
                 }
             }
@@ -153,8 +153,8 @@ __device__ __forceinline__ uint64_t block_small_q(const uint32_t *xs, const uint
                 X[i] = g0 + i < wpb ? xs[g0 + i] : 0u;
                 Y[i] = g0 + i < wpb ? ys[g0 + i] : 0u;
             }
-            slice<Q>(X, mu);
-            slice<Q>(Y, mu);
+            slice<Q>(X);
+            slice<Q>(Y);
             acc.add(X, Y);
         }
     }

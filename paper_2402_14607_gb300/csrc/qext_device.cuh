@@ -23,12 +23,10 @@
 
 namespace qxd {
 
-// 2^G and 2^(32-G) for G = 1, 2, 4 (index log2 G).  Passed at run time so
-// that shifts written as multiplies stay IMAD / IMAD.HI on the FMA pipe.  The
-// q = 80 kernel (latency-bound) slices that way; elsewhere plain shifts, which
-// the compiler places itself, measured faster.
+// 2^(32-G) for G = 1, 2, 4 (index log2 G), passed at run time so
+// that shifts written as multiplies stay IMAD / IMAD.HI (the POPC chains of
+// the wide fields use 2^31).
 struct ShiftMuls {
-    uint32_t lo[3];  // 2^G
     uint32_t hi[3];  // 2^(32-G): umulhi(a, 2^(32-G)) = a >> G
 };
 
@@ -48,10 +46,7 @@ struct StreamArgs {
 
 __host__ __device__ inline ShiftMuls make_shift_muls() {
     ShiftMuls mu;
-    for (int i = 0; i < 3; ++i) {
-        mu.lo[i] = 1u << (1 << i);
-        mu.hi[i] = 1u << (32 - (1 << i));
-    }
+    for (int i = 0; i < 3; ++i) mu.hi[i] = 1u << (32 - (1 << i));
     return mu;
 }
 
@@ -61,11 +56,6 @@ __host__ __device__ inline ShiftMuls make_shift_muls() {
 template <int G>
 __device__ __forceinline__ constexpr uint32_t low_mask() {
     return G == 1 ? 0x55555555u : G == 2 ? 0x33333333u : G == 4 ? 0x0F0F0F0Fu : G == 8 ? 0x00FF00FFu : 0x0000FFFFu;
-}
-
-template <int G>
-__device__ __forceinline__ constexpr int log2_of() {
-    return G == 1 ? 0 : G == 2 ? 1 : 2;
 }
 
 // Single LOP3 instructions (truth tables over a = 0xF0, b = 0xCC, c = 0xAA).
@@ -90,10 +80,10 @@ __device__ __forceinline__ uint32_t lop_xor3(uint32_t a, uint32_t b, uint32_t c)
 
 // One exchange stage of a recursive bit transpose between words a and b:
 // in every 2G-bit lane, a keeps its low G bits and receives b's low G bits
-// on top; b receives a's high G bits below its own high G bits.  kMul: the
-// shifts as run-time multiplies (see ShiftMuls).
-template <int G, bool kMul>
-__device__ __forceinline__ void exchange(uint32_t &a, uint32_t &b, const ShiftMuls &mu) {
+// on top; b receives a's high G bits below its own high G bits.  (Shifts
+// written as run-time multiplies measured slower in every kernel.)
+template <int G>
+__device__ __forceinline__ void exchange(uint32_t &a, uint32_t &b) {
     if constexpr (G == 16) {
         const uint32_t na = __byte_perm(a, b, 0x5410), nb = __byte_perm(a, b, 0x7632);
         a = na;
@@ -104,8 +94,7 @@ __device__ __forceinline__ void exchange(uint32_t &a, uint32_t &b, const ShiftMu
         b = nb;
     } else {
         constexpr uint32_t M = low_mask<G>();
-        const uint32_t up = kMul ? b * mu.lo[log2_of<G>()] : b << G;           // b << G
-        const uint32_t dn = kMul ? __umulhi(a, mu.hi[log2_of<G>()]) : a >> G;  // a >> G
+        const uint32_t up = b << G, dn = a >> G;
         const uint32_t na = lop_select(a, up, M);
         const uint32_t nb = lop_select(dn, b, M);
         a = na;
@@ -116,19 +105,19 @@ __device__ __forceinline__ void exchange(uint32_t &a, uint32_t &b, const ShiftMu
 // Transpose stages G = N/2 .. 1 over N words.  With N = Q <= 32 and Q-bit
 // elements packed 32/Q per word, word j afterwards holds bit j of every
 // element; with N = 32 it is the full 32x32 bit transpose.
-template <int N, int G, bool kMul>
-__device__ __forceinline__ void slice_stages(uint32_t (&w)[N], const ShiftMuls &mu) {
+template <int N, int G>
+__device__ __forceinline__ void slice_stages(uint32_t (&w)[N]) {
     if constexpr (G >= 1) {
 #pragma unroll
         for (int i = 0; i < N; ++i)
-            if ((i & G) == 0) exchange<G, kMul>(w[i], w[i + G], mu);
-        slice_stages<N, G / 2, kMul>(w, mu);
+            if ((i & G) == 0) exchange<G>(w[i], w[i + G]);
+        slice_stages<N, G / 2>(w);
     }
 }
 
-template <int N, bool kMul = false>
-__device__ __forceinline__ void slice(uint32_t (&w)[N], const ShiftMuls &mu) {
-    if constexpr (N > 1) slice_stages<N, N / 2, kMul>(w, mu);
+template <int N>
+__device__ __forceinline__ void slice(uint32_t (&w)[N]) {
+    if constexpr (N > 1) slice_stages<N, N / 2>(w);
 }
 
 // acc[j + l] ^= X[j] & Y[l] for j < NX, l < NY (offsets into the arrays).

@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(kThreads) extract_tiled_kernel(const TileArgs 
             if (part == 0) vals[lb] = v;
         } else {
             if (blk < s.nblocks)
-                v = block_small_q<Q>(xs + lb * s.wpb, ys + lb * s.wpb, s.wpb, ta.vec, tid, ta.mu, s) &
+                v = block_small_q<Q>(xs + lb * s.wpb, ys + lb * s.wpb, s.wpb, ta.vec, tid, s) &
                     mask_m(s.m);
             vals[lb] = v;
         }
@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(kThreads) extract_direct_kernel(const StreamAr
                 const uint64_t C = half_product64<2>(xb, yb, s.wpb, 0, 0, 0, 1, mu);
                 v = combine_q64(A, B, C, s);
             } else {
-                v = block_small_q<Q>(xb, yb, s.wpb, 0, 0, mu, s);
+                v = block_small_q<Q>(xb, yb, s.wpb, 0, 0, s);
             }
             v &= mask_m(s.m);
         }

@@ -5,7 +5,9 @@
 // Layout.  Block l is stream bits [l*n, (l+1)*n), n = 80 n_p, element i its
 // bits [80i, 80i+80).  Both l*n and 80i are multiples of 16, so every element
 // starts on a 16-bit boundary: its parts x0 (bits 0..31), x1 (32..63) and
-// x2 (64..79) are read from one or two stream words with one PRMT.
+// x2 (64..79) are read from one or two stream words with one PRMT.  The
+// loads of a warp's 32 blocks are coalesced through a shared staging array
+// (load_part32).
 //
 // Product.  Three-way Karatsuba over the parts (six products instead of
 // nine):  x*y = P00 + t^32 (P01 - P00 - P11) + t^64 (P02 - P00 - P22 + P11)
@@ -38,60 +40,76 @@ struct Q80Args {
     uint32_t zero;  // always 0 (see after())
 };
 
-// Raw operand of one product for elements 32g + e, e < 32 (element e in word
-// e): part A (0: bits 0..31, 1: bits 32..63), plus part 1 (kAdd1) and/or the
-// zero-extended x2 = bits 64..79 (kAddX2).  The block's bit 0 is bit 16*odd of
-// word w0; element e starts at bit 16 * ((odd + e) & 1) of its first word,
-// which sel[e & 1] undoes (PRMT 0x5432: from bit 16, 0x3210: from bit 0).
-// Elements past n_p read as 0.
 // Left alone, the compilers overlap the products of a group (loads and
 // slicing of the next product hoisted into the previous one: several hundred
-// registers).  Each product's operand addresses therefore depend on the
-// previous product's parity word through a run-time zero (`zero` = 0, a kernel
-// argument): w0 + (parity & zero) cannot be formed before that product ends.
-__device__ __forceinline__ uint64_t after(uint64_t w0, uint64_t done, uint32_t zero) {
-    return w0 + (uint32_t(done) & zero);
+// registers).  Each load therefore takes its blocks' base through a run-time
+// zero (`zero` = 0, a kernel argument) added to the previous result: base +
+// (value & zero) cannot be formed before that value exists.
+__device__ __forceinline__ uint64_t after(uint64_t base, uint64_t done, uint32_t zero) {
+    return base + (uint32_t(done) & zero);
 }
 
-// 32-bit part A (0: bits 0..31, 1: bits 32..63) of elements 32g + e, e < 32
-// (element e in word e).  The block's bit 0 is bit 16*odd of word w0; element
-// e starts at bit 16 * ((odd + e) & 1) of its first word, which sel[e & 1]
-// undoes (PRMT 0x5432: from bit 16, 0x3210: from bit 0).  Past n_p: 0.
-// Loads go in batches of 8 elements (16 in flight): each batch's addresses
-// wait for the previous batch's first value through the run-time zero.
+// Operand loads through a per-warp staging array.  Thread t of a warp owns
+// block base + t, whose elements lie 710 bytes (n / 8) apart from the next
+// block's: one element per thread would touch 32 lines per load.  Instead
+// lane j loads element 32g + j of each of the warp's 32 blocks in turn (the
+// 32 lanes read 320 consecutive bytes: three lines per load), the values go
+// through shared memory (row b = block b, rows padded to an odd number of
+// words so that both the row writes and the column reads are conflict-free)
+// and each thread reads back its own block's row.  Blocks past nblocks
+// repeat the last block (their outputs are not stored); elements past n_p
+// read as 0.  A block's bit 0 and every element start on a 16-bit boundary,
+// so a part is one PRMT of the two words it touches.
+constexpr uint32_t kStageRow32 = 33;  // words per staged row of 32-bit parts
+constexpr uint32_t kStageRow16 = 17;  // words per staged row of x2 pairs
+constexpr uint32_t kStageWords = 32 * kStageRow32;
+
+// 32-bit part A (0: bits 0..31, 1: bits 32..63) of elements 32g + e, e < 32,
+// of the thread's block: R[e] (element e in word e).
 template <int A>
-__device__ __forceinline__ void load_part32(const uint32_t *__restrict__ w, uint64_t w0, uint32_t odd, uint32_t g,
-                                            uint32_t n_p, const uint32_t (&sel)[2], uint32_t zero,
+__device__ __forceinline__ void load_part32(const uint32_t *__restrict__ w, uint64_t base, uint64_t nblocks,
+                                            uint64_t n, uint32_t g, uint32_t n_p, uint32_t *stage,
                                             uint32_t (&R)[32]) {
-#pragma unroll
-    for (int e = 0; e < 32; ++e) {
-        if (e % 8 == 0 && e) w0 = after(w0, R[e - 8], zero);
-        const uint32_t elem = 32 * g + uint32_t(e);
-        const uint32_t in = elem < n_p;
-        const uint32_t bit = 16 * odd + 80 * (in ? elem : 0u) + 32 * A;
-        const uint32_t *p = w + w0 + (bit >> 5);
-        const uint32_t v = __byte_perm(__ldg(p), __ldg(p + 1), sel[e & 1]);
-        R[e] = in ? v : 0u;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t elem = 32 * g + lane;
+    const bool in = elem < n_p;
+    const uint64_t off = 80ull * (in ? elem : 0u) + 32 * A;
+#pragma unroll 16
+    for (uint32_t b = 0; b < 32; ++b) {
+        const uint64_t blk = base + b < nblocks ? base + b : nblocks - 1;
+        const uint64_t bit = blk * n + off;
+        const uint32_t *p = w + (bit >> 5);
+        const uint32_t v = __byte_perm(__ldg(p), __ldg(p + 1), (bit & 16u) ? 0x5432u : 0x3210u);
+        stage[b * kStageRow32 + lane] = in ? v : 0u;
     }
+    __syncwarp();
+#pragma unroll
+    for (int e = 0; e < 32; ++e) R[e] = stage[lane * kStageRow32 + e];
+    __syncwarp();  // the next load reuses the stage
 }
 
-// x2 parts (bits 64..79) of elements 32g + k and 32g + k + 16 in word k.
-__device__ __forceinline__ void load_part16(const uint32_t *__restrict__ w, uint64_t w0, uint32_t odd, uint32_t g,
-                                            uint32_t n_p, const uint32_t (&sel)[2], uint32_t (&R)[16]) {
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-        uint32_t v[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const uint32_t elem = 32 * g + uint32_t(k + 16 * h);
-            const uint32_t el = elem < n_p ? elem : 0u;
-            const uint32_t bit = 16 * odd + 80 * el + 64;
-            v[h] = elem < n_p ? __ldg(w + w0 + (bit >> 5)) : 0u;
-        }
-        // low half from element k, high half from element k + 16; both start
-        // at the same half-word position (80 * 16 = 0 mod 32)
-        R[k] = __byte_perm(v[0], v[1], sel[k & 1]);
+// x2 parts (bits 64..79) of elements 32g + k and 32g + k + 16 in word k of
+// R (low and high half), k < 16, of the thread's block.
+__device__ __forceinline__ void load_part16(const uint32_t *__restrict__ w, uint64_t base, uint64_t nblocks,
+                                            uint64_t n, uint32_t g, uint32_t n_p, uint32_t *stage,
+                                            uint32_t (&R)[16]) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t elem = 32 * g + lane;
+    const bool in = elem < n_p;
+    const uint64_t off = 80ull * (in ? elem : 0u) + 64;
+#pragma unroll 16
+    for (uint32_t b = 0; b < 32; ++b) {
+        const uint64_t blk = base + b < nblocks ? base + b : nblocks - 1;
+        const uint64_t bit = blk * n + off;
+        const uint32_t word = __ldg(w + (bit >> 5));
+        const uint32_t v = in ? ((bit & 16u) ? word >> 16 : word & 0xFFFFu) : 0u;
+        const uint32_t hi = __shfl_down_sync(0xffffffffu, v, 16);  // element 32g + lane + 16
+        if (lane < 16) stage[b * kStageRow16 + lane] = v | (hi << 16);
     }
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < 16; ++k) R[k] = stage[lane * kStageRow16 + k];
+    __syncwarp();
 }
 
 // z (159 bits: z0 = bits 0..63, z1 = 64..127, z2 = 128..158) mod P, P = x^80 +
@@ -164,7 +182,9 @@ __global__ void __launch_bounds__(kThreads80, 6) extract_q80_kernel(const Q80Arg
     // per thread: 80 sliced words of each source, interleaved across threads
     // (word k of thread t at k * kThreads80 + t: conflict-free)
     __shared__ uint32_t slices[2 * 80 * kThreads80];
+    __shared__ uint32_t stages[kThreads80 / 32][kStageWords];
     uint32_t *const sl = slices + threadIdx.x;
+    uint32_t *const stage = stages[threadIdx.x >> 5];
     const StreamArgs &s = a.s;
     const uint32_t lane = threadIdx.x & 31u;
     const uint64_t warp = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
@@ -173,13 +193,6 @@ __global__ void __launch_bounds__(kThreads80, 6) extract_q80_kernel(const Q80Arg
     const uint32_t ngroups = (a.n_p + 31) / 32;
     for (uint64_t base = warp * 32; base < s.nblocks; base += nwarps * 32) {
         const uint64_t blk = base + lane;
-        const uint64_t lb = blk < s.nblocks ? blk : s.nblocks - 1;
-        const uint64_t bit0 = lb * n;
-        const uint64_t w0 = bit0 >> 5;
-        const uint32_t odd = uint32_t(bit0 >> 4) & 1u;  // block starts at bit 16 of w0
-        const uint32_t sel32[2] = {odd ? 0x5432u : 0x3210u, odd ? 0x3210u : 0x5432u};
-        // word k of the x2 slices: elements k, k + 16 (same alignment)
-        const uint32_t sel16[2] = {odd ? 0x7632u : 0x5410u, odd ? 0x5410u : 0x7632u};
         uint64_t p00 = 0, p11 = 0, p01 = 0, p02 = 0, p12 = 0;
         uint32_t p22 = 0;
         for (uint32_t g = 0; g < ngroups; ++g) {
@@ -193,24 +206,24 @@ __global__ void __launch_bounds__(kThreads80, 6) extract_q80_kernel(const Q80Arg
                 uint32_t *const col = sl + src * 80 * kThreads80;
                 {
                     uint32_t R[32];
-                    load_part32<0>(ws, after(w0, dep, a.zero), odd, g, a.n_p, sel32, a.zero, R);
-                    slice<32, true>(R, a.mu);
+                    load_part32<0>(ws, after(base, dep, a.zero), s.nblocks, n, g, a.n_p, stage, R);
+                    slice<32>(R);
 #pragma unroll
                     for (int k = 0; k < 32; ++k) col[k * kThreads80] = R[k];
                     dep = R[31];
                 }
                 {
                     uint32_t R[32];
-                    load_part32<1>(ws, after(w0, dep, a.zero), odd, g, a.n_p, sel32, a.zero, R);
-                    slice<32, true>(R, a.mu);
+                    load_part32<1>(ws, after(base, dep, a.zero), s.nblocks, n, g, a.n_p, stage, R);
+                    slice<32>(R);
 #pragma unroll
                     for (int k = 0; k < 32; ++k) col[(32 + k) * kThreads80] = R[k];
                     dep = R[31];
                 }
                 {
                     uint32_t R[16];
-                    load_part16(ws, after(w0, dep, a.zero), odd, g, a.n_p, sel16, R);
-                    slice<16, true>(R, a.mu);
+                    load_part16(ws, after(base, dep, a.zero), s.nblocks, n, g, a.n_p, stage, R);
+                    slice<16>(R);
 #pragma unroll
                     for (int k = 0; k < 16; ++k) col[(64 + k) * kThreads80] = R[k];
                     dep = R[15];

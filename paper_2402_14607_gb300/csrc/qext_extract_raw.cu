@@ -57,7 +57,6 @@ struct RawLayout {
 
 struct RawArgs {
     StreamArgs s;
-    ShiftMuls mu;
     const uint16_t *sx;
     const uint16_t *sy;
     uint64_t nsamples;
@@ -262,8 +261,8 @@ __global__ void __launch_bounds__(32 * kWarps) extract_raw_kernel(const RawArgs 
             {
                 uint32_t X[Q], Y[Q];
                 raw_group<Q, B, 0>(bx, by, fp_rel, rot, ex1, ey1, X, Y);
-                slice<Q>(X, a.mu);
-                slice<Q>(Y, a.mu);
+                slice<Q>(X);
+                slice<Q>(Y);
                 acc.add(X, Y);
             }
             {
@@ -283,8 +282,8 @@ __global__ void __launch_bounds__(32 * kWarps) extract_raw_kernel(const RawArgs 
                         }
                     }
                 }
-                slice<Q>(X, a.mu);
-                slice<Q>(Y, a.mu);
+                slice<Q>(X);
+                slice<Q>(Y);
                 acc.add(X, Y);
             }
             uint64_t v = reduce_mod_p<Q>(acc.unreduced(), s) & mask_m(s.m);
@@ -322,7 +321,6 @@ int launch_raw(const StreamArgs &s, const uint16_t *sx, const uint16_t *sy, uint
     if (o <= 0) return QEXT_E_CUDA;
     RawArgs a;
     a.s = s;
-    a.mu = make_shift_muls();
     a.sx = sx;
     a.sy = sy;
     a.nsamples = nsamples;

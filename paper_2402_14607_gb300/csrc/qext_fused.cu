@@ -31,7 +31,6 @@ struct FusedArgs {
     const uint16_t *sy;
     uint64_t nsamples;
     uint64_t ntiles;
-    ShiftMuls mu;
 };
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
@@ -82,7 +81,7 @@ __global__ void __launch_bounds__(kConsumers + kProducers) extract_fused_kernel(
             const uint64_t blk = tile * kTile + tid;
             uint64_t v = 0;
             if (blk < s.nblocks)
-                v = block_small_q<Q>(xs + tid * s.wpb, ys + tid * s.wpb, s.wpb, s.wpb % 4 == 0, tid, fa.mu, s) &
+                v = block_small_q<Q>(xs + tid * s.wpb, ys + tid * s.wpb, s.wpb, s.wpb % 4 == 0, tid, s) &
                     mask_m(s.m);
             mbar_arrive(&empty[b]);
             store_warp(v, tile * kTile + (tid & ~31u), s.nblocks, s.m, s.out);
@@ -116,7 +115,6 @@ int launch_fused(const StreamArgs &s, const uint16_t *sx, const uint16_t *sy, ui
     fa.sy = sy;
     fa.nsamples = nsamples;
     fa.ntiles = (s.nblocks + kTile - 1) / kTile;
-    fa.mu = make_shift_muls();
     const int grid = int(fa.ntiles < uint64_t(grid_cap) ? fa.ntiles : uint64_t(grid_cap));
     extract_fused_kernel<Q, B><<<grid, kConsumers + kProducers, smem, st>>>(fa);
     return cudaGetLastError() == cudaSuccess ? QEXT_OK : QEXT_E_CUDA;

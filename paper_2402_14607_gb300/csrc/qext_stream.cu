@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(kStreamThreads) stream_general_kernel(const Ge
             half_products64(xs, ys, s.wpb, 0, 0, 0, 1, g.mu, A, B, C);
             v = combine_q64(A, B, C, s);
         } else {
-            v = block_small_q<Q>(xs, ys, s.wpb, 0, 0, g.mu, s);
+            v = block_small_q<Q>(xs, ys, s.wpb, 0, 0, s);
         }
         v &= mask_m(s.m);
         // OR the value into the zeroed output at bit g.out_bit0 + j*m

@@ -176,8 +176,8 @@ __device__ __forceinline__ uint64_t half_product64(const uint32_t *xs, const uin
                 Y[e] = in ? pick64<PART>(ys[w], ys[w + 1], sel, mask) : 0u;
             }
         }
-        slice<32>(X, mu);
-        slice<32>(Y, mu);
+        slice<32>(X);
+        slice<32>(Y);
         z ^= gram32_parities(X, Y, mu);
     }
     return z;
