@@ -477,6 +477,14 @@ def run_gpu(args):
     dev = torch.device("cuda", local)
     qbuild.build()
     qext.lib()
+    if args.only:
+        # one extra measurement alone (profiling captures of its kernel)
+        fn = {"batched": measure_batched, "serving": measure_serving, "paper_params": measure_paper_params,
+              "alg2": measure_alg2, "sustained": measure_sustained, "monitor": measure_monitor}[args.only]
+        res = fn(args, dev)
+        if rank == 0:
+            print(json.dumps({"only": args.only, args.only: res}), flush=True)
+        return 0
 
     spec = workload_spec(rank, args.nblocks)
     plan = qext.qext_plan_create(spec.n, 0, spec.k, spec.eps)
@@ -686,6 +694,8 @@ def main(argv=None):
     ap.add_argument("--ref-sample-blocks", type=int, default=1 << 15)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched and serving measurements")
+    ap.add_argument("--only", choices=["batched", "serving", "paper_params", "alg2", "sustained", "monitor"],
+                    default=None, help="run only this extra measurement and print it (for kernel profiles)")
     ap.add_argument("--e2e-chunk-blocks", type=int, default=1 << 17)
     ap.add_argument("--serving-requests", type=int, default=1000)
     ap.add_argument("--unfused", action="store_true",
