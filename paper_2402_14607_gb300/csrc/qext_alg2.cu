@@ -54,7 +54,7 @@ constexpr uint32_t kMaxUnits = 16;  // q_l <= 256
 
 __global__ void __launch_bounds__(kAlg2Threads)
     alg2_kernel(const Alg2Block *__restrict__ table, uint32_t n_p, const uint16_t *__restrict__ x,
-                const uint16_t *__restrict__ y, uint16_t *__restrict__ out, const ShiftMuls mu) {
+                const uint16_t *__restrict__ y, uint16_t *__restrict__ out) {
     __shared__ uint32_t S[2][kMaxUnits][16];  // sliced units of the current group
     __shared__ uint32_t z[kMaxUnits + 1];     // unreduced sum, 2 q_l - 1 bits
     const Alg2Block blk = table[blockIdx.x];
@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(kAlg2Threads)
                 X[i] = S[0][u][i];
                 Y[i] = S[1][v][i];
             }
-            const uint32_t c = diagonal_chain<16>(X, Y, mu.hi[0]) >> 1;  // diagonal d at bit d
+            const uint32_t c = diagonal_chain<16>(X, Y) >> 1;  // diagonal d at bit d
             const uint32_t off = u + v;                                   // in 16-bit units
             if (off & 1u) {
                 atomicXor(&z[off >> 1], c << 16);
@@ -225,8 +225,7 @@ int qext_alg2_extract(const qext_alg2_plan *p, const uint16_t *x, const uint16_t
     if (!x || !y || !out || reinterpret_cast<uintptr_t>(x) % 2 || reinterpret_cast<uintptr_t>(y) % 2 ||
         reinterpret_cast<uintptr_t>(out) % 2)
         return QEXT_E_INVAL;
-    alg2_kernel<<<nblocks, kAlg2Threads, 0, reinterpret_cast<cudaStream_t>(stream)>>>(p->d_blocks, p->n_p, x, y, out,
-                                                                                       make_shift_muls());
+    alg2_kernel<<<nblocks, kAlg2Threads, 0, reinterpret_cast<cudaStream_t>(stream)>>>(p->d_blocks, p->n_p, x, y, out);
     return cudaGetLastError() == cudaSuccess ? QEXT_OK : QEXT_E_CUDA;
 }
 

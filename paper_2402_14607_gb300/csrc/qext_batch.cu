@@ -70,7 +70,7 @@ __device__ __forceinline__ void load_tile(const StreamArgs &s, uint64_t first, u
 
 template <int Q>
 __device__ __forceinline__ void compute_tile(const StreamArgs &s, uint64_t first, uint32_t nb, const uint32_t *xs,
-                                             const uint32_t *ys, uint64_t *vals, const ShiftMuls &mu) {
+                                             const uint32_t *ys, uint64_t *vals) {
     const uint32_t tid = threadIdx.x;
     if constexpr (Q == 64) {
         // two threads per block, 64 blocks per pass
@@ -80,7 +80,7 @@ __device__ __forceinline__ void compute_tile(const StreamArgs &s, uint64_t first
             if (lb < nb) {
                 const uint32_t *xb = xs + lb * s.wpb, *yb = ys + lb * s.wpb;
                 const int vec = s.wpb % 4 == 0;
-                half_products64(xb, yb, s.wpb, vec, tid, part, 2, mu, A, B, C);
+                half_products64(xb, yb, s.wpb, vec, tid, part, 2, A, B, C);
             }
             A ^= __shfl_xor_sync(0xffffffffu, A, 1);
             B ^= __shfl_xor_sync(0xffffffffu, B, 1);
@@ -96,7 +96,7 @@ __device__ __forceinline__ void compute_tile(const StreamArgs &s, uint64_t first
 
 __global__ void __launch_bounds__(kThreads) batch_kernel(const BatchStreamDev *__restrict__ items,
                                                          const BatchTileDev *__restrict__ tiles, uint32_t ntiles,
-                                                         uint32_t *counter, const ShiftMuls mu) {
+                                                         uint32_t *counter) {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t next_tile;
@@ -130,13 +130,13 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(const BatchStreamDev *_
         for (uint32_t i = tid; i < ((tl.nb + 31u) & ~31u); i += kThreads) vals[i] = 0;
         __syncthreads();
         switch (it.q) {
-            case 1: compute_tile<1>(s, tl.first, tl.nb, xs, ys, vals, mu); break;
-            case 2: compute_tile<2>(s, tl.first, tl.nb, xs, ys, vals, mu); break;
-            case 4: compute_tile<4>(s, tl.first, tl.nb, xs, ys, vals, mu); break;
-            case 8: compute_tile<8>(s, tl.first, tl.nb, xs, ys, vals, mu); break;
-            case 16: compute_tile<16>(s, tl.first, tl.nb, xs, ys, vals, mu); break;
-            case 32: compute_tile<32>(s, tl.first, tl.nb, xs, ys, vals, mu); break;
-            default: compute_tile<64>(s, tl.first, tl.nb, xs, ys, vals, mu); break;
+            case 1: compute_tile<1>(s, tl.first, tl.nb, xs, ys, vals); break;
+            case 2: compute_tile<2>(s, tl.first, tl.nb, xs, ys, vals); break;
+            case 4: compute_tile<4>(s, tl.first, tl.nb, xs, ys, vals); break;
+            case 8: compute_tile<8>(s, tl.first, tl.nb, xs, ys, vals); break;
+            case 16: compute_tile<16>(s, tl.first, tl.nb, xs, ys, vals); break;
+            case 32: compute_tile<32>(s, tl.first, tl.nb, xs, ys, vals); break;
+            default: compute_tile<64>(s, tl.first, tl.nb, xs, ys, vals); break;
         }
         __syncthreads();
         // warps assemble 32 consecutive blocks at a time (tiles start at
@@ -229,8 +229,7 @@ int enqueue(qext_batch *b, cudaStream_t st) {
     if (!b->ntiles) return QEXT_OK;
     const uint64_t cap = uint64_t(b->sms) * b->cfg.ctas_per_sm;
     const int grid = int(std::min<uint64_t>(cap, b->ntiles));
-    batch_kernel<<<grid, kThreads, kSmemBytes, st>>>(b->d_items, b->d_tiles, b->ntiles, b->d_counter,
-                                                     make_shift_muls());
+    batch_kernel<<<grid, kThreads, kSmemBytes, st>>>(b->d_items, b->d_tiles, b->ntiles, b->d_counter);
     return cudaGetLastError() == cudaSuccess ? QEXT_OK : QEXT_E_CUDA;
 }
 
@@ -443,7 +442,7 @@ struct NoallocScratch {
 // process exits, shared by every call (see qext_batch_run_noalloc).
 static __device__ __align__(256) unsigned char qext_noalloc_scratch[sizeof(NoallocScratch)];
 
-__global__ void __launch_bounds__(kThreads) batch_noalloc_kernel(NoallocScratch *sc, const ShiftMuls mu) {
+__global__ void __launch_bounds__(kThreads) batch_noalloc_kernel(NoallocScratch *sc) {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t next_tile;
@@ -487,13 +486,13 @@ __global__ void __launch_bounds__(kThreads) batch_noalloc_kernel(NoallocScratch 
         for (uint32_t i = tid; i < ((nb + 31u) & ~31u); i += kThreads) vals[i] = 0;
         __syncthreads();
         switch (it.q) {
-            case 1: compute_tile<1>(s, first, nb, xs, ys, vals, mu); break;
-            case 2: compute_tile<2>(s, first, nb, xs, ys, vals, mu); break;
-            case 4: compute_tile<4>(s, first, nb, xs, ys, vals, mu); break;
-            case 8: compute_tile<8>(s, first, nb, xs, ys, vals, mu); break;
-            case 16: compute_tile<16>(s, first, nb, xs, ys, vals, mu); break;
-            case 32: compute_tile<32>(s, first, nb, xs, ys, vals, mu); break;
-            default: compute_tile<64>(s, first, nb, xs, ys, vals, mu); break;
+            case 1: compute_tile<1>(s, first, nb, xs, ys, vals); break;
+            case 2: compute_tile<2>(s, first, nb, xs, ys, vals); break;
+            case 4: compute_tile<4>(s, first, nb, xs, ys, vals); break;
+            case 8: compute_tile<8>(s, first, nb, xs, ys, vals); break;
+            case 16: compute_tile<16>(s, first, nb, xs, ys, vals); break;
+            case 32: compute_tile<32>(s, first, nb, xs, ys, vals); break;
+            default: compute_tile<64>(s, first, nb, xs, ys, vals); break;
         }
         __syncthreads();
         for (uint32_t g = tid >> 5; g * 32 < nb; g += kThreads / 32)
@@ -579,8 +578,7 @@ extern "C" int qext_batch_run_noalloc(const qext_batch_item *items, uint32_t nit
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return QEXT_E_CUDA;
     const uint64_t cap = uint64_t(sms) * cfg.ctas_per_sm;
     const int grid = int(tiles < cap ? tiles : cap);
-    batch_noalloc_kernel<<<grid, kThreads, kSmemBytes, st>>>(static_cast<NoallocScratch *>(g_noalloc_dev[dev]),
-                                                              make_shift_muls());
+    batch_noalloc_kernel<<<grid, kThreads, kSmemBytes, st>>>(static_cast<NoallocScratch *>(g_noalloc_dev[dev]));
     return cudaGetLastError() == cudaSuccess ? QEXT_OK : QEXT_E_CUDA;
 }
 
@@ -644,8 +642,7 @@ int batch_launch_tables(const qext_batch_item *items, uint32_t nitems, void *d_t
     if (sms <= 0) return QEXT_E_CUDA;
     const uint64_t cap = uint64_t(sms) * cfg.ctas_per_sm;
     const int grid = int(tiles < cap ? tiles : cap);
-    batch_noalloc_kernel<<<grid, kThreads, kSmemBytes, st>>>(static_cast<NoallocScratch *>(d_table),
-                                                              make_shift_muls());
+    batch_noalloc_kernel<<<grid, kThreads, kSmemBytes, st>>>(static_cast<NoallocScratch *>(d_table));
     return cudaGetLastError() == cudaSuccess ? QEXT_OK : QEXT_E_CUDA;
 }
 

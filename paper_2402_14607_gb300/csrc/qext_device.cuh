@@ -23,13 +23,6 @@
 
 namespace qxd {
 
-// 2^(32-G) for G = 1, 2, 4 (index log2 G), passed at run time so
-// that shifts written as multiplies stay IMAD / IMAD.HI (the POPC chains of
-// the wide fields use 2^31).
-struct ShiftMuls {
-    uint32_t hi[3];  // 2^(32-G): umulhi(a, 2^(32-G)) = a >> G
-};
-
 // Everything a kernel needs to know about one stream pair.
 struct StreamArgs {
     const uint32_t *x;      // packed words (or samples, for the fused ingest)
@@ -40,15 +33,9 @@ struct StreamArgs {
     uint32_t m;             // output bits per block
     uint32_t ntaps;         // taps of P below x^q (0 for q = 1), descending, last 0
     uint32_t taps[4];
-    uint32_t tap_mul[4];    // 2^taps[t] for t < ntaps, else 0 (run-time multipliers, see ShiftMuls)
+    uint32_t tap_mul[4];    // 2^taps[t] for t < ntaps, else 0 (run-time multipliers: shifts by taps as IMADs)
     int *status;            // device status word (qext_device_status), or null
 };
-
-__host__ __device__ inline ShiftMuls make_shift_muls() {
-    ShiftMuls mu;
-    for (int i = 0; i < 3; ++i) mu.hi[i] = 1u << (32 - (1 << i));
-    return mu;
-}
 
 // ---------------------------------------------------------------------------
 // Register bit-matrix primitives.

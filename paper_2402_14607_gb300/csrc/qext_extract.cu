@@ -36,7 +36,6 @@ struct TileArgs {
     const uint16_t *sx;  // raw ADC samples (fused ingest), else null
     const uint16_t *sy;
     uint64_t nsamples;
-    ShiftMuls mu;
     uint64_t ntiles;
     uint32_t T;     // blocks per tile (multiple of 32)
     uint32_t nbuf;  // 1 or 2 tile buffers
@@ -195,7 +194,7 @@ __global__ void __launch_bounds__(kThreads) extract_tiled_kernel(const TileArgs 
             uint64_t A = 0, Bm = 0, C = 0;
             if (blk < s.nblocks) {
                 const uint32_t *xb = xs + lb * s.wpb, *yb = ys + lb * s.wpb;
-                half_products64(xb, yb, s.wpb, ta.vec, tid, part, TPB, ta.mu, A, Bm, C);
+                half_products64(xb, yb, s.wpb, ta.vec, tid, part, TPB, A, Bm, C);
             }
             A ^= __shfl_xor_sync(0xffffffffu, A, 1);
             Bm ^= __shfl_xor_sync(0xffffffffu, Bm, 1);
@@ -221,7 +220,7 @@ __global__ void __launch_bounds__(kThreads) extract_tiled_kernel(const TileArgs 
 // too long to stage in shared memory).
 // ---------------------------------------------------------------------------
 template <int Q>
-__global__ void __launch_bounds__(kThreads) extract_direct_kernel(const StreamArgs s, const ShiftMuls mu) {
+__global__ void __launch_bounds__(kThreads) extract_direct_kernel(const StreamArgs s) {
     const uint32_t lane = threadIdx.x & 31u;
     const uint64_t warp = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
@@ -232,9 +231,9 @@ __global__ void __launch_bounds__(kThreads) extract_direct_kernel(const StreamAr
             const uint32_t *xb = s.x + blk * s.wpb, *yb = s.y + blk * s.wpb;
             if constexpr (Q == 64) {
                 // scalar loads here: the per-part templates beat the one-copy loop
-                const uint64_t A = half_product64<0>(xb, yb, s.wpb, 0, 0, 0, 1, mu);
-                const uint64_t B = half_product64<1>(xb, yb, s.wpb, 0, 0, 0, 1, mu);
-                const uint64_t C = half_product64<2>(xb, yb, s.wpb, 0, 0, 0, 1, mu);
+                const uint64_t A = half_product64<0>(xb, yb, s.wpb, 0, 0, 0, 1);
+                const uint64_t B = half_product64<1>(xb, yb, s.wpb, 0, 0, 0, 1);
+                const uint64_t C = half_product64<2>(xb, yb, s.wpb, 0, 0, 0, 1);
                 v = combine_q64(A, B, C, s);
             } else {
                 v = block_small_q<Q>(xb, yb, s.wpb, 0, 0, s);
@@ -254,7 +253,6 @@ int launch_q(const StreamArgs &s, const uint16_t *sx, const uint16_t *sy, uint64
     const uint32_t nb_max = (flags & QEXT_F_NBUF1) ? 1u : 2u;
     // per device: SM count, "attribute set", occupancies by tile shape
     static qext::DeviceSlots attr_set, occ_tiled[24], occ_direct;
-    const ShiftMuls mu = make_shift_muls();
     const int dev = qext::current_device();
     if (dev < 0) return QEXT_E_CUDA;
     const int sms = qext::sm_count(dev);
@@ -289,7 +287,6 @@ int launch_q(const StreamArgs &s, const uint16_t *sx, const uint16_t *sy, uint64
         ta.sx = sx;
         ta.sy = sy;
         ta.nsamples = nsamples;
-        ta.mu = mu;
         ta.T = T;
         ta.nbuf = nbuf;
         ta.ntiles = (s.nblocks + T - 1) / T;
@@ -337,7 +334,7 @@ int launch_q(const StreamArgs &s, const uint16_t *sx, const uint16_t *sy, uint64
         const uint64_t ctas = (s.nblocks + kThreads - 1) / kThreads;
         const uint64_t cap = uint64_t(sms) * occd;
         const int grid = int(ctas < cap ? ctas : cap);
-        extract_direct_kernel<Q><<<grid, kThreads, 0, st>>>(s, mu);
+        extract_direct_kernel<Q><<<grid, kThreads, 0, st>>>(s);
     }
     return cudaGetLastError() == cudaSuccess ? QEXT_OK : QEXT_E_CUDA;
 }

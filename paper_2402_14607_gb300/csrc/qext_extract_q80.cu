@@ -35,7 +35,6 @@ constexpr int kThreads80 = 64;
 
 struct Q80Args {
     StreamArgs s;
-    ShiftMuls mu;
     uint32_t n_p;
     uint32_t zero;  // always 0 (see after())
 };
@@ -237,7 +236,7 @@ __global__ void __launch_bounds__(kThreads80, 6) extract_q80_kernel(const Q80Arg
                     X2[k] = cx[(64 + k) * kThreads80];
                     Y2[k] = cy[(64 + k) * kThreads80];
                 }
-                p22 ^= diagonal_chain<16>(X2, Y2, a.mu.hi[0]) >> 1;
+                p22 ^= diagonal_chain<16>(X2, Y2) >> 1;
             }
             // the five 32 x 32 products; operands are XORs of slices (slicing
             // is linear):  pr 0: S1 (P11), 1: S1 + S2 (P12), 2: S0 + S1 (P01),
@@ -264,7 +263,7 @@ __global__ void __launch_bounds__(kThreads80, 6) extract_q80_kernel(const Q80Arg
                         Y[k] ^= cy[(64 + k) * kThreads80];
                     }
                 }
-                const uint64_t r = gram32_parities_3x16(X, Y, a.mu);
+                const uint64_t r = gram32_parities_3x16(X, Y);
                 p11 ^= pr == 0 ? r : 0;
                 p12 ^= pr == 1 ? r : 0;
                 p01 ^= pr == 2 ? r : 0;
@@ -328,7 +327,6 @@ int launch_extract_q80(const qext_plan *p, const uint32_t *x, const uint32_t *y,
         a.s.tap_mul[i] = 0;
     }
     a.s.status = device_status_ptr();
-    a.mu = make_shift_muls();
     a.n_p = p->n_p;
     a.zero = 0;
     const uint64_t ctas = (nblocks + kThreads80 - 1) / kThreads80;

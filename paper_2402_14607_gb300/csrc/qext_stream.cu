@@ -57,7 +57,6 @@ struct GeneralArgs {
     uint64_t t;             // tail bits
     uint64_t chunk_words;
     uint32_t out_bit0;      // pending bits before the first new value
-    ShiftMuls mu;
 };
 
 template <int Q>
@@ -75,7 +74,7 @@ __global__ void __launch_bounds__(kStreamThreads) stream_general_kernel(const Ge
         uint64_t v;
         if constexpr (Q == 64) {
             uint64_t A = 0, B = 0, C = 0;
-            half_products64(xs, ys, s.wpb, 0, 0, 0, 1, g.mu, A, B, C);
+            half_products64(xs, ys, s.wpb, 0, 0, 0, 1, A, B, C);
             v = combine_q64(A, B, C, s);
         } else {
             v = block_small_q<Q>(xs, ys, s.wpb, 0, 0, s);
@@ -255,7 +254,6 @@ int qext_stream_push(qext_stream *s, const uint32_t *x, const uint32_t *y, uint6
             g.t = t;
             g.chunk_words = chunk_words;
             g.out_bit0 = uint32_t(p);
-            g.mu = make_shift_muls();
             rc = launch_general_q(s->plan->q, g, st);
         }
         if (rc != QEXT_OK) return rc;

@@ -20,7 +20,7 @@ namespace qxd {
 // at a time (one live accumulator): bit 32 - (2H-1) + d of the result is
 // parity(XOR_{j+l=d} X[j] & Y[l]) (see parity_bits32_top).
 template <int H>
-__device__ __forceinline__ uint32_t diagonal_chain(const uint32_t *X, const uint32_t *Y, uint32_t top) {
+__device__ __forceinline__ uint32_t diagonal_chain(const uint32_t *X, const uint32_t *Y) {
     static_assert(2 * H - 1 <= 32, "one word of parities");
     uint32_t c = 0;
 #pragma unroll
@@ -28,7 +28,7 @@ __device__ __forceinline__ uint32_t diagonal_chain(const uint32_t *X, const uint
         uint32_t acc = 0;
 #pragma unroll
         for (int j = d < H ? 0 : d - H + 1; j <= (d < H ? d : H - 1); ++j) acc = lop_and_xor(X[j], Y[d - j], acc);
-        c = __umulhi(c, top) + uint32_t(__popc(acc)) * top;
+        c = (c >> 1) + (uint32_t(__popc(acc)) << 31);
     }
     return c;
 }
@@ -36,15 +36,15 @@ __device__ __forceinline__ uint32_t diagonal_chain(const uint32_t *X, const uint
 // Parities of the 31 diagonals of a sliced 16 x 16 Gram product by one
 // Karatsuba level (8 + 8): bit d of the result = parity of diagonal d.  X and
 // Y are overwritten (their low halves become the halves' sums).
-__device__ __forceinline__ uint32_t gram16_parities(uint32_t *X, uint32_t *Y, uint32_t top) {
-    const uint32_t a = diagonal_chain<8>(X, Y, top);  // 15 parities in bits 17..31
-    const uint32_t b = diagonal_chain<8>(X + 8, Y + 8, top);
+__device__ __forceinline__ uint32_t gram16_parities(uint32_t *X, uint32_t *Y) {
+    const uint32_t a = diagonal_chain<8>(X, Y);  // 15 parities in bits 17..31
+    const uint32_t b = diagonal_chain<8>(X + 8, Y + 8);
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         X[j] ^= X[j + 8];
         Y[j] ^= Y[j + 8];
     }
-    const uint32_t c = diagonal_chain<8>(X, Y, top);
+    const uint32_t c = diagonal_chain<8>(X, Y);
     return lop_xor3(a >> 17, b >> 1, lop_xor3(a, b, c) >> 9);
 }
 
@@ -54,8 +54,7 @@ __device__ __forceinline__ uint32_t gram16_parities(uint32_t *X, uint32_t *Y, ui
 // 16 x 16 products (135 diagonal parities; the q = 80 kernel, latency-bound,
 // measured faster with this form than with gram32_parities).  X and Y are
 // overwritten.  Bit d of the result = parity of diagonal d.
-__device__ __forceinline__ uint64_t gram32_parities_3x16(uint32_t (&X)[32], uint32_t (&Y)[32], const ShiftMuls &mu) {
-    const uint32_t top = mu.hi[0];  // 2^31 at run time
+__device__ __forceinline__ uint64_t gram32_parities_3x16(uint32_t (&X)[32], uint32_t (&Y)[32]) {
     // sums of the halves first (gram16_parities overwrites its operands)
     uint32_t XS[16], YS[16];
 #pragma unroll
@@ -63,9 +62,9 @@ __device__ __forceinline__ uint64_t gram32_parities_3x16(uint32_t (&X)[32], uint
         XS[j] = X[j] ^ X[j + 16];
         YS[j] = Y[j] ^ Y[j + 16];
     }
-    const uint64_t A = gram16_parities(X, Y, top);
-    const uint64_t B = gram16_parities(X + 16, Y + 16, top);
-    const uint64_t C = gram16_parities(XS, YS, top);
+    const uint64_t A = gram16_parities(X, Y);
+    const uint64_t B = gram16_parities(X + 16, Y + 16);
+    const uint64_t C = gram16_parities(XS, YS);
     const uint64_t M = A ^ B ^ C;
     return A ^ (M << 16) ^ (B << 32);
 }
@@ -76,7 +75,7 @@ __device__ __forceinline__ uint64_t gram32_parities_3x16(uint32_t (&X)[32], uint
 // pairs j + l = d - S b of block b.  One live accumulator; bit
 // 32 - (D1 - D0) + (d - D0) of the result is the parity of diagonal d.
 template <int NB, int O0, int OSTEP, int S, int D0, int D1>
-__device__ __forceinline__ uint32_t block_chain(const uint32_t *X, const uint32_t *Y, uint32_t top) {
+__device__ __forceinline__ uint32_t block_chain(const uint32_t *X, const uint32_t *Y) {
     static_assert(D1 - D0 >= 1 && D1 - D0 <= 32, "one word of parities");
     uint32_t c = 0;
 #pragma unroll
@@ -89,7 +88,7 @@ __device__ __forceinline__ uint32_t block_chain(const uint32_t *X, const uint32_
             for (int j = 0; j < 8; ++j)
                 if (k - j >= 0 && k - j < 8) acc = lop_and_xor(X[o + j], Y[o + k - j], acc);
         }
-        c = __umulhi(c, top) + uint32_t(__popc(acc)) * top;
+        c = (c >> 1) + (uint32_t(__popc(acc)) << 31);
     }
     return c;
 }
@@ -105,10 +104,9 @@ __device__ __forceinline__ uint32_t block_chain(const uint32_t *X, const uint32_
 // the 16 x 16 products of the outer level): 107 diagonal parities instead
 // of 135.  X and Y are overwritten.  Bit d of the result = parity of
 // diagonal d.
-__device__ __forceinline__ uint64_t gram32_parities(uint32_t (&X)[32], uint32_t (&Y)[32], const ShiftMuls &mu) {
-    const uint32_t top = mu.hi[0];  // 2^31 at run time
-    const uint64_t E = uint64_t(block_chain<4, 0, 8, 8, 0, 32>(X, Y, top)) |
-                       (uint64_t(block_chain<4, 0, 8, 8, 32, 39>(X, Y, top) >> 25) << 32);
+__device__ __forceinline__ uint64_t gram32_parities(uint32_t (&X)[32], uint32_t (&Y)[32]) {
+    const uint64_t E = uint64_t(block_chain<4, 0, 8, 8, 0, 32>(X, Y)) |
+                       (uint64_t(block_chain<4, 0, 8, 8, 32, 39>(X, Y) >> 25) << 32);
     // inner sums of A's and B's halves (words 8.. and 24..)
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
@@ -117,8 +115,8 @@ __device__ __forceinline__ uint64_t gram32_parities(uint32_t (&X)[32], uint32_t 
         X[24 + j] ^= X[16 + j];
         Y[24 + j] ^= Y[16 + j];
     }
-    const uint64_t F = uint64_t(block_chain<1, 8, 0, 0, 0, 15>(X, Y, top) >> 17) |
-                       (uint64_t(block_chain<1, 24, 0, 0, 0, 15>(X, Y, top) >> 17) << 16);
+    const uint64_t F = uint64_t(block_chain<1, 8, 0, 0, 0, 15>(X, Y) >> 17) |
+                       (uint64_t(block_chain<1, 24, 0, 0, 0, 15>(X, Y) >> 17) << 16);
     // outer sum (words 0..15) and its inner half sum (words 24..31)
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
@@ -129,8 +127,8 @@ __device__ __forceinline__ uint64_t gram32_parities(uint32_t (&X)[32], uint32_t 
         X[8 + j] = X[24 + j] ^ X[j];
         Y[8 + j] = Y[24 + j] ^ Y[j];
     }
-    const uint64_t DC = block_chain<2, 0, 8, 8, 0, 23>(X, Y, top) >> 9;
-    const uint64_t SC = block_chain<1, 24, 0, 0, 0, 15>(X, Y, top) >> 17;
+    const uint64_t DC = block_chain<2, 0, 8, 8, 0, 23>(X, Y) >> 9;
+    const uint64_t SC = block_chain<1, 24, 0, 0, 0, 15>(X, Y) >> 17;
     return E ^ ((E ^ F) << 8) ^ ((E ^ DC) << 16) ^ ((E ^ F ^ DC ^ SC) << 24);
 }
 
@@ -147,8 +145,7 @@ __device__ __forceinline__ uint32_t pick64(uint32_t lo, uint32_t hi, uint32_t se
 template <int PART>
 __device__ __forceinline__ uint64_t half_product64(const uint32_t *xs, const uint32_t *ys, uint32_t wpb, int vec,
                                                    uint32_t rot, uint32_t g_first, uint32_t g_step,
-                                                   const ShiftMuls &mu, uint32_t sel = 0x3210u,
-                                                   uint32_t mask = 0) {
+                                                   uint32_t sel = 0x3210u, uint32_t mask = 0) {
     uint64_t z = 0;  // parities are linear: XOR of the groups' parities
     for (uint32_t g0 = 64 * g_first; g0 < wpb; g0 += 64 * g_step) {
         uint32_t X[32], Y[32];
@@ -178,7 +175,7 @@ __device__ __forceinline__ uint64_t half_product64(const uint32_t *xs, const uin
         }
         slice<32>(X);
         slice<32>(Y);
-        z ^= gram32_parities(X, Y, mu);
+        z ^= gram32_parities(X, Y);
     }
     return z;
 }
@@ -186,11 +183,11 @@ __device__ __forceinline__ uint64_t half_product64(const uint32_t *xs, const uin
 // A, B and C of one thread's groups with a single copy of half_product64
 // (a run-time loop over the parts).
 __device__ __forceinline__ void half_products64(const uint32_t *xs, const uint32_t *ys, uint32_t wpb, int vec,
-                                                uint32_t rot, uint32_t g_first, uint32_t g_step, const ShiftMuls &mu,
-                                                uint64_t &A, uint64_t &B, uint64_t &C) {
+                                                uint32_t rot, uint32_t g_first, uint32_t g_step, uint64_t &A,
+                                                uint64_t &B, uint64_t &C) {
 #pragma unroll 1
     for (uint32_t part = 0; part < 3; ++part) {
-        const uint64_t r = half_product64<-1>(xs, ys, wpb, vec, rot, g_first, g_step, mu,
+        const uint64_t r = half_product64<-1>(xs, ys, wpb, vec, rot, g_first, g_step,
                                               part == 1 ? 0x7654u : 0x3210u, part == 2 ? ~0u : 0u);
         A = part == 0 ? r : A;
         B = part == 1 ? r : B;
