@@ -69,8 +69,8 @@ __device__ __forceinline__ void load_tile(const StreamArgs &s, uint64_t first, u
 }
 
 template <int Q>
-__device__ __forceinline__ void compute_tile(const StreamArgs &s, uint64_t first, uint32_t nb, const uint32_t *xs,
-                                             const uint32_t *ys, uint64_t *vals) {
+__device__ __forceinline__ void compute_tile(const StreamArgs &s, uint64_t first, uint32_t nb, uint32_t *xs,
+                                             uint32_t *ys, uint64_t *vals) {
     const uint32_t tid = threadIdx.x;
     if constexpr (Q == 64) {
         // two threads per block, 64 blocks per pass
@@ -78,15 +78,18 @@ __device__ __forceinline__ void compute_tile(const StreamArgs &s, uint64_t first
             const uint32_t lb = base + tid / 2, part = tid & 1u;
             uint64_t A = 0, B = 0, C = 0;
             if (lb < nb) {
-                const uint32_t *xb = xs + lb * s.wpb, *yb = ys + lb * s.wpb;
-                const int vec = s.wpb % 4 == 0;
-                half_products64(xb, yb, s.wpb, vec, tid, part, 2, A, B, C);
+                uint32_t *xb = xs + lb * s.wpb, *yb = ys + lb * s.wpb;
+                if (s.wpb % 4 == 0)
+                    half_products64_inplace(xb, yb, s.wpb, tid, part, 2, A, B, C);
+                else
+                    half_products64(xb, yb, s.wpb, 0, tid, part, 2, A, B, C);
             }
             A ^= __shfl_xor_sync(0xffffffffu, A, 1);
             B ^= __shfl_xor_sync(0xffffffffu, B, 1);
             C ^= __shfl_xor_sync(0xffffffffu, C, 1);
             if (lb < nb && part == 0) vals[lb] = combine_q64(A, B, C, s) & mask_m(s.m);
         }
+        fence_proxy_async_smem();  // slices written over the tile, which a bulk copy refills later
     } else {
         for (uint32_t lb = tid; lb < nb; lb += kThreads)
             vals[lb] = block_small_q<Q>(xs + lb * s.wpb, ys + lb * s.wpb, s.wpb, s.wpb % 4 == 0, tid, s) &

@@ -10,7 +10,9 @@
 // the next tile is issued before the current one is computed (two buffers).
 // Each thread (two for q = 64) computes one block from shared memory, reading
 // its 16-byte chunks in a lane-rotated order so that eight consecutive lanes
-// hit eight different bank groups.  Block values go to shared memory and warps
+// hit eight different bank groups (q = 64 writes its slices back over its own
+// part of the tile and reads them again: half_products64_inplace).  Block
+// values go to shared memory and warps
 // assemble m-bit outputs of 32 consecutive blocks into whole words.  From raw
 // samples (B != 0) the tile's samples arrive by TMA and are packed in place.
 //
@@ -193,9 +195,13 @@ __global__ void __launch_bounds__(kThreads) extract_tiled_kernel(const TileArgs 
             const uint32_t part = tid % TPB;
             uint64_t A = 0, Bm = 0, C = 0;
             if (blk < s.nblocks) {
-                const uint32_t *xb = xs + lb * s.wpb, *yb = ys + lb * s.wpb;
-                half_products64(xb, yb, s.wpb, ta.vec, tid, part, TPB, A, Bm, C);
+                uint32_t *xb = xs + lb * s.wpb, *yb = ys + lb * s.wpb;
+                if (ta.vec)
+                    half_products64_inplace(xb, yb, s.wpb, tid, part, TPB, A, Bm, C);
+                else
+                    half_products64(xb, yb, s.wpb, ta.vec, tid, part, TPB, A, Bm, C);
             }
+            fence_proxy_async_smem();  // slices written over the tile, which a bulk copy refills later
             A ^= __shfl_xor_sync(0xffffffffu, A, 1);
             Bm ^= __shfl_xor_sync(0xffffffffu, Bm, 1);
             C ^= __shfl_xor_sync(0xffffffffu, C, 1);

@@ -195,6 +195,84 @@ __device__ __forceinline__ void half_products64(const uint32_t *xs, const uint32
     }
 }
 
+// A, B and C of one thread's groups, each group sliced once.  Slicing is
+// linear, so the slices of lo ^ hi are the XOR of the slices of lo and hi:
+// the group's 32 elements (lo and hi words, 64 words per source) are loaded
+// once, lo and hi sliced in registers, and the four slice sets written back
+// over the group's own 64 words of x and y in shared memory (the raw words are
+// no longer needed; chunks in the same lane-rotated order as the loads), then
+// read back for A = lo x lo, B = hi x hi and C = (lo ^ hi) x (lo ^ hi).  Two
+// transposes fewer per group than half_products64 and no part selection.
+// Only whole groups are staged this way: a last group that ends past the
+// block (its tail words belong to the next block) goes through
+// half_product64.  xs, ys are shared memory; a bulk copy into them later needs
+// a proxy fence after this (the caller's).
+__device__ __forceinline__ void half_products64_inplace(uint32_t *xs, uint32_t *ys, uint32_t wpb, uint32_t rot,
+                                                        uint32_t g_first, uint32_t g_step, uint64_t &A, uint64_t &B,
+                                                        uint64_t &C) {
+    A = B = C = 0;
+    for (uint32_t g0 = 64 * g_first; g0 < wpb; g0 += 64 * g_step) {
+        if (g0 + 64 > wpb) {
+            const uint32_t g = g0 / 64, one = wpb;  // a step past the block: this group only
+            A ^= half_product64<0>(xs, ys, wpb, 1, rot, g, one);
+            B ^= half_product64<1>(xs, ys, wpb, 1, rot, g, one);
+            C ^= half_product64<2>(xs, ys, wpb, 1, rot, g, one);
+            continue;
+        }
+#pragma unroll 1
+        for (uint32_t src = 0; src < 2; ++src) {
+            uint32_t *const w = (src ? ys : xs) + g0;
+            uint32_t L[32], H[32];
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+                const uint4 v = lds4(w + 4 * ((uint32_t(c) + rot) & 15u));
+                L[2 * c] = v.x;
+                H[2 * c] = v.y;
+                L[2 * c + 1] = v.z;
+                H[2 * c + 1] = v.w;
+            }
+            slice<32>(L);
+            slice<32>(H);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                *reinterpret_cast<uint4 *>(w + 4 * ((uint32_t(k) + rot) & 15u)) =
+                    make_uint4(L[4 * k], L[4 * k + 1], L[4 * k + 2], L[4 * k + 3]);
+                *reinterpret_cast<uint4 *>(w + 4 * ((uint32_t(k) + 8u + rot) & 15u)) =
+                    make_uint4(H[4 * k], H[4 * k + 1], H[4 * k + 2], H[4 * k + 3]);
+            }
+        }
+        const uint32_t *const wx = xs + g0, *const wy = ys + g0;
+#pragma unroll 1
+        for (uint32_t part = 0; part < 3; ++part) {
+            uint32_t X[32], Y[32];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                // lo slices in chunks k + rot, hi slices in chunks k + 8 + rot (mod 16)
+                const uint32_t cl = 4 * ((uint32_t(k) + rot) & 15u), ch = 4 * ((uint32_t(k) + 8u + rot) & 15u);
+                const uint32_t c0 = part == 1 ? ch : cl;
+                uint4 vx = lds4(wx + c0), vy = lds4(wy + c0);
+                if (part == 2) {
+                    const uint4 hx = lds4(wx + ch), hy = lds4(wy + ch);
+                    vx = make_uint4(vx.x ^ hx.x, vx.y ^ hx.y, vx.z ^ hx.z, vx.w ^ hx.w);
+                    vy = make_uint4(vy.x ^ hy.x, vy.y ^ hy.y, vy.z ^ hy.z, vy.w ^ hy.w);
+                }
+                X[4 * k] = vx.x;
+                X[4 * k + 1] = vx.y;
+                X[4 * k + 2] = vx.z;
+                X[4 * k + 3] = vx.w;
+                Y[4 * k] = vy.x;
+                Y[4 * k + 1] = vy.y;
+                Y[4 * k + 2] = vy.z;
+                Y[4 * k + 3] = vy.w;
+            }
+            const uint64_t r = gram32_parities(X, Y);
+            A ^= part == 0 ? r : 0;
+            B ^= part == 1 ? r : 0;
+            C ^= part == 2 ? r : 0;
+        }
+    }
+}
+
 __device__ __forceinline__ uint64_t combine_q64(uint64_t A, uint64_t B, uint64_t C, const StreamArgs &s) {
     const uint64_t M = C ^ A ^ B;  // middle term, degree <= 62
     return reduce_mod_p64(A ^ (M << 32), B ^ (M >> 32), s);
