@@ -54,6 +54,7 @@ MIXED = [
     (16, 64, 16, 1000, 0), (4, 64, 4, 3000, 0), (64, 64, 64, 300, 0), (8, 64, 8, 129, 0), (1, 64, 1, 700, 1),
     (32, 64, 32, 65, 0), (2, 64, 2, 33, 3), (16, 64, 13, 257, 1), (64, 71, 41, 70, 2), (4, 64, 3, 31, 0),
     (16, 70, 16, 45, 1), (64, 64, 64, 1, 0), (16, 64, 16, 0, 0), (4, 72, 4, 600, 1),
+    (64, 40, 64, 100, 0), (64, 72, 50, 70, 1),   # q = 64 with a partial last group
 ]
 
 

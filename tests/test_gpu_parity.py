@@ -28,6 +28,7 @@ CASES = [
     (16, 64, 16, 4133, 0), (16, 64, 13, 1000, 0), (16, 70, 16, 97, 1), (16, 26, 9, 200, 0), (16, 64, 1, 31, 2),
     (32, 64, 32, 500, 0), (32, 33, 17, 65, 1), (32, 25, 32, 40, 0),
     (64, 64, 64, 300, 0), (64, 71, 41, 70, 1), (64, 64, 1, 100, 0), (64, 25, 64, 33, 0), (64, 64, 63, 257, 2),
+    (64, 40, 64, 300, 0), (64, 72, 37, 129, 0), (64, 34, 64, 65, 1),     # q = 64, last group partial
     (64, 64, 64, 1000, 0), (16, 64, 16, 20000, 0), (4, 64, 4, 30001, 0),    # many tiles per CTA
     (16, 800, 16, 70, 0), (64, 200, 64, 40, 0), (8, 1600, 8, 33, 0),        # long blocks: direct fallback
 ]
