@@ -155,3 +155,54 @@ def test_alg2_plan_checks_without_gpu():
     with pytest.raises(qext.QextError) as e:
         qext.qext_alg2_plan_create(0.8, 16, 0, 1, 4)
     assert e.value.code == qext.QEXT_E_INVAL
+
+
+def test_samples_argument_checks_without_gpu():
+    """qext_extract_samples_ex rejects bad flags, widths, lengths and pointers
+    before any device work."""
+    p = qext.qext_plan_create(1024, 0, 867, 2.0 ** -50)   # q = 16, n = 1024
+    F = qext
+    cases = [
+        ((12, 16, 16, 1000, 1, 16), 0x100, qext.QEXT_E_INVAL),                                  # unknown flag
+        ((12, 16, 16, 1000, 1, 16), F.QEXT_F_TEST_TIMEOUT | F.QEXT_F_WARP_SPECIALIZED, qext.QEXT_E_INVAL),
+        ((12, 16, 16, 1000, 1, 16), F.QEXT_F_TEST_TIMEOUT | F.QEXT_F_CTA_TILES, qext.QEXT_E_INVAL),
+        ((10, 16, 16, 1000, 1, 16), 0, qext.QEXT_E_UNSUPPORTED),                                # b not 8 / 12 / 16
+        ((12, 16, 16, 85, 1, 16), 0, qext.QEXT_E_INVAL),                                         # 85 samples < 1 block
+        ((12, 0, 16, 1000, 1, 16), 0, qext.QEXT_E_INVAL),                                        # null x
+        ((12, 16, 8, 1000, 1, 16), 0, qext.QEXT_E_INVAL),                                        # y not 16-byte aligned
+        ((12, 16, 16, 1000, 1, 2), 0, qext.QEXT_E_INVAL),                                        # out not 4-byte aligned
+    ]
+    for args, flags, code in cases:
+        with pytest.raises(qext.QextError) as e:
+            qext.qext_extract_samples_ex(p, *args, stream=0, flags=flags)
+        assert e.value.code == code, (args, flags)
+    qext.qext_extract_samples_ex(p, 12, 0, 0, 0, 0, 0, stream=0)   # nblocks = 0: nothing to do
+    p80 = qext.qext_plan_create(5680, 80, 0.67125 * 5680, 2.0 ** -30)
+    with pytest.raises(qext.QextError) as e:
+        qext.qext_extract_samples_ex(p80, 16, 16, 16, 10 ** 6, 1, 16, stream=0, flags=qext.QEXT_F_RAW_PREFETCH)
+    assert e.value.code == qext.QEXT_E_INVAL    # the q = 80 kernel takes no flags
+
+
+def test_monitor_host_side_without_gpu():
+    """The histogram entry checks its arguments before any device work; the
+    plug-in min-entropy is host code and agrees with the oracle's."""
+    import numpy as np
+    for b in (0, 17):
+        with pytest.raises(qext.QextError) as e:
+            qext.qext_sample_histogram(b, 16, 10, 16, stream=0)
+        assert e.value.code == qext.QEXT_E_INVAL
+    qext.qext_sample_histogram(12, 0, 0, 0, stream=0)   # no samples: nothing to do
+    for samples, counts in [(0, 16), (1, 16), (16, 12)]:  # null / misaligned samples, misaligned counts
+        with pytest.raises(qext.QextError) as e:
+            qext.qext_sample_histogram(12, samples, 10, counts, stream=0)
+        assert e.value.code == qext.QEXT_E_INVAL
+    rng = np.random.Generator(np.random.PCG64(5))
+    for b in (1, 4, 8, 12, 16):
+        counts = rng.integers(0, 1000, 1 << b).astype(np.uint64)
+        counts[rng.integers(0, 1 << b)] = 5000
+        assert qext.qext_min_entropy_estimate(b, counts) == pytest.approx(oracle.min_entropy_estimate(b, counts),
+                                                                           abs=1e-12)
+    assert qext.qext_min_entropy_estimate(8, np.zeros(256, np.uint64)) == -1.0     # no samples
+    assert qext.qext_min_entropy_estimate(17, np.zeros(1, np.uint64)) == -1.0      # bad width
+    flat = np.full(1 << 12, 7, np.uint64)
+    assert qext.qext_min_entropy_estimate(12, flat) == pytest.approx(12.0, abs=1e-12)
