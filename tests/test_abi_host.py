@@ -206,3 +206,49 @@ def test_monitor_host_side_without_gpu():
     assert qext.qext_min_entropy_estimate(17, np.zeros(1, np.uint64)) == -1.0      # bad width
     flat = np.full(1 << 12, 7, np.uint64)
     assert qext.qext_min_entropy_estimate(12, flat) == pytest.approx(12.0, abs=1e-12)
+
+
+def test_null_handles_are_rejected_without_gpu():
+    """Every entry taking a handle returns QEXT_E_INVAL for a null handle (and
+    the destroy entries accept null), with no device work."""
+    import ctypes
+    L = qext.lib()
+    u64, u32 = ctypes.c_uint64(), ctypes.c_uint32()
+    INVAL = qext.QEXT_E_INVAL
+    calls = [
+        (L.qext_plan_info, (None, None, None, None, None, None, None)),
+        (L.qext_extract, (None, 16, 16, 1, 16, None)),
+        (L.qext_stream_info, (None, None, None, None)),
+        (L.qext_stream_push, (None, 16, 16, 32, 16, 1, ctypes.byref(u64), None)),
+        (L.qext_stream_flush, (None, 16, 1, ctypes.byref(u32), None)),
+        (L.qext_stream_save, (None, 16, 16, None, None)),
+        (L.qext_stream_restore, (None, 16, 16, None, None)),
+        (L.qext_stream_create, (None, None)),
+        (L.qext_batch_get_config, (None, None, None)),
+        (L.qext_batch_set_config, (None, None)),
+        (L.qext_batch_run, (None, None)),
+        (L.qext_batch_capture, (None, None)),
+        (L.qext_batch_launch, (None, None)),
+        (L.qext_batch_autotune, (None, 1, None, None)),
+        (L.qext_batch_create, (None, 1, None)),
+        (L.qext_batch_run_noalloc, (None, 1, None)),
+        (L.qext_server_add_channel, (None, None, None)),
+        (L.qext_server_submit, (None, 0, 12, 16, 16, 1, 16, 1, None)),
+        (L.qext_server_poll, (None, None, 0, None)),
+        (L.qext_server_drain, (None, 1.0)),
+        (L.qext_server_get_stats, (None, None)),
+        (L.qext_server_create, (None, None)),
+        (L.qext_pipeline_create, (None, 12, 1024, None)),
+        (L.qext_pipeline_info, (None, None)),
+        (L.qext_pipeline_run, (None, 16, 16, 1, 1, 16)),
+        (L.qext_alg2_plan_info, (None, None, None, None)),
+        (L.qext_alg2_block_info, (None, 0, None, None, None, None)),
+        (L.qext_alg2_extract, (None, 16, 16, 1, 16, None)),
+        (L.qext_device_status, (None,)),
+    ]
+    for fn, args in calls:
+        assert fn(*args) == INVAL, fn.__name__
+    for fn in (L.qext_destroy, L.qext_stream_destroy, L.qext_batch_destroy, L.qext_server_destroy,
+               L.qext_pipeline_destroy, L.qext_alg2_destroy):
+        assert fn(None) == qext.QEXT_OK, fn.__name__
+    assert L.qext_stream_state_size(None) == 0
