@@ -1,10 +1,12 @@
 #!/usr/bin/env python3
 """Throughput benchmark of the block-wise two-source extraction hot path.
 
-A step is one pass of the path over one batch of synthetic raw data: ingest
-(pack the 12-bit ADC samples of both sources into bit streams) and per-block
+A step is one pass of the path over one batch of synthetic raw data: per-block
 extraction Ext_IP^{64,16} over 2^20 block pairs of 1024 bits (1 Gbit per
-source), output truncated to m = q = 16 bits per block.
+source) of 12-bit ADC samples delivered packed to bits (3 bytes per 2
+samples, LSB-first), output truncated to m = q = 16 bits per block.  The
+same data in uint16 sample containers, whose ingest (bit-packing) runs fused
+into the extraction kernel, is measured beside it (``uint16_step``).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl qext|reference]
 
@@ -32,6 +34,9 @@ import numpy as np  # noqa: E402
 METRIC = "extracted Gbps on 1 GB300 (bit-exact), %HBM roofline; serving p50/p99 ms"
 UNIT = "Gbps"
 L2_BYTES = 126 << 20
+# kernel sources whose hash must match a profile's capture for its traffic figure to be reported
+PACKED16_SOURCES = ["qext_extract_raw.cu", "qext_block.cuh", "qext_device.cuh"]
+RAW_SOURCES = ["qext_extract_raw.cu", "qext_block.cuh", "qext_device.cuh"]
 
 
 def measured_peaks():
@@ -95,12 +100,12 @@ def workload_spec(rank: int, nblocks: int):
 def workload_config(spec, info, world):
     return {
         "workload": "large single stream: %d block pairs x %d bits (%.2f Gbit/source), %d-bit ADC samples "
-                    "(uint16) with bias offset U(-0.05,0.05) sigma, packed then extracted" %
+                    "with bias offset U(-0.05,0.05) sigma, packed to bits (LSB-first) as the ADC delivers them" %
                     (spec.nblocks, spec.n, spec.nbits / 2 ** 30, spec.b),
         "n": spec.n, "nblocks": spec.nblocks, "b": spec.b, "k": spec.k, "eps_block": spec.eps,
         "q": info["q"], "n_p": info["n_p"], "m": info["m"], "log2_eps_block": round(info["log2_eps_block"], 2),
         "step": None,
-        "l2": "inputs larger than L2 (%.0f MB of samples per step)" % (2 * spec.nsamples * 2 / 1e6),
+        "l2": "inputs larger than L2 (%.0f MB of packed input per step)" % (2 * spec.nbits / 8 / 1e6),
         "parallelism": "blocks sharded per rank, no collective" if world > 1 else "single GPU",
     }
 
@@ -108,30 +113,36 @@ def workload_config(spec, info, world):
 # ---------------------------------------------------------------------------
 # CPU oracle leg (the only part of this file that runs oracle code)
 # ---------------------------------------------------------------------------
-def run_oracle_sample(spec, sx, sy, nblocks, threads):
+def oracle_packed(spec, sx, sy, nblocks):
+    """The packed streams of the first nblocks blocks (the oracle's ingest)."""
     import oracle
-    info_q = None
-    p = oracle.plan(spec.n, 0, spec.k, spec.eps)
-    info_q = (p["q"], p["n_p"], p["m"], p["poly"])
     ns = -(-nblocks * spec.n // spec.b)
+    words = nblocks * spec.n // 32
+    return oracle.pack_samples(spec.b, sx[:ns])[:words], oracle.pack_samples(spec.b, sy[:ns])[:words]
+
+
+def run_oracle_sample(spec, ox, oy, nblocks, threads):
+    """The oracle's extraction of nblocks blocks from packed words, timed."""
+    import oracle
+    p = oracle.plan(spec.n, 0, spec.k, spec.eps)
     t0 = time.perf_counter()
-    ox = oracle.pack_samples(spec.b, sx[:ns])
-    oy = oracle.pack_samples(spec.b, sy[:ns])
-    out = oracle.extract(info_q[0], info_q[1], info_q[2], info_q[3], ox, oy, nblocks, threads=threads)
+    out = oracle.extract(p["q"], p["n_p"], p["m"], p["poly"], ox, oy, nblocks, threads=threads)
     dt = time.perf_counter() - t0
-    return out, dt, info_q[2]
+    return out, dt, p["m"]
 
 
 def cpu_baseline(spec, sx, sy, gpu_out_words, sample_blocks):
     threads = os.cpu_count() or 1
-    out, dt, m = run_oracle_sample(spec, sx, sy, sample_blocks, threads)
+    ox, oy = oracle_packed(spec, sx, sy, sample_blocks)
+    out, dt, m = run_oracle_sample(spec, ox, oy, sample_blocks, threads)
     match = None
     if gpu_out_words is not None:
         nw = out.size
         match = bool((gpu_out_words[:nw] == out).all()) if sample_blocks * m % 32 == 0 else None
     return {
         "value": round(sample_blocks * m / dt / 1e9, 6), "unit": UNIT, "cores": threads, "kind": "oracle",
-        "sample": "first %d block pairs of the same workload (ingest + extraction), %.1f s" % (sample_blocks, dt),
+        "sample": "first %d block pairs of the same workload (extraction from the packed words), %.1f s" %
+                  (sample_blocks, dt),
         "matches_gpu_output": match,
     }
 
@@ -148,12 +159,13 @@ def run_reference(args):
     sx = workloads.adc_samples(spec.seed_x, ns, spec.b, offset_amp=spec.offset_amp)   # prefix of the stream
     sy = workloads.adc_samples(spec.seed_y, ns, spec.b, offset_amp=spec.offset_amp)
     threads = os.cpu_count() or 1
+    ox, oy = oracle_packed(spec, sx, sy, sample)
     for _ in range(args.warmup):
-        run_oracle_sample(spec, sx, sy, 1, threads)
+        run_oracle_sample(spec, ox, oy, 1, threads)
     times = []
     m = None
     for _ in range(args.steps):
-        _, dt, m = run_oracle_sample(spec, sx, sy, sample, threads)
+        _, dt, m = run_oracle_sample(spec, ox, oy, sample, threads)
         times.append(dt)
     total = sum(times)
     value = args.steps * sample * m / total / 1e9
@@ -162,10 +174,11 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total / args.steps * 1e3, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic (seeded quantised-Gaussian ADC samples)",
-        "config": {"workload": "large single stream (n=1024, 12-bit ADC), each step a bounded sample of "
-                               "%d block pairs" % sample, "n": spec.n, "nblocks_per_step": sample, "b": spec.b},
+        "config": {"workload": "large single stream (n=1024, 12-bit ADC samples packed to bits), each step a "
+                               "bounded sample of %d block pairs" % sample, "n": spec.n, "nblocks_per_step": sample,
+                   "b": spec.b},
         "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": "%d block pairs per step (ingest + extraction)" % sample},
+                         "sample": "%d block pairs per step (extraction from the packed words)" % sample},
         "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -493,36 +506,41 @@ def run_gpu(args):
     sx = spec.samples("x")
     sy = spec.samples("y")
     ns = sx.size
-    nwords_packed = -(-ns * spec.b // 32)
+    nwords = spec.nbits // 32                  # packed words of the blocks, per source
+    nwords_packed = -(-ns * spec.b // 32)      # packed words of all samples
     out_words = -(-spec.nblocks * m // 32)
 
     stream = torch.cuda.Stream(device=dev)
     sh = int(stream.cuda_stream)
-    # device-resident inputs
+    # device-resident inputs: the raw samples in uint16 containers, and the
+    # same samples packed to bits (what a packing ADC delivers), packed here by
+    # the library's ingest kernel before any timing
     d_sx = torch.from_numpy(sx.view(np.int16)).to(dev)
     d_sy = torch.from_numpy(sy.view(np.int16)).to(dev)
     d_px = torch.empty(nwords_packed, dtype=torch.int32, device=dev)
     d_py = torch.empty(nwords_packed, dtype=torch.int32, device=dev)
+    qext.qext_pack_samples(spec.b, d_sx, ns, d_px, sh)
+    qext.qext_pack_samples(spec.b, d_sy, ns, d_py, sh)
     d_out = torch.empty(out_words, dtype=torch.int32, device=dev)
     torch.cuda.synchronize()
 
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
     def step(timing=None):
-        if timing is not None:
-            timing[0].record(stream)
         if args.unfused:
+            if timing is not None:
+                timing[0].record(stream)
             qext.qext_pack_samples(spec.b, d_sx, ns, d_px, sh)
             qext.qext_pack_samples(spec.b, d_sy, ns, d_py, sh)
             if timing is not None:
                 timing[1].record(stream)
             qext.qext_extract(plan, d_px, d_py, spec.nblocks, d_out, sh)
-        else:
             if timing is not None:
-                timing[1].record(stream)
+                timing[2].record(stream)
+        elif args.step == "uint16":
             qext.qext_extract_samples(plan, spec.b, d_sx, d_sy, ns, spec.nblocks, d_out, sh)
-        if timing is not None:
-            timing[2].record(stream)
+        else:
+            qext.qext_extract(plan, d_px, d_py, spec.nblocks, d_out, sh)
 
     launches_per_step = 3 if args.unfused else 1
     for _ in range(args.warmup):
@@ -530,9 +548,9 @@ def run_gpu(args):
     torch.cuda.synchronize()
 
     clocks = ClockSampler(local)
-    # the fused step is one kernel: the timed region / K is its average launch
-    # duration, and events between its launches would only add gaps; the
-    # unfused step (three kernels) records per-kernel events
+    # a one-kernel step: the timed region / K is its average launch duration
+    # (events between launches would add gaps); the unfused step (three
+    # kernels) records per-kernel events
     kev = [(ev(), ev(), ev()) for _ in range(args.steps)] if args.unfused else None
     e_start, e_stop = ev(), ev()
     if world > 1:
@@ -557,89 +575,118 @@ def run_gpu(args):
     bits_per_step = spec.nblocks * m
     value = world * args.steps * bits_per_step / t / 1e9
     input_gbps = world * args.steps * 2 * spec.nbits / t / 1e9
+    gpu_out = d_out.cpu().numpy().view(np.uint32)
 
-    # dominant kernel and its roofline (algorithmic bytes / average launch time)
+    # dominant kernel and its roofline: algorithmic bytes per launch / its
+    # average launch duration, against the measured HBM copy bandwidth
     peak, peak_src = measured_peaks()
     ext_s = statistics.mean(ext_ms) * 1e-3
+    packed_bytes = spec.nblocks * (2 * spec.n // 8) + out_words * 4      # 2n/8 in + m/8 out per block
+    uint16_bytes = 2 * ns * 2 + out_words * 4                            # raw uint16 samples in + output
     if args.unfused:
-        ext_bytes = spec.nblocks * (2 * spec.n // 8) + out_words * 4
         pack_bytes = ns * 2 + nwords_packed * 4
         pack_s = statistics.mean(pack_ms) * 1e-3 / 2
         if ext_s >= 2 * pack_s:
-            dom = {"kernel": "extract_tiled_kernel<16,0>", "bytes": ext_bytes, "t": ext_s,
-               "traffic": measured_traffic("tiled_extract_q16_large_single_stream",
-                                           ["qext_extract.cu", "qext_block.cuh", "qext_device.cuh"])}
+            dom = {"kernel": "extract_packed16_kernel (per-warp TMA pipelines, packed words)", "bytes": packed_bytes,
+                   "t": ext_s, "traffic": measured_traffic("packed16_q16_large_single_stream", PACKED16_SOURCES)}
         else:
             dom = {"kernel": "pack_kernel_vec<12>", "bytes": pack_bytes, "t": pack_s, "traffic": None}
         per_kernel = {"pack_x_plus_y": round(statistics.mean(pack_ms), 4), "extract": round(statistics.mean(ext_ms), 4)}
-    else:
-        # the step kernel reads both sample arrays once and writes the output
+    elif args.step == "uint16":
         dom = {"kernel": "extract_raw_kernel<16,12> (per-warp TMA pipelines, samples packed in registers)",
-               "bytes": 2 * ns * 2 + out_words * 4, "t": ext_s,
-               "traffic": measured_traffic("raw_ingest_q16_b12_large_single_stream",
-                                           ["qext_extract_raw.cu", "qext_block.cuh", "qext_device.cuh"])}
+               "bytes": uint16_bytes, "t": ext_s,
+               "traffic": measured_traffic("raw_ingest_q16_b12_large_single_stream", RAW_SOURCES)}
         per_kernel = {"extract_samples": round(statistics.mean(ext_ms), 4)}
+    else:
+        dom = {"kernel": "extract_packed16_kernel (per-warp TMA pipelines, packed words)", "bytes": packed_bytes,
+               "t": ext_s, "traffic": measured_traffic("packed16_q16_large_single_stream", PACKED16_SOURCES)}
+        per_kernel = {"extract": round(statistics.mean(ext_ms), 4)}
     achieved = dom["bytes"] / dom["t"] / 1e9
     roofline = {"bound": "hbm", "kernel": dom["kernel"], "achieved": round(achieved, 1), "peak": peak,
                 "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "traffic": args.traffic if args.traffic is not None else dom["traffic"],
                 "algorithmic_bytes_per_launch": dom["bytes"],
-                "peak_source": ("measured hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured"
-                                else "fallback 6.8 TB/s"),
+                "bytes_per_block": round(dom["bytes"] / spec.nblocks, 2),
+                "peak_source": ("measured hbm_gbs (MEASURED_PEAKS.json), of measured" if peak_src == "measured"
+                                else "fallback 6.8 TB/s, of fallback"),
                 "per_kernel_ms": per_kernel,
-                # the same step counted by the packed-stream figure per block,
-                # 2 n / 8 bytes in + m / 8 out (the ingest's raw uint16 samples
-                # left out): the scale on which the packed-input kernels sit
-                "packed_bits_view": {
-                    "bytes_per_block": 2 * spec.n // 8 + info["m"] / 8,
-                    "achieved": round((2 * spec.n // 8 + info["m"] / 8) * spec.nblocks / ext_s / 1e9, 1),
-                    "frac": round((2 * spec.n // 8 + info["m"] / 8) * spec.nblocks / ext_s / 1e9 / peak, 4)},
                 "kernel_time": ("per-kernel CUDA events in the timed region" if args.unfused else
                                 "timed region / K on the launching stream (one kernel per step)")}
 
+    # the same data in uint16 sample containers: ingest fused into the
+    # extraction kernel (qext_extract_samples), timed the same way
+    uint16_step = None
+    if not args.unfused and args.step == "packed" and not args.no_extra:
+        reps = max(20, min(args.steps, 200))
+        for _ in range(3):
+            qext.qext_extract_samples(plan, spec.b, d_sx, d_sy, ns, spec.nblocks, d_out, sh)
+        u0, u1 = ev(), ev()
+        u0.record(stream)
+        for _ in range(reps):
+            qext.qext_extract_samples(plan, spec.b, d_sx, d_sy, ns, spec.nblocks, d_out, sh)
+        u1.record(stream)
+        torch.cuda.synchronize()
+        tu = u0.elapsed_time(u1) * 1e-3 / reps
+        uint16_step = {
+            "kernel": "extract_raw_kernel<16,12> (per-warp TMA pipelines, samples packed in registers)",
+            "us": round(tu * 1e6, 2), "extracted_gbps": round(bits_per_step / tu / 1e9, 2),
+            "frac_uint16_bytes": round(uint16_bytes / tu / 1e9 / peak, 4),
+            "bytes_per_block_uint16": round(uint16_bytes / spec.nblocks, 2),
+            "frac_packed_bytes": round(packed_bytes / tu / 1e9 / peak, 4),
+            "outputs_equal_packed_step": bool((d_out.cpu().numpy().view(np.uint32) == gpu_out).all()),
+            "traffic": measured_traffic("raw_ingest_q16_b12_large_single_stream", RAW_SOURCES)}
+
     # end to end through the C ABI with HOST buffers: qext_pipeline_run copies
-    # pinned host samples in, extracts and copies the output back, per step
-    gpu_out = d_out.cpu().numpy().view(np.uint32)
+    # the pinned host input in, extracts and copies the output back, per step
+    del d_sx, d_sy
+    if args.step == "uint16" or args.unfused:
+        pb, h_x, h_y, count = spec.b, torch.from_numpy(sx.view(np.int16)), torch.from_numpy(sy.view(np.int16)), ns
+        h2d = 2 * ns * 2
+    else:
+        pb, h_x, h_y, count = 0, d_px[:nwords].cpu(), d_py[:nwords].cpu(), nwords * 32
+        h2d = 2 * nwords * 4
     del d_px, d_py
-    h_sx = torch.from_numpy(sx.view(np.int16)).pin_memory()
-    h_sy = torch.from_numpy(sy.view(np.int16)).pin_memory()
+    h_x, h_y = h_x.pin_memory(), h_y.pin_memory()
     h_out = torch.empty(out_words, dtype=torch.int32).pin_memory()
-    pp = qext.qext_pipeline_create(plan, spec.b, args.e2e_chunk_blocks)
+    pp = qext.qext_pipeline_create(plan, pb, args.e2e_chunk_blocks)
     for _ in range(max(1, min(args.warmup, 3))):
-        qext.qext_pipeline_run(pp, h_sx, h_sy, ns, spec.nblocks, h_out)
+        qext.qext_pipeline_run(pp, h_x, h_y, count, spec.nblocks, h_out)
     if world > 1:
         dist.barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        qext.qext_pipeline_run(pp, h_sx, h_sy, ns, spec.nblocks, h_out)
+        qext.qext_pipeline_run(pp, h_x, h_y, count, spec.nblocks, h_out)
     te = max_over_ranks(time.perf_counter() - t0, world)
     e2e_ok = bool((h_out.numpy().view(np.uint32) == gpu_out).all())
     # the host link: one step's input copied host -> device alone (pinned,
     # the same bytes), the bound of the end-to-end number
-    d_sx = torch.empty_like(h_sx, device=dev)
-    d_sy = torch.empty_like(h_sy, device=dev)
+    d_x = torch.empty_like(h_x, device=dev)
+    d_y = torch.empty_like(h_y, device=dev)
     link = []
     for _ in range(3):
         c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         c0.record()
-        d_sx.copy_(h_sx, non_blocking=True)
-        d_sy.copy_(h_sy, non_blocking=True)
+        d_x.copy_(h_x, non_blocking=True)
+        d_y.copy_(h_y, non_blocking=True)
         c1.record()
         torch.cuda.synchronize()
         link.append(c0.elapsed_time(c1) * 1e-3)
-    link_gbs = 2 * ns * 2 / statistics.median(link) / 1e9
-    del d_sx, d_sy
-    link_bound = bits_per_step / (2 * ns * 2 / (link_gbs * 1e9)) / 1e9
+    link_gbs = h2d / statistics.median(link) / 1e9
+    del d_x, d_y
+    link_bound = bits_per_step / (h2d / (link_gbs * 1e9)) / 1e9
     e2e = {"value": round(world * args.steps * bits_per_step / te / 1e9, 3), "unit": UNIT,
-           "h2d_bytes_per_step": 2 * ns * 2, "d2h_bytes_per_step": out_words * 4,
-           "path": "qext_pipeline_run: pinned host samples -> H2D chunks -> qext_extract_samples -> D2H, "
-                   "three CUDA streams overlapped, chunk %d blocks" % qext.qext_pipeline_info(pp)["chunk_blocks"],
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": out_words * 4,
+           "path": "qext_pipeline_run: pinned host %s -> H2D chunks -> %s -> D2H, three CUDA streams "
+                   "overlapped, chunk %d blocks" % (
+                       "12-bit samples (uint16)" if pb else "packed words",
+                       "qext_extract_samples" if pb else "qext_extract",
+                       qext.qext_pipeline_info(pp)["chunk_blocks"]),
            "matches_device_path": e2e_ok,
            "h2d_link_gbs": round(link_gbs, 1),
            "link_bound_value": round(link_bound, 3),
            "frac_of_link_bound": round(args.steps * bits_per_step / te / 1e9 / link_bound, 4)}
     pp.close()
-    del h_sx, h_sy
+    del h_x, h_y
 
     extra = {}
     if not args.no_extra and world == 1:
@@ -668,10 +715,11 @@ def run_gpu(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic (seeded quantised-Gaussian 12-bit ADC samples, numpy PCG64)",
             "config": dict(workload_config(spec, info, world), step=(
-                "qext_pack_samples(x), qext_pack_samples(y), qext_extract" if args.unfused
-                else "qext_extract_samples (fused ingest + extraction, one kernel)")),
+                "qext_pack_samples(x), qext_pack_samples(y), qext_extract (from uint16 samples)" if args.unfused
+                else "qext_extract_samples (uint16 samples, ingest fused into the extraction kernel)"
+                if args.step == "uint16" else "qext_extract (packed 12-bit samples, one kernel)")),
             "input_gbps": round(input_gbps, 2),
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "uint16_step": uint16_step,
             "clocks": {k: clk.get(k) for k in ("sm_mhz", "sm_max_mhz", "reasons", "samples", "source")},
             "gpu_launches": launches_per_step * args.steps,
         }
@@ -699,7 +747,10 @@ def main(argv=None):
     ap.add_argument("--e2e-chunk-blocks", type=int, default=1 << 17)
     ap.add_argument("--serving-requests", type=int, default=1000)
     ap.add_argument("--unfused", action="store_true",
-                    help="step = qext_pack_samples x2 + qext_extract instead of the fused qext_extract_samples")
+                    help="step = qext_pack_samples x2 (uint16 samples) + qext_extract")
+    ap.add_argument("--step", choices=["packed", "uint16"], default="packed",
+                    help="input of the step: packed 12-bit samples (qext_extract) or uint16 sample containers "
+                         "(qext_extract_samples, ingest fused)")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per launch of the dominant kernel, if captured for this build")
     args = ap.parse_args(argv)

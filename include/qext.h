@@ -145,19 +145,24 @@ int qext_extract(const qext_plan *p, const uint32_t *x, const uint32_t *y, uint6
 #define QEXT_F_NBUF1 0x2u  /* one tile buffer per CTA (more CTAs per SM) instead of two (prefetch) */
 #define QEXT_F_TILE32 0x4u /* at most 32 blocks per tile */
 #define QEXT_F_TILE64 0x8u /* at most 64 blocks per tile (exclusive with TILE32) */
-#define QEXT_F_TEST_TIMEOUT 0x10u /* test of failure detection: every CTA arms its tile barrier but issues no
-                                   copy, gives up its bounded wait after a few polls, records QEXT_E_TIMEOUT
-                                   (qext_device_status) and returns; outputs are not written.  Needs 16-byte
-                                   aligned x, y and a staged tile (else INVAL).  qext_extract_samples_ex
-                                   accepts it for its per-warp kernel (q = 4, 16 with n_p = 64): every
-                                   warp arms its barrier without a copy (else INVAL). */
+#define QEXT_F_TEST_TIMEOUT 0x10u /* test of failure detection: every CTA (or, in the per-warp kernels,
+                                   every warp) arms its barrier but issues no copy, gives up its bounded
+                                   wait after a few polls, records QEXT_E_TIMEOUT (qext_device_status) and
+                                   returns; outputs are not written.  Needs 16-byte aligned x, y and a
+                                   staged tile (else INVAL).  Alone it tests the default kernel of the
+                                   plan (the per-warp kernel for q = 16 with n_p = 64); with
+                                   QEXT_F_CTA_TILES, the CTA-tile kernel.  qext_extract_samples_ex
+                                   accepts it for its per-warp kernel (q = 4, 16 with n_p = 64) only. */
 #define QEXT_F_ALL 0x1Fu
 
 /*
  * qext_extract_ex -- qext_extract with launch options (flags, 0 = the
  * default path chosen by qext_extract).  Same arguments, ownership and errors;
  * INVAL also for unknown flag bits.  The output is identical for every flag
- * combination.
+ * combination.  The default path for q = 16 with n_p = 64 and 16-byte
+ * aligned x, y is the per-warp copy pipeline of qext_extract_samples_ex (its
+ * 16-bit samples are the packed stream); any flag, including
+ * QEXT_F_CTA_TILES (below), selects the CTA-tile kernel instead.
  */
 int qext_extract_ex(const qext_plan *p, const uint32_t *x, const uint32_t *y, uint64_t nblocks, uint32_t *out,
                     qext_cuda_stream stream, uint32_t flags);
@@ -195,7 +200,8 @@ int qext_extract_samples(const qext_plan *p, uint32_t b, const uint16_t *x_sampl
 /* Two raw-sample buffers (per warp, or per CTA with CTA-wide tiles), the next
  * copy issued one whole tile ahead (more shared memory, fewer warps per SM). */
 #define QEXT_F_RAW_PREFETCH 0x40u
-/* CTA-wide tiles packed in place even where the per-warp kernel applies. */
+/* CTA-wide tiles (packed in place, for samples) even where the per-warp
+ * kernel applies; also accepted by qext_extract_ex. */
 #define QEXT_F_CTA_TILES 0x80u
 int qext_extract_samples_ex(const qext_plan *p, uint32_t b, const uint16_t *x_samples, const uint16_t *y_samples,
                             uint64_t nsamples, uint64_t nblocks, uint32_t *out, qext_cuda_stream stream,

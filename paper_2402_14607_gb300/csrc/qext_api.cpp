@@ -14,7 +14,7 @@ extern "C" {
 int qext_extract_ex(const qext_plan *p, const uint32_t *x, const uint32_t *y, uint64_t nblocks, uint32_t *out,
                     qext_cuda_stream stream, uint32_t flags) {
     if (!p) return QEXT_E_INVAL;
-    if (flags & ~uint32_t(QEXT_F_ALL)) return QEXT_E_INVAL;
+    if (flags & ~uint32_t(QEXT_F_ALL | QEXT_F_CTA_TILES)) return QEXT_E_INVAL;
     if ((flags & QEXT_F_TILE32) && (flags & QEXT_F_TILE64)) return QEXT_E_INVAL;
     if (!p->gpu_supported && !p->gpu_q80) return QEXT_E_UNSUPPORTED;
     if (p->gpu_q80 && flags) return QEXT_E_INVAL;  // one kernel, no launch options

@@ -294,8 +294,8 @@ int qext_batch_create(const qext_batch_item *items, uint32_t nitems, qext_batch 
         d.s.ntaps = it.plan->ntaps;
         for (int k = 0; k < 4; ++k) {
             d.s.taps[k] = it.plan->taps[k];
-            d.s.tap_mul[k] = k < int(it.plan->ntaps) ? 1u << (it.plan->taps[k] & 31u) : 0u;
         }
+        d.s.set_multipliers();
         d.s.status = qext::device_status_ptr();
         d.q = it.plan->q;
         d.tma = al % 16 == 0;
@@ -556,8 +556,8 @@ extern "C" int qext_batch_run_noalloc(const qext_batch_item *items, uint32_t nit
         d.s.ntaps = it.plan->ntaps;
         for (int j = 0; j < 4; ++j) {
             d.s.taps[j] = it.plan->taps[j];
-            d.s.tap_mul[j] = j < int(it.plan->ntaps) ? 1u << (it.plan->taps[j] & 31u) : 0u;
         }
+        d.s.set_multipliers();
         d.s.status = qext::device_status_ptr();
         d.q = it.plan->q;
         d.tma = al % 16 == 0;
@@ -624,8 +624,8 @@ int batch_launch_tables(const qext_batch_item *items, uint32_t nitems, void *d_t
         d.s.ntaps = it.plan->ntaps;
         for (int j = 0; j < 4; ++j) {
             d.s.taps[j] = it.plan->taps[j];
-            d.s.tap_mul[j] = j < int(it.plan->ntaps) ? 1u << (it.plan->taps[j] & 31u) : 0u;
         }
+        d.s.set_multipliers();
         d.s.status = qext::device_status_ptr();
         d.q = it.plan->q;
         d.tma = ((reinterpret_cast<uintptr_t>(it.x) | reinterpret_cast<uintptr_t>(it.y)) % 16) == 0;

@@ -12,8 +12,9 @@ __device__ __forceinline__ uint4 lds4(const uint32_t *p) { return *reinterpret_c
 // ---------------------------------------------------------------------------
 // Accumulator of one block's sliced Gram diagonals, q <= 32.
 // ---------------------------------------------------------------------------
-// q = 16: one Karatsuba level over the element bits, with low half L (bits
-// 0..7), high half H (8..15) and sum S = L + H of each element:
+// One Karatsuba level over the element bits (q = 16 in kernels whose register
+// budget is tight), with low half L (bits 0..7), high half H (8..15) and sum
+// S = L + H of each element:
 //     x y = A + t^8 (A + B + C) + t^16 B,   A = LxLy, B = HxHy, C = SxSy,
 //         = D + t^8 D + t^8 C,             D = A + t^8 B.
 // So A and B accumulate into one array D (A at offset 0, B at offset 8; 23
@@ -50,7 +51,7 @@ struct Acc {
         }
     }
     // z (2q-1 bits) = parities of the Gram diagonals
-    __device__ __forceinline__ uint64_t unreduced() {
+    __device__ __forceinline__ uint64_t unreduced(const StreamArgs &) {
         if constexpr (kKaratsuba) {
             // z = D + t^8 D + t^8 C on the parities (parity is linear): rD
             // holds D's 23 parity bits in bits 9..31, rC C's 15 in bits 17..31
@@ -62,12 +63,133 @@ struct Acc {
     }
 };
 
+// ---------------------------------------------------------------------------
+// q = 16 with two Karatsuba levels and byte-field parity sums (the default
+// wherever 128 registers per thread are available).
+// ---------------------------------------------------------------------------
+// The second level splits every 8 x 8 product U V (U = U0 + t^4 U1) into
+//     U V = E + t^4 E + t^4 M,   E = U0 V0 + t^4 U1 V1,   M = (U0 + U1)(V0 + V1),
+// three 4 x 4 products.  With the first level's D = A + t^8 B this gives
+//     D = F + t^4 F + t^4 G,     F = E_A + t^8 E_B (19),  G = M_A + t^8 M_B (15),
+//     C = E_C + t^4 E_C + t^4 M_C,                        E_C (11), M_C (7),
+//     x y = D + t^8 D + t^8 C,
+// 9 x 16 = 144 AND-XORs and 40 operand sums per group of 32 elements
+// (instead of 192 and 16) into 52 accumulators.  Their parities are linear
+// combinations, taken in byte fields: the popcounts of four consecutive
+// accumulators are packed into one word by IMADs (w = w * 256 + popc, every
+// field <= 32), so t^4 and t^8 are shifts by one and two whole words and sums
+// of three fields stay below 256; the fields' low bits are masked between
+// combination steps, and the four parity bits of a word gather into a nibble
+// by one multiply: ((w & 0x01010101) * 0x01020408) >> 24.  The field steps
+// run on the FMA pipe, next to the products and transposes that fill the
+// ALU pipe.
+struct Acc16K2 {
+    uint32_t F[19], G[15], E[11], M[7];
+    __device__ __forceinline__ Acc16K2() {
+#pragma unroll
+        for (int i = 0; i < 19; ++i) F[i] = 0;
+#pragma unroll
+        for (int i = 0; i < 15; ++i) G[i] = 0;
+#pragma unroll
+        for (int i = 0; i < 11; ++i) E[i] = 0;
+#pragma unroll
+        for (int i = 0; i < 7; ++i) M[i] = 0;
+    }
+    // acc[j + l] ^= u[j] & v[l], 4 x 4
+    __device__ __forceinline__ static void mul4(const uint32_t *u, const uint32_t *v, uint32_t *acc) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int l = 0; l < 4; ++l) acc[j + l] = lop_and_xor(u[j], v[l], acc[j + l]);
+    }
+    // one 8 x 8 product: E-part into e (11 diagonals), M-part into m (7)
+    __device__ __forceinline__ static void mul8(const uint32_t *U, const uint32_t *V, uint32_t *e, uint32_t *m) {
+        uint32_t us[4], vs[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            us[j] = U[j] ^ U[j + 4];
+            vs[j] = V[j] ^ V[j + 4];
+        }
+        mul4(U, V, e);
+        mul4(U + 4, V + 4, e + 4);
+        mul4(us, vs, m);
+    }
+    // Sliced group of 32 elements: X[j], Y[j] = bit j of the 32 elements.
+    __device__ __forceinline__ void add(uint32_t (&X)[16], uint32_t (&Y)[16]) {
+        uint32_t XS[8], YS[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            XS[j] = X[j] ^ X[j + 8];
+            YS[j] = Y[j] ^ Y[j + 8];
+        }
+        mul8(X, Y, F, G);              // A = L L
+        mul8(X + 8, Y + 8, F + 8, G + 8);  // B = H H, at t^8
+        mul8(XS, YS, E, M);            // C = S S
+    }
+    // popcounts of acc[0 .. N) as byte fields of ceil(N / 4) words
+    template <int N, int W>
+    __device__ __forceinline__ static void fields(const uint32_t *acc, uint32_t (&w)[W], const StreamArgs &s) {
+        static_assert(W == (N + 3) / 4, "one word per four fields");
+#pragma unroll
+        for (int i = 0; i < W; ++i) {
+            const int top = (4 * i + 3 < N ? 4 * i + 3 : N - 1);
+            uint32_t v = __popc(acc[top]);
+#pragma unroll
+            for (int f = top - 1; f >= 4 * i; --f) v = v * s.byte_mul + uint32_t(__popc(acc[f]));
+            w[i] = v;
+        }
+    }
+    // z (31 bits), unreduced
+    __device__ __forceinline__ uint64_t unreduced(const StreamArgs &s) const {
+        constexpr uint32_t ONE = 0x01010101u;
+        uint32_t WF[5], WG[4], WE[3], WM[2];
+        fields<19, 5>(F, WF, s);
+        fields<15, 4>(G, WG, s);
+        fields<11, 3>(E, WE, s);
+        fields<7, 2>(M, WM, s);
+        uint32_t WD[6], WC[4];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {  // D = F + t^4 F + t^4 G
+            uint32_t v = i < 5 ? WF[i] : 0u;
+            if (i >= 1) v += WF[i - 1] + (i - 1 < 4 ? WG[i - 1] : 0u);
+            WD[i] = v & ONE;
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {  // C = E + t^4 E + t^4 M
+            uint32_t v = i < 3 ? WE[i] : 0u;
+            if (i >= 1) v += WE[i - 1] + (i - 1 < 2 ? WM[i - 1] : 0u);
+            WC[i] = v & ONE;
+        }
+        uint32_t z = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {  // z = D + t^8 D + t^8 C
+            uint32_t v = i < 6 ? WD[i] : 0u;
+            if (i >= 2) v += WD[i - 2] + (i - 2 < 4 ? WC[i - 2] : 0u);
+            const uint32_t nib = ((v & ONE) * 0x01020408u) >> 24;
+            z = nib * s.nib_mul[i] + z;
+        }
+        return z;
+    }
+};
+
+template <int Q>
+struct BlockAccT {
+    using type = Acc<Q>;
+};
+template <>
+struct BlockAccT<16> {
+    using type = Acc16K2;
+};
+// The accumulator of one block at field degree Q.
+template <int Q>
+using BlockAcc = typename BlockAccT<Q>::type;
+
 // One block, q <= 32, from a block's words xs / ys (shared or global memory).
 // With vec, the block's 16-byte chunks are read starting at chunk rot.
 template <int Q>
 __device__ __forceinline__ uint64_t block_small_q(const uint32_t *xs, const uint32_t *ys, uint32_t wpb, int vec,
                                                   uint32_t rot, const StreamArgs &s) {
-    Acc<Q> acc;
+    BlockAcc<Q> acc;
     if constexpr (Q >= 4) {
         if (vec && wpb == 2 * Q) {
             // n_p = 64: two groups of 32 elements, 2Q/4 chunks, fully unrolled
@@ -93,7 +215,7 @@ __device__ __forceinline__ uint64_t block_small_q(const uint32_t *xs, const uint
                 slice<Q>(Y);
                 acc.add(X, Y);
             }
-            return reduce_mod_p<Q>(acc.unreduced(), s);
+            return reduce_mod_p<Q>(acc.unreduced(s), s);
         }
     }
     if (vec) {
@@ -158,7 +280,7 @@ __device__ __forceinline__ uint64_t block_small_q(const uint32_t *xs, const uint
             acc.add(X, Y);
         }
     }
-    return reduce_mod_p<Q>(acc.unreduced(), s);
+    return reduce_mod_p<Q>(acc.unreduced(s), s);
 }
 
 // ---------------------------------------------------------------------------

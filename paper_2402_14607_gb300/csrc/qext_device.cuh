@@ -35,7 +35,29 @@ struct StreamArgs {
     uint32_t taps[4];
     uint32_t tap_mul[4];    // 2^taps[t] for t < ntaps, else 0 (run-time multipliers: shifts by taps as IMADs)
     int *status;            // device status word (qext_device_status), or null
+    // Run-time multipliers of the byte-field parity assembly (Acc16K2): kept
+    // out of the compiler's sight so that the steps stay IMADs on the FMA pipe
+    // instead of shifts on the ALU pipe, which the products saturate.
+    uint32_t byte_mul;      // 256
+    uint32_t nib_mul[8];    // 2^(4i)
+    __host__ __device__ void set_multipliers() {
+        for (int t = 0; t < 4; ++t) tap_mul[t] = t < int(ntaps) ? 1u << (taps[t] & 31u) : 0u;
+        byte_mul = 256u;
+        for (int i = 0; i < 8; ++i) nib_mul[i] = 1u << (4 * i);
+    }
 };
+
+// Programmatic dependent launch (sm_90+).  A kernel launched with the
+// programmatic-serialization attribute lets the next kernel of its stream be
+// scheduled as soon as every CTA has passed pdl_prologue(), and that next
+// kernel's own pdl_prologue() returns only once this grid has completed and
+// its memory is visible.  So nothing before the prologue may touch global
+// memory; the overlap is the next launch's set-up and CTA start-up, hidden
+// behind this grid's tail.  Without the attribute both instructions are no-ops.
+__device__ __forceinline__ void pdl_prologue() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
 
 // ---------------------------------------------------------------------------
 // Register bit-matrix primitives.

@@ -360,8 +360,8 @@ static StreamArgs stream_args(const qext_plan *p, const uint32_t *x, const uint3
     s.ntaps = p->ntaps;
     for (int i = 0; i < 4; ++i) {
         s.taps[i] = p->taps[i];
-        s.tap_mul[i] = i < int(p->ntaps) ? 1u << (p->taps[i] & 31u) : 0u;
     }
+    s.set_multipliers();
     s.status = device_status_ptr();
     return s;
 }
@@ -370,6 +370,11 @@ int launch_extract(const qext_plan *p, const uint32_t *x, const uint32_t *y, uin
                    qext_cuda_stream stream, uint32_t flags) {
     const StreamArgs s = stream_args(p, x, y, nblocks, out);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    // q = 16, n_p = 64, 16-byte aligned sources, default launch: per-warp
+    // copy pipelines (qext_extract_raw.cu)
+    const uintptr_t al = reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y);
+    if (p->q == 16 && p->n == 1024 && al % 16 == 0 && (flags & ~uint32_t(QEXT_F_TEST_TIMEOUT)) == 0)
+        return launch_extract_packed16(s, stream, flags);
     switch (p->q) {
         case 1: return launch_q<1, 0>(s, nullptr, nullptr, 0, st, flags);
         case 2: return launch_q<2, 0>(s, nullptr, nullptr, 0, st, flags);

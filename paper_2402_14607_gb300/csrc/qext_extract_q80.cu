@@ -324,8 +324,8 @@ int launch_extract_q80(const qext_plan *p, const uint32_t *x, const uint32_t *y,
     a.s.ntaps = p->ntaps;
     for (int i = 0; i < 4; ++i) {
         a.s.taps[i] = p->taps[i];
-        a.s.tap_mul[i] = 0;
     }
+    a.s.set_multipliers();
     a.s.status = device_status_ptr();
     a.n_p = p->n_p;
     a.zero = 0;

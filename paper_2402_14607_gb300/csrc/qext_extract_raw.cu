@@ -36,7 +36,11 @@ using namespace qxd;
 
 namespace {
 
-constexpr int kWarps = 4;  // warps per CTA, each an independent pipeline
+// Warps per CTA, each an independent pipeline: q = 16 runs one CTA of up to
+// kMaxWarps warps per SM (as many as the shared-memory buffers allow), q = 4
+// several CTAs of kSmallWarps.
+constexpr int kMaxWarps = 16;
+constexpr int kSmallWarps = 4;
 
 template <int Q, int B>
 struct RawLayout {
@@ -166,12 +170,12 @@ __device__ __forceinline__ void edge_words(uint4 h, uint4 t, const EdgeSel &es, 
 }
 
 template <int Q, int B>
-__global__ void __launch_bounds__(32 * kWarps) extract_raw_kernel(const RawArgs a) {
+__global__ void __launch_bounds__(Q == 16 ? 32 * kMaxWarps : 32 * kSmallWarps) extract_raw_kernel(const RawArgs a) {
     using L = RawLayout<Q, B>;
     extern __shared__ __align__(16) uint4 raw[];
-    __shared__ __align__(8) uint64_t full[kWarps][2];
+    __shared__ __align__(8) uint64_t full[kMaxWarps][2];
     const StreamArgs &s = a.s;
-    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     uint4 *const buf0 = raw + size_t(warp) * a.nbuf * 2 * L::kCap;  // [x periods | y periods] per buffer
     uint4 *const buf1 = buf0 + (a.nbuf > 1 ? 2 * L::kCap : 0);
     if (lane == 0) {
@@ -180,9 +184,10 @@ __global__ void __launch_bounds__(32 * kWarps) extract_raw_kernel(const RawArgs 
         fence_mbar_init();
     }
     __syncwarp();
+    pdl_prologue();
 
-    const uint64_t gwarps = uint64_t(gridDim.x) * kWarps;
-    uint64_t t = uint64_t(blockIdx.x) * kWarps + warp;
+    const uint64_t gwarps = uint64_t(gridDim.x) * nwarps;
+    uint64_t t = uint64_t(blockIdx.x) * nwarps + warp;
     uint32_t uses0 = 0, uses1 = 0;  // completed phases of full[warp][0], [1]
     bool next_issued = false;       // lane 0: the next sub-tile's copy is in flight
     if (t < a.nsub && lane == 0) {
@@ -257,7 +262,7 @@ __global__ void __launch_bounds__(32 * kWarps) extract_raw_kernel(const RawArgs 
                 edge_words(bx[hp], bx[tp], es, ex1, ex2);
                 edge_words(by[hp], by[tp], es, ey1, ey2);
             }
-            Acc<Q> acc;
+            BlockAcc<Q> acc;
             {
                 uint32_t X[Q], Y[Q];
                 raw_group<Q, B, 0>(bx, by, fp_rel, rot, ex1, ey1, X, Y);
@@ -286,7 +291,7 @@ __global__ void __launch_bounds__(32 * kWarps) extract_raw_kernel(const RawArgs 
                 slice<Q>(Y);
                 acc.add(X, Y);
             }
-            uint64_t v = reduce_mod_p<Q>(acc.unreduced(), s) & mask_m(s.m);
+            uint64_t v = reduce_mod_p<Q>(acc.unreduced(s), s) & mask_m(s.m);
             if (blk >= s.nblocks) v = 0;
             store_warp(v, base, s.nblocks, s.m, s.out);
         }
@@ -294,31 +299,160 @@ __global__ void __launch_bounds__(32 * kWarps) extract_raw_kernel(const RawArgs 
     (void)next_issued;
 }
 
+// ---------------------------------------------------------------------------
+// Packed-word variant (qext_extract for q = 16 with n_p = 64 and 16-byte
+// aligned sources): the same per-warp pipeline over sub-tiles of 32 blocks,
+// without the period bookkeeping of raw samples.  A sub-tile's blocks (128
+// bytes per source each) arrive by one bulk copy per source; lane l reads its
+// block's eight 16-byte chunks starting at chunk l mod 8, so a quarter-warp's
+// reads fall on eight distinct bank groups.  Lanes past the last block of a
+// partial sub-tile compute on stale buffer contents and store nothing.
+// ---------------------------------------------------------------------------
+struct PackedArgs {
+    StreamArgs s;
+    uint64_t nsub;       // sub-tiles of 32 blocks
+    uint32_t max_polls;  // bound of every mbarrier wait
+    int no_copy;         // test of failure detection: barriers armed, no copy issued
+};
+
+constexpr uint32_t kPackedWpb = 32;                 // words per block and source (q = 16, n_p = 64)
+constexpr uint32_t kPackedChunks = kPackedWpb / 4;  // 16-byte chunks per block
+
+__global__ void __launch_bounds__(32 * kMaxWarps) extract_packed16_kernel(const PackedArgs a) {
+    extern __shared__ __align__(16) uint4 pk[];
+    __shared__ __align__(8) uint64_t full[kMaxWarps];
+    const StreamArgs &s = a.s;
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    uint4 *const bx = pk + size_t(warp) * 2 * 32 * kPackedChunks, *const by = bx + 32 * kPackedChunks;
+    if (lane == 0) {
+        mbar_init(&full[warp], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    pdl_prologue();
+
+    const uint64_t gwarps = uint64_t(gridDim.x) * nwarps;
+    uint64_t t = uint64_t(blockIdx.x) * nwarps + warp;
+    auto issue = [&](uint64_t tt) {
+        const uint64_t b0 = 32 * tt;
+        const uint32_t nb = s.nblocks - b0 < 32 ? uint32_t(s.nblocks - b0) : 32u;
+        const uint32_t bytes = nb * kPackedWpb * 4u;
+        mbar_expect_tx(&full[warp], 2u * bytes);
+        if (a.no_copy) return;  // the completion never comes: the wait must give up
+        tma_load_1d(bx, s.x + b0 * kPackedWpb, bytes, &full[warp]);
+        tma_load_1d(by, s.y + b0 * kPackedWpb, bytes, &full[warp]);
+    };
+    if (lane == 0 && t < a.nsub) issue(t);
+    const uint4 *const px = bx + lane * kPackedChunks, *const py = by + lane * kPackedChunks;
+    for (uint32_t k = 0; t < a.nsub; ++k, t += gwarps) {
+        const bool ok = mbar_wait_bounded(&full[warp], k & 1u, a.max_polls);
+        if (!__all_sync(0xffffffffu, ok)) {
+            if (lane == 0) {
+                record_status(s.status, QEXT_E_TIMEOUT);
+                if (!a.no_copy) mbar_wait_bounded(&full[warp], k & 1u, a.max_polls);  // let the copy in flight land
+            }
+            return;
+        }
+        Acc16K2 acc;
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+            uint32_t X[16], Y[16];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const uint32_t ch = (uint32_t(4 * g + c) + lane) & (kPackedChunks - 1);
+                const uint4 vx = px[ch], vy = py[ch];
+                X[4 * c] = vx.x;
+                X[4 * c + 1] = vx.y;
+                X[4 * c + 2] = vx.z;
+                X[4 * c + 3] = vx.w;
+                Y[4 * c] = vy.x;
+                Y[4 * c + 1] = vy.y;
+                Y[4 * c + 2] = vy.z;
+                Y[4 * c + 3] = vy.w;
+            }
+            if (g == 1) {
+                // every lane holds its block: the buffer may be refilled
+                __syncwarp();
+                if (lane == 0 && t + gwarps < a.nsub) issue(t + gwarps);
+            }
+            slice<16>(X);
+            slice<16>(Y);
+            acc.add(X, Y);
+        }
+        uint64_t v = reduce_mod_p<16>(acc.unreduced(s), s) & mask_m(s.m);
+        if (32 * t + lane >= s.nblocks) v = 0;
+        store_warp(v, 32 * t, s.nblocks, s.m, s.out);
+    }
+}
+
+int launch_packed16(const StreamArgs &s, cudaStream_t st, uint32_t flags) {
+    static qext::DeviceSlots attr_set, smem_optin;
+    const int dev = qext::current_device();
+    if (dev < 0) return QEXT_E_CUDA;
+    const int sms = qext::sm_count(dev);
+    if (sms <= 0) return QEXT_E_CUDA;
+    const int optin = smem_optin.get(dev, [dev] {
+        int v = 0;
+        return cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess ? v : 0;
+    });
+    if (optin <= 0) return QEXT_E_CUDA;
+    const size_t per_warp = size_t(2) * 32 * kPackedChunks * sizeof(uint4);
+    const size_t fit = (size_t(optin) - 1024) / per_warp;
+    const int W = int(fit < size_t(kMaxWarps) ? fit : size_t(kMaxWarps));
+    if (attr_set.get(dev, [optin] {
+            return cudaFuncSetAttribute(extract_packed16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        optin - 1024) == cudaSuccess ? 1 : 0;
+        }) <= 0)
+        return QEXT_E_CUDA;
+    PackedArgs a;
+    a.s = s;
+    a.nsub = (s.nblocks + 31) / 32;
+    a.no_copy = (flags & QEXT_F_TEST_TIMEOUT) ? 1 : 0;
+    a.max_polls = a.no_copy ? 256u : kMaxPolls;
+    const uint64_t ctas = (a.nsub + W - 1) / W;
+    const int grid = int(ctas < uint64_t(sms) ? ctas : uint64_t(sms));
+    return qext::launch_pdl(extract_packed16_kernel, grid, 32 * W, size_t(W) * per_warp, st, a);
+}
+
 template <int Q, int B>
 int launch_raw(const StreamArgs &s, const uint16_t *sx, const uint16_t *sy, uint64_t nsamples, cudaStream_t st,
                uint32_t flags) {
     using L = RawLayout<Q, B>;
     if (s.wpb != uint32_t(L::WPB)) return QEXT_E_UNSUPPORTED;
-    static qext::DeviceSlots attr_set, occ[2];  // per device; occupancy by buffers per warp
+    static qext::DeviceSlots attr_set, occ[2], smem_optin;  // per device; occupancy by buffers per warp
     const int dev = qext::current_device();
     if (dev < 0) return QEXT_E_CUDA;
     const int sms = qext::sm_count(dev);
     if (sms <= 0) return QEXT_E_CUDA;
+    const int optin = smem_optin.get(dev, [dev] {
+        int v = 0;
+        return cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess ? v : 0;
+    });
+    if (optin <= 0) return QEXT_E_CUDA;
     const uint32_t nbuf = (flags & QEXT_F_RAW_PREFETCH) ? 2u : 1u;
-    const size_t smem = size_t(kWarps) * nbuf * 2 * L::kCap * sizeof(uint4);
-    if (attr_set.get(dev, [] {
+    const size_t per_warp = size_t(nbuf) * 2 * L::kCap * sizeof(uint4);
+    // warps per CTA: q = 16 fills one CTA per SM (as many warps as the
+    // buffers allow), q = 4 keeps small CTAs
+    size_t fit = (size_t(optin) - 1024) / per_warp;
+    int W = Q == 16 ? int(fit < size_t(kMaxWarps) ? fit : size_t(kMaxWarps)) : kSmallWarps;
+    if (W < 1) return QEXT_E_UNSUPPORTED;
+    const size_t smem = size_t(W) * per_warp;
+    if (attr_set.get(dev, [optin] {
             return cudaFuncSetAttribute(extract_raw_kernel<Q, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        int(size_t(kWarps) * 2 * 2 * L::kCap * sizeof(uint4))) == cudaSuccess ? 1 : 0;
+                                        optin - 1024) == cudaSuccess ? 1 : 0;
         }) <= 0)
         return QEXT_E_CUDA;
-    const int o = occ[nbuf - 1].get(dev, [&] {
-        int v = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, extract_raw_kernel<Q, B>, 32 * kWarps, smem) !=
-            cudaSuccess)
-            return 0;
-        return v < 1 ? 1 : v;
-    });
-    if (o <= 0) return QEXT_E_CUDA;
+    int o = 1;
+    if (Q != 16) {
+        o = occ[nbuf - 1].get(dev, [&] {
+            int v = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, extract_raw_kernel<Q, B>, 32 * W, smem) !=
+                cudaSuccess)
+                return 0;
+            return v < 1 ? 1 : v;
+        });
+        if (o <= 0) return QEXT_E_CUDA;
+    }
     RawArgs a;
     a.s = s;
     a.sx = sx;
@@ -328,10 +462,9 @@ int launch_raw(const StreamArgs &s, const uint16_t *sx, const uint16_t *sy, uint
     a.nbuf = nbuf;
     a.no_copy = (flags & QEXT_F_TEST_TIMEOUT) ? 1 : 0;
     a.max_polls = a.no_copy ? 256u : kMaxPolls;
-    const uint64_t ctas = (a.nsub + kWarps - 1) / kWarps, cap = uint64_t(sms) * o;
+    const uint64_t ctas = (a.nsub + W - 1) / W, cap = uint64_t(sms) * o;
     const int grid = int(ctas < cap ? ctas : cap);
-    extract_raw_kernel<Q, B><<<grid, 32 * kWarps, smem, st>>>(a);
-    return cudaGetLastError() == cudaSuccess ? QEXT_OK : QEXT_E_CUDA;
+    return qext::launch_pdl(extract_raw_kernel<Q, B>, grid, 32 * W, smem, st, a);
 }
 
 template <int Q>
@@ -348,6 +481,12 @@ int launch_raw_q(uint32_t b, const StreamArgs &s, const uint16_t *sx, const uint
 }  // namespace
 
 namespace qext {
+
+int launch_extract_packed16(const StreamArgs &s, qext_cuda_stream stream, uint32_t flags) {
+    if (s.nblocks == 0) return QEXT_OK;
+    if (s.wpb != kPackedWpb) return QEXT_E_UNSUPPORTED;
+    return launch_packed16(s, reinterpret_cast<cudaStream_t>(stream), flags);
+}
 
 int launch_raw_samples(uint32_t q, uint32_t b, const StreamArgs &s, const uint16_t *sx, const uint16_t *sy,
                        uint64_t nsamples, qext_cuda_stream stream, uint32_t flags) {

@@ -5,6 +5,7 @@
 
 #include <atomic>
 #include <cstdint>
+#include <utility>
 
 #include "../../include/qext.h"
 
@@ -69,6 +70,26 @@ struct DeviceSlots {
     }
 };
 
+// Launches kernel<<<grid, block, smem, stream>>>(args...) with programmatic
+// stream serialization: the next kernel of the stream may be scheduled while
+// this one drains.  Only for kernels that begin with qxd::pdl_prologue(),
+// which makes every such kernel wait for its predecessor's completion before
+// it touches global memory.
+template <typename... KArgs, typename... Args>
+int launch_pdl(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t stream, Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(grid));
+    cfg.blockDim = dim3(unsigned(block));
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...) == cudaSuccess ? QEXT_OK : QEXT_E_CUDA;
+}
+
 // Multiprocessor count of device dev (cached), or 0 on error.
 int sm_count(int dev);
 
@@ -93,6 +114,10 @@ int launch_fused_samples(uint32_t q, uint32_t b, const qxd::StreamArgs &s, const
 // other shapes.
 int launch_raw_samples(uint32_t q, uint32_t b, const qxd::StreamArgs &s, const uint16_t *sx, const uint16_t *sy,
                        uint64_t nsamples, qext_cuda_stream stream, uint32_t flags);
+// Per-warp kernel for packed words, q = 16 with n_p = 64 (s.x, s.y 16-byte
+// aligned); QEXT_E_UNSUPPORTED for other block lengths.  flags: 0 or
+// QEXT_F_TEST_TIMEOUT.
+int launch_extract_packed16(const qxd::StreamArgs &s, qext_cuda_stream stream, uint32_t flags);
 // q = 80 blocks (any n_p), packed words.
 int launch_extract_q80(const qext_plan *p, const uint32_t *x, const uint32_t *y, uint64_t nblocks, uint32_t *out,
                        qext_cuda_stream stream);

@@ -246,8 +246,8 @@ int qext_stream_push(qext_stream *s, const uint32_t *x, const uint32_t *y, uint6
             g.s.ntaps = s->plan->ntaps;
             for (int i = 0; i < 4; ++i) {
                 g.s.taps[i] = s->plan->taps[i];
-                g.s.tap_mul[i] = i < int(s->plan->ntaps) ? 1u << (s->plan->taps[i] & 31u) : 0u;
             }
+            g.s.set_multipliers();
             g.s.status = qext::device_status_ptr();
             g.tx = s->tail[s->cur][0];
             g.ty = s->tail[s->cur][1];

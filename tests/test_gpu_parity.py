@@ -34,7 +34,7 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("flags", [0, qext.QEXT_F_DIRECT], ids=["tiled", "direct"])
+@pytest.mark.parametrize("flags", [0, qext.QEXT_F_DIRECT, qext.QEXT_F_CTA_TILES], ids=["default", "direct", "cta_tiles"])
 @pytest.mark.parametrize("q,n_p,m,nblocks,off", CASES)
 def test_extract_matches_oracle(q, n_p, m, nblocks, off, flags):
     plan = plan_for(q, n_p, m)
@@ -277,11 +277,12 @@ def test_pipeline_host_to_host_matches_oracle(q, b, nblocks, chunk):
     pp.close()
 
 
-def test_bounded_wait_times_out_and_context_survives():
-    """Failure detection without a fault: the tile barrier is armed but no
-    copy is issued, so every CTA's bounded wait runs out; the kernel records
-    QEXT_E_TIMEOUT and returns, the host reads the status, and the next
-    extraction on the same context is correct."""
+@pytest.mark.parametrize("kernel", [0, qext.QEXT_F_CTA_TILES], ids=["per_warp_packed", "cta_tiles"])
+def test_bounded_wait_times_out_and_context_survives(kernel):
+    """Failure detection without a fault: the barrier is armed but no copy is
+    issued, so every CTA's (per-warp kernel: every warp's) bounded wait runs
+    out; the kernel records QEXT_E_TIMEOUT and returns, the host reads the
+    status, and the next extraction on the same context is correct."""
     plan = plan_for(16, 64)
     nb = 4096
     x = workloads.random_words(71, nb * 32)
@@ -289,7 +290,7 @@ def test_bounded_wait_times_out_and_context_survives():
     tx, ty = dev_words(x), dev_words(y)
     out = torch.zeros(nb // 2, dtype=torch.int32, device="cuda")
     assert qext.qext_device_status() == qext.QEXT_OK
-    qext.qext_extract_ex(plan, tx, ty, nb, out, None, qext.QEXT_F_TEST_TIMEOUT)
+    qext.qext_extract_ex(plan, tx, ty, nb, out, None, qext.QEXT_F_TEST_TIMEOUT | kernel)
     torch.cuda.synchronize()
     assert qext.qext_device_status() == qext.QEXT_E_TIMEOUT
     assert qext.qext_device_status() == qext.QEXT_OK          # read clears it
