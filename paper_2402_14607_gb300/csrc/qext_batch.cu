@@ -80,9 +80,9 @@ __device__ __forceinline__ void compute_tile(const StreamArgs &s, uint64_t first
             if (lb < nb) {
                 uint32_t *xb = xs + lb * s.wpb, *yb = ys + lb * s.wpb;
                 if (s.wpb % 4 == 0)
-                    half_products64_inplace(xb, yb, s.wpb, tid, part, 2, A, B, C);
+                    half_products64_inplace(xb, yb, s.wpb, tid, part, 2, A, B, C, s);
                 else
-                    half_products64(xb, yb, s.wpb, 0, tid, part, 2, A, B, C);
+                    half_products64(xb, yb, s.wpb, 0, tid, part, 2, A, B, C, s);
             }
             A ^= __shfl_xor_sync(0xffffffffu, A, 1);
             B ^= __shfl_xor_sync(0xffffffffu, B, 1);

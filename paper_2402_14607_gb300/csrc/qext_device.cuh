@@ -39,10 +39,12 @@ struct StreamArgs {
     // out of the compiler's sight so that the steps stay IMADs on the FMA pipe
     // instead of shifts on the ALU pipe, which the products saturate.
     uint32_t byte_mul;      // 256
+    uint32_t byte_pos[4];   // 2^(8i)
     uint32_t nib_mul[8];    // 2^(4i)
     __host__ __device__ void set_multipliers() {
         for (int t = 0; t < 4; ++t) tap_mul[t] = t < int(ntaps) ? 1u << (taps[t] & 31u) : 0u;
         byte_mul = 256u;
+        for (int i = 0; i < 4; ++i) byte_pos[i] = 1u << (8 * i);
         for (int i = 0; i < 8; ++i) nib_mul[i] = 1u << (4 * i);
     }
 };

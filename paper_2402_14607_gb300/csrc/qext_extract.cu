@@ -77,6 +77,7 @@ __global__ void __launch_bounds__(kThreads) extract_tiled_kernel(const TileArgs 
         fence_mbar_init();
     }
     __syncthreads();
+    pdl_prologue();
 
     auto full_tile = [&](uint64_t t) { return (t + 1) * uint64_t(T) <= s.nblocks; };
     auto issue = [&](uint64_t t, int b) {
@@ -197,9 +198,9 @@ __global__ void __launch_bounds__(kThreads) extract_tiled_kernel(const TileArgs 
             if (blk < s.nblocks) {
                 uint32_t *xb = xs + lb * s.wpb, *yb = ys + lb * s.wpb;
                 if (ta.vec)
-                    half_products64_inplace(xb, yb, s.wpb, tid, part, TPB, A, Bm, C);
+                    half_products64_inplace(xb, yb, s.wpb, tid, part, TPB, A, Bm, C, s);
                 else
-                    half_products64(xb, yb, s.wpb, ta.vec, tid, part, TPB, A, Bm, C);
+                    half_products64(xb, yb, s.wpb, ta.vec, tid, part, TPB, A, Bm, C, s);
             }
             fence_proxy_async_smem();  // slices written over the tile, which a bulk copy refills later
             A ^= __shfl_xor_sync(0xffffffffu, A, 1);
@@ -227,6 +228,7 @@ __global__ void __launch_bounds__(kThreads) extract_tiled_kernel(const TileArgs 
 // ---------------------------------------------------------------------------
 template <int Q>
 __global__ void __launch_bounds__(kThreads) extract_direct_kernel(const StreamArgs s) {
+    pdl_prologue();
     const uint32_t lane = threadIdx.x & 31u;
     const uint64_t warp = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
@@ -237,9 +239,9 @@ __global__ void __launch_bounds__(kThreads) extract_direct_kernel(const StreamAr
             const uint32_t *xb = s.x + blk * s.wpb, *yb = s.y + blk * s.wpb;
             if constexpr (Q == 64) {
                 // scalar loads here: the per-part templates beat the one-copy loop
-                const uint64_t A = half_product64<0>(xb, yb, s.wpb, 0, 0, 0, 1);
-                const uint64_t B = half_product64<1>(xb, yb, s.wpb, 0, 0, 0, 1);
-                const uint64_t C = half_product64<2>(xb, yb, s.wpb, 0, 0, 0, 1);
+                const uint64_t A = half_product64<0>(xb, yb, s.wpb, 0, 0, 0, 1, s);
+                const uint64_t B = half_product64<1>(xb, yb, s.wpb, 0, 0, 0, 1, s);
+                const uint64_t C = half_product64<2>(xb, yb, s.wpb, 0, 0, 0, 1, s);
                 v = combine_q64(A, B, C, s);
             } else {
                 v = block_small_q<Q>(xb, yb, s.wpb, 0, 0, s);
@@ -327,7 +329,7 @@ int launch_q(const StreamArgs &s, const uint16_t *sx, const uint16_t *sy, uint64
         if (occ <= 0) return QEXT_E_CUDA;
         const uint64_t cap = uint64_t(sms) * occ;
         const int grid = int(ta.ntiles < cap ? ta.ntiles : cap);
-        extract_tiled_kernel<Q, B><<<grid, T * TPB, smem, st>>>(ta);
+        return qext::launch_pdl(extract_tiled_kernel<Q, B>, grid, int(T * TPB), smem, st, ta);
     } else {
         if (B != 0) return QEXT_E_UNSUPPORTED;  // fused ingest needs a staged tile
         const int occd = occ_direct.get(dev, [] {
@@ -340,9 +342,8 @@ int launch_q(const StreamArgs &s, const uint16_t *sx, const uint16_t *sy, uint64
         const uint64_t ctas = (s.nblocks + kThreads - 1) / kThreads;
         const uint64_t cap = uint64_t(sms) * occd;
         const int grid = int(ctas < cap ? ctas : cap);
-        extract_direct_kernel<Q><<<grid, kThreads, 0, st>>>(s);
+        return qext::launch_pdl(extract_direct_kernel<Q>, grid, kThreads, 0, st, s);
     }
-    return cudaGetLastError() == cudaSuccess ? QEXT_OK : QEXT_E_CUDA;
 }
 
 }  // namespace

@@ -184,6 +184,7 @@ __global__ void __launch_bounds__(kThreads80, 6) extract_q80_kernel(const Q80Arg
     __shared__ uint32_t stages[kThreads80 / 32][kStageWords];
     uint32_t *const sl = slices + threadIdx.x;
     uint32_t *const stage = stages[threadIdx.x >> 5];
+    pdl_prologue();
     const StreamArgs &s = a.s;
     const uint32_t lane = threadIdx.x & 31u;
     const uint64_t warp = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
@@ -331,8 +332,7 @@ int launch_extract_q80(const qext_plan *p, const uint32_t *x, const uint32_t *y,
     a.zero = 0;
     const uint64_t ctas = (nblocks + kThreads80 - 1) / kThreads80;
     const int grid = int(ctas < uint64_t(grid_cap) ? ctas : uint64_t(grid_cap));
-    extract_q80_kernel<<<grid, kThreads80, 0, reinterpret_cast<cudaStream_t>(stream)>>>(a);
-    return cudaGetLastError() == cudaSuccess ? QEXT_OK : QEXT_E_CUDA;
+    return launch_pdl(extract_q80_kernel, grid, kThreads80, 0, reinterpret_cast<cudaStream_t>(stream), a);
 }
 
 }  // namespace qext

@@ -186,8 +186,10 @@ __global__ void __launch_bounds__(Q == 16 ? 32 * kMaxWarps : 32 * kSmallWarps) e
     __syncwarp();
     pdl_prologue();
 
+    // warp-major numbering: every CTA (one per SM at q = 16) gets the same
+    // number of warps with the extra sub-tile of the last round
     const uint64_t gwarps = uint64_t(gridDim.x) * nwarps;
-    uint64_t t = uint64_t(blockIdx.x) * nwarps + warp;
+    uint64_t t = uint64_t(warp) * gridDim.x + blockIdx.x;
     uint32_t uses0 = 0, uses1 = 0;  // completed phases of full[warp][0], [1]
     bool next_issued = false;       // lane 0: the next sub-tile's copy is in flight
     if (t < a.nsub && lane == 0) {
@@ -331,8 +333,10 @@ __global__ void __launch_bounds__(32 * kMaxWarps) extract_packed16_kernel(const 
     __syncwarp();
     pdl_prologue();
 
+    // warp-major numbering: every CTA (one per SM) gets the same number of
+    // warps with the extra sub-tile of the last round
     const uint64_t gwarps = uint64_t(gridDim.x) * nwarps;
-    uint64_t t = uint64_t(blockIdx.x) * nwarps + warp;
+    uint64_t t = uint64_t(warp) * gridDim.x + blockIdx.x;
     auto issue = [&](uint64_t tt) {
         const uint64_t b0 = 32 * tt;
         const uint32_t nb = s.nblocks - b0 < 32 ? uint32_t(s.nblocks - b0) : 32u;

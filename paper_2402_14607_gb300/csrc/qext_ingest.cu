@@ -5,6 +5,7 @@
 
 #include <cstdint>
 
+#include "qext_device.cuh"
 #include "qext_internal.h"
 
 // Sticky device status (QEXT_OK or a negative QEXT_E_* code) written by
@@ -20,6 +21,7 @@ namespace {
 __global__ void __launch_bounds__(256) pack_kernel(const uint16_t *__restrict__ s, uint64_t nsamples, uint32_t b,
                                                    uint32_t S, uint32_t L, uint32_t *__restrict__ out,
                                                    uint64_t nwords, uint64_t nperiods) {
+    qxd::pdl_prologue();
     const uint32_t mask = b >= 16 ? 0xFFFFu : ((1u << b) - 1u);
     for (uint64_t c = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; c < nperiods;
          c += uint64_t(gridDim.x) * blockDim.x) {
@@ -49,6 +51,7 @@ template <int B>
 __global__ void __launch_bounds__(256) pack_kernel_vec(const uint16_t *__restrict__ s, uint64_t nsamples,
                                                        uint32_t *__restrict__ out, uint64_t nwords,
                                                        uint64_t nperiods) {
+    qxd::pdl_prologue();
     constexpr uint32_t S = B == 8 ? 16 : 8;                 // samples per thread
     constexpr uint32_t L = B == 12 ? 3 : 4;                  // words per thread
     constexpr uint32_t MASK2 = B == 16 ? 0xFFFFFFFFu : B == 12 ? 0x0FFF0FFFu : 0x00FF00FFu;
@@ -134,17 +137,17 @@ int launch_pack(uint32_t b, const uint16_t *samples, uint64_t nsamples, uint32_t
     };
     if (a16 && b == 12) {
         const uint64_t np = (nsamples + 7) / 8;
-        pack_kernel_vec<12><<<grid_for(np), 256, 0, st>>>(samples, nsamples, out, nwords, np);
+        return launch_pdl(pack_kernel_vec<12>, grid_for(np), 256, 0, st, samples, nsamples, out, nwords, np);
     } else if (a16 && o16 && b == 8) {
         const uint64_t np = (nsamples + 15) / 16;
-        pack_kernel_vec<8><<<grid_for(np), 256, 0, st>>>(samples, nsamples, out, nwords, np);
+        return launch_pdl(pack_kernel_vec<8>, grid_for(np), 256, 0, st, samples, nsamples, out, nwords, np);
     } else if (a16 && o16 && b == 16) {
         const uint64_t np = (nsamples + 7) / 8;
-        pack_kernel_vec<16><<<grid_for(np), 256, 0, st>>>(samples, nsamples, out, nwords, np);
+        return launch_pdl(pack_kernel_vec<16>, grid_for(np), 256, 0, st, samples, nsamples, out, nwords, np);
     } else {
-        pack_kernel<<<grid_for(nperiods), 256, 0, st>>>(samples, nsamples, b, S, L, out, nwords, nperiods);
+        return launch_pdl(pack_kernel, grid_for(nperiods), 256, 0, st, samples, nsamples, b, S, L, out, nwords,
+                          nperiods);
     }
-    return cudaGetLastError() == cudaSuccess ? QEXT_OK : QEXT_E_CUDA;
 }
 
 int sm_count(int dev) {

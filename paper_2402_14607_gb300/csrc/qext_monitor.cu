@@ -15,6 +15,7 @@
 #include <cmath>
 #include <cstdint>
 
+#include "qext_device.cuh"
 #include "qext_internal.h"
 
 namespace {
@@ -27,6 +28,7 @@ __global__ void __launch_bounds__(kMonThreads)
     histogram_kernel(const uint16_t *__restrict__ samples, uint64_t nsamples, uint32_t b,
                      unsigned long long *__restrict__ counts, int vec) {
     extern __shared__ uint32_t bins[];
+    qxd::pdl_prologue();
     const uint32_t nbins = 1u << b, mask = nbins - 1u;
     // several copies of the bins (warp w counts into copy w % copies) spread
     // the shared atomics of the few hot values a noise distribution has
@@ -100,11 +102,8 @@ int qext_sample_histogram(uint32_t b, const uint16_t *samples, uint64_t nsamples
     const int grid = int(want < 1 ? 1 : want < uint64_t(cap) ? want : uint64_t(cap));
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     auto *c = reinterpret_cast<unsigned long long *>(counts);
-    if (shared)
-        histogram_kernel<true><<<grid, kMonThreads, smem, st>>>(samples, nsamples, b, c, vec);
-    else
-        histogram_kernel<false><<<grid, kMonThreads, 0, st>>>(samples, nsamples, b, c, vec);
-    return cudaGetLastError() == cudaSuccess ? QEXT_OK : QEXT_E_CUDA;
+    if (shared) return qext::launch_pdl(histogram_kernel<true>, grid, kMonThreads, smem, st, samples, nsamples, b, c, vec);
+    return qext::launch_pdl(histogram_kernel<false>, grid, kMonThreads, 0, st, samples, nsamples, b, c, vec);
 }
 
 double qext_min_entropy_estimate(uint32_t b, const uint64_t *counts_host) {

@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(kStreamThreads) stream_general_kernel(const Ge
         uint64_t v;
         if constexpr (Q == 64) {
             uint64_t A = 0, B = 0, C = 0;
-            half_products64(xs, ys, s.wpb, 0, 0, 0, 1, A, B, C);
+            half_products64(xs, ys, s.wpb, 0, 0, 0, 1, A, B, C, s);
             v = combine_q64(A, B, C, s);
         } else {
             v = block_small_q<Q>(xs, ys, s.wpb, 0, 0, s);

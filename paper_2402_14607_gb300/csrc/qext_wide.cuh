@@ -70,14 +70,18 @@ __device__ __forceinline__ uint64_t gram32_parities_3x16(uint32_t (&X)[32], uint
 }
 
 
-// Parity chain of the diagonals D0 .. D1-1 of sum_b t^(S b) (X_b x Y_b),
-// where X_b = X[O0 + OSTEP b .. + 8) and likewise Y_b: diagonal d takes the
-// pairs j + l = d - S b of block b.  One live accumulator; bit
-// 32 - (D1 - D0) + (d - D0) of the result is the parity of diagonal d.
+// Parities of the diagonals D0 .. D1-1 of sum_b t^(S b) (X_b x Y_b), where
+// X_b = X[O0 + OSTEP b .. + 8) and likewise Y_b: diagonal d takes the pairs
+// j + l = d - S b of block b.  One live accumulator per diagonal; bit d - D0
+// of the result is the parity of diagonal d.  The parities are assembled in
+// byte fields (popcounts of four consecutive diagonals packed by IMADs,
+// w = w + popc * 2^(8f), every field <= 32; the four low bits gathered by
+// ((w & 0x01010101) * 0x01020408) >> 24 and placed by an IMAD), which keeps
+// the assembly on the FMA pipe, off the ALU pipe the products fill.
 template <int NB, int O0, int OSTEP, int S, int D0, int D1>
-__device__ __forceinline__ uint32_t block_chain(const uint32_t *X, const uint32_t *Y) {
+__device__ __forceinline__ uint32_t block_parities(const uint32_t *X, const uint32_t *Y, const StreamArgs &s) {
     static_assert(D1 - D0 >= 1 && D1 - D0 <= 32, "one word of parities");
-    uint32_t c = 0;
+    uint32_t r = 0, w = 0;
 #pragma unroll
     for (int d = D0; d < D1; ++d) {
         uint32_t acc = 0;
@@ -88,9 +92,15 @@ __device__ __forceinline__ uint32_t block_chain(const uint32_t *X, const uint32_
             for (int j = 0; j < 8; ++j)
                 if (k - j >= 0 && k - j < 8) acc = lop_and_xor(X[o + j], Y[o + k - j], acc);
         }
-        c = (c >> 1) + (uint32_t(__popc(acc)) << 31);
+        const int f = (d - D0) & 3;
+        const uint32_t pc = uint32_t(__popc(acc));
+        w = f == 0 ? pc : pc * s.byte_pos[f] + w;
+        if (f == 3 || d == D1 - 1) {
+            const uint32_t nib = ((w & 0x01010101u) * 0x01020408u) >> 24;
+            r = nib * s.nib_mul[(d - D0) >> 2] + r;
+        }
     }
-    return c;
+    return r;
 }
 
 // Parities of the 63 diagonals of a sliced 32 x 32 Gram product by two
@@ -104,9 +114,9 @@ __device__ __forceinline__ uint32_t block_chain(const uint32_t *X, const uint32_
 // the 16 x 16 products of the outer level): 107 diagonal parities instead
 // of 135.  X and Y are overwritten.  Bit d of the result = parity of
 // diagonal d.
-__device__ __forceinline__ uint64_t gram32_parities(uint32_t (&X)[32], uint32_t (&Y)[32]) {
-    const uint64_t E = uint64_t(block_chain<4, 0, 8, 8, 0, 32>(X, Y)) |
-                       (uint64_t(block_chain<4, 0, 8, 8, 32, 39>(X, Y) >> 25) << 32);
+__device__ __forceinline__ uint64_t gram32_parities(uint32_t (&X)[32], uint32_t (&Y)[32], const StreamArgs &s) {
+    const uint64_t E = uint64_t(block_parities<4, 0, 8, 8, 0, 32>(X, Y, s)) |
+                       (uint64_t(block_parities<4, 0, 8, 8, 32, 39>(X, Y, s)) << 32);
     // inner sums of A's and B's halves (words 8.. and 24..)
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
@@ -115,8 +125,8 @@ __device__ __forceinline__ uint64_t gram32_parities(uint32_t (&X)[32], uint32_t 
         X[24 + j] ^= X[16 + j];
         Y[24 + j] ^= Y[16 + j];
     }
-    const uint64_t F = uint64_t(block_chain<1, 8, 0, 0, 0, 15>(X, Y) >> 17) |
-                       (uint64_t(block_chain<1, 24, 0, 0, 0, 15>(X, Y) >> 17) << 16);
+    const uint64_t F = uint64_t(block_parities<1, 8, 0, 0, 0, 15>(X, Y, s)) |
+                       (uint64_t(block_parities<1, 24, 0, 0, 0, 15>(X, Y, s)) << 16);
     // outer sum (words 0..15) and its inner half sum (words 24..31)
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
@@ -127,8 +137,8 @@ __device__ __forceinline__ uint64_t gram32_parities(uint32_t (&X)[32], uint32_t 
         X[8 + j] = X[24 + j] ^ X[j];
         Y[8 + j] = Y[24 + j] ^ Y[j];
     }
-    const uint64_t DC = block_chain<2, 0, 8, 8, 0, 23>(X, Y) >> 9;
-    const uint64_t SC = block_chain<1, 24, 0, 0, 0, 15>(X, Y) >> 17;
+    const uint64_t DC = block_parities<2, 0, 8, 8, 0, 23>(X, Y, s);
+    const uint64_t SC = block_parities<1, 24, 0, 0, 0, 15>(X, Y, s);
     return E ^ ((E ^ F) << 8) ^ ((E ^ DC) << 16) ^ ((E ^ F ^ DC ^ SC) << 24);
 }
 
@@ -145,7 +155,7 @@ __device__ __forceinline__ uint32_t pick64(uint32_t lo, uint32_t hi, uint32_t se
 template <int PART>
 __device__ __forceinline__ uint64_t half_product64(const uint32_t *xs, const uint32_t *ys, uint32_t wpb, int vec,
                                                    uint32_t rot, uint32_t g_first, uint32_t g_step,
-                                                   uint32_t sel = 0x3210u, uint32_t mask = 0) {
+                                                   const StreamArgs &s, uint32_t sel = 0x3210u, uint32_t mask = 0) {
     uint64_t z = 0;  // parities are linear: XOR of the groups' parities
     for (uint32_t g0 = 64 * g_first; g0 < wpb; g0 += 64 * g_step) {
         uint32_t X[32], Y[32];
@@ -175,7 +185,7 @@ __device__ __forceinline__ uint64_t half_product64(const uint32_t *xs, const uin
         }
         slice<32>(X);
         slice<32>(Y);
-        z ^= gram32_parities(X, Y);
+        z ^= gram32_parities(X, Y, s);
     }
     return z;
 }
@@ -184,10 +194,10 @@ __device__ __forceinline__ uint64_t half_product64(const uint32_t *xs, const uin
 // (a run-time loop over the parts).
 __device__ __forceinline__ void half_products64(const uint32_t *xs, const uint32_t *ys, uint32_t wpb, int vec,
                                                 uint32_t rot, uint32_t g_first, uint32_t g_step, uint64_t &A,
-                                                uint64_t &B, uint64_t &C) {
+                                                uint64_t &B, uint64_t &C, const StreamArgs &s) {
 #pragma unroll 1
     for (uint32_t part = 0; part < 3; ++part) {
-        const uint64_t r = half_product64<-1>(xs, ys, wpb, vec, rot, g_first, g_step,
+        const uint64_t r = half_product64<-1>(xs, ys, wpb, vec, rot, g_first, g_step, s,
                                               part == 1 ? 0x7654u : 0x3210u, part == 2 ? ~0u : 0u);
         A = part == 0 ? r : A;
         B = part == 1 ? r : B;
@@ -209,14 +219,14 @@ __device__ __forceinline__ void half_products64(const uint32_t *xs, const uint32
 // a proxy fence after this (the caller's).
 __device__ __forceinline__ void half_products64_inplace(uint32_t *xs, uint32_t *ys, uint32_t wpb, uint32_t rot,
                                                         uint32_t g_first, uint32_t g_step, uint64_t &A, uint64_t &B,
-                                                        uint64_t &C) {
+                                                        uint64_t &C, const StreamArgs &s) {
     A = B = C = 0;
     for (uint32_t g0 = 64 * g_first; g0 < wpb; g0 += 64 * g_step) {
         if (g0 + 64 > wpb) {
             const uint32_t g = g0 / 64, one = wpb;  // a step past the block: this group only
-            A ^= half_product64<0>(xs, ys, wpb, 1, rot, g, one);
-            B ^= half_product64<1>(xs, ys, wpb, 1, rot, g, one);
-            C ^= half_product64<2>(xs, ys, wpb, 1, rot, g, one);
+            A ^= half_product64<0>(xs, ys, wpb, 1, rot, g, one, s);
+            B ^= half_product64<1>(xs, ys, wpb, 1, rot, g, one, s);
+            C ^= half_product64<2>(xs, ys, wpb, 1, rot, g, one, s);
             continue;
         }
 #pragma unroll 1
@@ -265,7 +275,7 @@ __device__ __forceinline__ void half_products64_inplace(uint32_t *xs, uint32_t *
                 Y[4 * k + 2] = vy.z;
                 Y[4 * k + 3] = vy.w;
             }
-            const uint64_t r = gram32_parities(X, Y);
+            const uint64_t r = gram32_parities(X, Y, s);
             A ^= part == 0 ? r : 0;
             B ^= part == 1 ? r : 0;
             C ^= part == 2 ? r : 0;
