@@ -331,6 +331,13 @@ int qext_batch_set_config(qext_batch *b, const qext_batch_config *cfg);
  * every item's output written.  Asynchronous.  Errors: INVAL, CUDA. */
 int qext_batch_run(qext_batch *b, qext_cuda_stream stream);
 
+/* qext_batch_run with flags: 0, or QEXT_F_TEST_TIMEOUT (test of failure
+ * detection: every CTA arms its tile barrier without issuing the bulk copy,
+ * gives up its bounded wait after a few polls, records QEXT_E_TIMEOUT in the
+ * device status word and returns; outputs are not written; every item with
+ * blocks must be 16-byte aligned, else INVAL).  Errors: INVAL, CUDA. */
+int qext_batch_run_ex(qext_batch *b, qext_cuda_stream stream, uint32_t flags);
+
 /* Records one run into a CUDA graph (capture on `stream`, which must not be
  * capturing already); qext_batch_launch replays it.  Errors: STATE (launch
  * before capture), CUDA. */
@@ -358,14 +365,17 @@ int qext_batch_autotune(qext_batch *b, uint32_t reps, qext_cuda_stream stream, f
  *   items, nitems  as for qext_batch_create; at most QEXT_NOALLOC_MAX_ITEMS
  *                  items (else QEXT_E_LIMIT, nothing done).
  * The first call on a device, with that device current, looks up the array's
- * device address and sets the kernel's shared-memory limit; make that first
- * call before any stream capture.  Every call reuses the same array: it is
- * rewritten (counter reset to 0) by each call, so calls whose work overlaps
- * on the GPU -- on different streams, or from different host threads without
- * ordering -- race and give wrong outputs; order them on one stream.  The
- * descriptor copy is staged from host memory before the call returns.
- * Default tile configuration (no autotuning).  Errors: INVAL, UNSUPPORTED,
- * LIMIT, CUDA.
+ * device address and sets the kernel's shared-memory limit.  Every call
+ * reuses the same array: it is rewritten (counter reset to 0) by each call,
+ * so calls whose work overlaps on the GPU -- on different streams, or from
+ * different host threads without ordering -- race and give wrong outputs;
+ * order them on one stream.  The descriptors travel from a static host
+ * buffer that the next call rewrites, staged before cudaMemcpyAsync returns
+ * on an ordinary stream; a stream that is being captured into a CUDA graph
+ * would instead record a copy that reads the buffer at replay time, so such
+ * a stream is refused with STATE before anything is enqueued.  Default tile
+ * configuration (no autotuning).  Errors: INVAL, UNSUPPORTED, LIMIT, STATE,
+ * CUDA.
  */
 #define QEXT_NOALLOC_MAX_ITEMS 1024
 int qext_batch_run_noalloc(const qext_batch_item *items, uint32_t nitems, qext_cuda_stream stream);

@@ -47,17 +47,22 @@ struct BatchTileDev {
     uint64_t first;  // first block
 };
 
+// no_copy (test of failure detection): the barrier is armed but no copy is
+// issued, so the bounded wait gives up.
 __device__ __forceinline__ void load_tile(const StreamArgs &s, uint64_t first, uint32_t nb, int tma, uint32_t *xs,
-                                          uint32_t *ys, uint64_t *bar, uint32_t &uses, bool &ok) {
+                                          uint32_t *ys, uint64_t *bar, uint32_t &uses, bool &ok, uint32_t max_polls,
+                                          int no_copy) {
     const uint32_t words = nb * s.wpb;
     const uint32_t tid = threadIdx.x;
     if (tma && (words % 4u) == 0) {
         if (tid == 0) {
             mbar_expect_tx(bar, 8u * words);
-            tma_load_1d(xs, s.x + first * s.wpb, 4u * words, bar);
-            tma_load_1d(ys, s.y + first * s.wpb, 4u * words, bar);
+            if (!no_copy) {
+                tma_load_1d(xs, s.x + first * s.wpb, 4u * words, bar);
+                tma_load_1d(ys, s.y + first * s.wpb, 4u * words, bar);
+            }
         }
-        ok = mbar_wait_bounded(bar, uses & 1u);
+        ok = mbar_wait_bounded(bar, uses & 1u, max_polls);
         ++uses;
     } else {
         for (uint32_t i = tid; i < words; i += blockDim.x) {
@@ -99,10 +104,11 @@ __device__ __forceinline__ void compute_tile(const StreamArgs &s, uint64_t first
 
 __global__ void __launch_bounds__(kThreads) batch_kernel(const BatchStreamDev *__restrict__ items,
                                                          const BatchTileDev *__restrict__ tiles, uint32_t ntiles,
-                                                         uint32_t *counter) {
+                                                         unsigned long long *counter, uint32_t max_polls,
+                                                         int no_copy) {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ __align__(8) uint64_t bar;
-    __shared__ uint32_t next_tile;
+    __shared__ unsigned long long next_tile;
     __shared__ uint64_t vals[512];
     const uint32_t tid = threadIdx.x;
     if (tid == 0) {
@@ -112,9 +118,9 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(const BatchStreamDev *_
     __syncthreads();
     uint32_t uses = 0;
     for (;;) {
-        if (tid == 0) next_tile = atomicAdd(counter, 1u);
+        if (tid == 0) next_tile = atomicAdd(counter, 1ull);
         __syncthreads();
-        const uint32_t t = next_tile;
+        const uint64_t t = next_tile;
         if (t >= ntiles) return;
         const BatchTileDev tl = tiles[t];
         const BatchStreamDev it = items[tl.item];
@@ -122,11 +128,11 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(const BatchStreamDev *_
         const uint32_t words = tl.nb * s.wpb;
         uint32_t *xs = smem, *ys = smem + words;
         bool ok;
-        load_tile(s, tl.first, tl.nb, it.tma, xs, ys, &bar, uses, ok);
+        load_tile(s, tl.first, tl.nb, it.tma, xs, ys, &bar, uses, ok, max_polls, no_copy);
         if (!__syncthreads_and(ok)) {
             if (tid == 0) {
                 record_status(s.status, QEXT_E_TIMEOUT);
-                mbar_wait_bounded(&bar, (uses - 1) & 1u);
+                if (!no_copy) mbar_wait_bounded(&bar, (uses - 1) & 1u, max_polls);  // let the copy in flight land
             }
             return;
         }
@@ -164,7 +170,7 @@ struct qext_batch {
     qext_batch_config cfg;
     BatchStreamDev *d_items = nullptr;
     BatchTileDev *d_tiles = nullptr;
-    uint32_t *d_counter = nullptr;
+    unsigned long long *d_counter = nullptr;  // 64-bit: every CTA takes one index past the last tile
     uint32_t ntiles = 0;
     size_t tiles_cap = 0;
     int sms = 0;
@@ -227,12 +233,14 @@ int build_tiles(qext_batch *b) {
     return QEXT_OK;
 }
 
-int enqueue(qext_batch *b, cudaStream_t st) {
-    if (cudaMemsetAsync(b->d_counter, 0, sizeof(uint32_t), st) != cudaSuccess) return QEXT_E_CUDA;
+int enqueue(qext_batch *b, cudaStream_t st, uint32_t flags = 0) {
+    if (cudaMemsetAsync(b->d_counter, 0, sizeof(*b->d_counter), st) != cudaSuccess) return QEXT_E_CUDA;
     if (!b->ntiles) return QEXT_OK;
     const uint64_t cap = uint64_t(b->sms) * b->cfg.ctas_per_sm;
     const int grid = int(std::min<uint64_t>(cap, b->ntiles));
-    batch_kernel<<<grid, kThreads, kSmemBytes, st>>>(b->d_items, b->d_tiles, b->ntiles, b->d_counter);
+    const int no_copy = (flags & QEXT_F_TEST_TIMEOUT) ? 1 : 0;
+    batch_kernel<<<grid, kThreads, kSmemBytes, st>>>(b->d_items, b->d_tiles, b->ntiles, b->d_counter,
+                                                     no_copy ? 256u : kMaxPolls, no_copy);
     return cudaGetLastError() == cudaSuccess ? QEXT_OK : QEXT_E_CUDA;
 }
 
@@ -301,7 +309,7 @@ int qext_batch_create(const qext_batch_item *items, uint32_t nitems, qext_batch 
         d.tma = al % 16 == 0;
         b->items.push_back(d);
     }
-    if (cudaMalloc(&b->d_counter, sizeof(uint32_t)) != cudaSuccess ||
+    if (cudaMalloc(&b->d_counter, sizeof(*b->d_counter)) != cudaSuccess ||
         (nitems && cudaMalloc(&b->d_items, sizeof(BatchStreamDev) * nitems) != cudaSuccess)) {
         qext_batch_destroy(b);
         return QEXT_E_CUDA;
@@ -352,9 +360,17 @@ int qext_batch_set_config(qext_batch *b, const qext_batch_config *cfg) {
     return build_tiles(b);
 }
 
-int qext_batch_run(qext_batch *b, qext_cuda_stream stream) {
+int qext_batch_run(qext_batch *b, qext_cuda_stream stream) { return qext_batch_run_ex(b, stream, 0); }
+
+int qext_batch_run_ex(qext_batch *b, qext_cuda_stream stream, uint32_t flags) {
     if (!b) return QEXT_E_INVAL;
-    return enqueue(b, reinterpret_cast<cudaStream_t>(stream));
+    if (flags & ~uint32_t(QEXT_F_TEST_TIMEOUT)) return QEXT_E_INVAL;
+    if (flags) {
+        // the test needs every tile on the bulk-copy path
+        for (const BatchStreamDev &d : b->items)
+            if (d.s.nblocks && !d.tma) return QEXT_E_INVAL;
+    }
+    return enqueue(b, reinterpret_cast<cudaStream_t>(stream), flags);
 }
 
 int qext_batch_capture(qext_batch *b, qext_cuda_stream stream) {
@@ -433,7 +449,7 @@ done:
 namespace {
 
 struct NoallocScratch {
-    uint32_t counter;  // next tile; 0 at the start of every call
+    unsigned long long counter;  // next tile; 0 at the start of every call (64-bit: cannot wrap)
     uint32_t nitems;
     uint64_t total_tiles;
     uint64_t tile_prefix[QEXT_NOALLOC_MAX_ITEMS + 1];  // tiles of the items before item i
@@ -448,7 +464,7 @@ static __device__ __align__(256) unsigned char qext_noalloc_scratch[sizeof(Noall
 __global__ void __launch_bounds__(kThreads) batch_noalloc_kernel(NoallocScratch *sc) {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ __align__(8) uint64_t bar;
-    __shared__ uint32_t next_tile;
+    __shared__ unsigned long long next_tile;
     __shared__ uint64_t vals[512];
     const uint32_t tid = threadIdx.x;
     if (tid == 0) {
@@ -458,7 +474,7 @@ __global__ void __launch_bounds__(kThreads) batch_noalloc_kernel(NoallocScratch 
     __syncthreads();
     uint32_t uses = 0;
     for (;;) {
-        if (tid == 0) next_tile = atomicAdd(&sc->counter, 1u);
+        if (tid == 0) next_tile = atomicAdd(&sc->counter, 1ull);
         __syncthreads();
         const uint64_t t = next_tile;
         if (t >= sc->total_tiles) return;
@@ -478,7 +494,7 @@ __global__ void __launch_bounds__(kThreads) batch_noalloc_kernel(NoallocScratch 
         const uint32_t words = nb * s.wpb;
         uint32_t *xs = smem, *ys = smem + words;
         bool ok;
-        load_tile(s, first, nb, it.tma, xs, ys, &bar, uses, ok);
+        load_tile(s, first, nb, it.tma, xs, ys, &bar, uses, ok, kMaxPolls, 0);
         if (!__syncthreads_and(ok)) {
             if (tid == 0) {
                 record_status(s.status, QEXT_E_TIMEOUT);
@@ -504,43 +520,22 @@ __global__ void __launch_bounds__(kThreads) batch_noalloc_kernel(NoallocScratch 
     }
 }
 
-constexpr int kNoallocMaxDevices = 64;
-std::mutex g_noalloc_mu;
-void *g_noalloc_dev[kNoallocMaxDevices];                 // device address of the scratch, per device
-unsigned char g_noalloc_stage[sizeof(NoallocScratch)];  // host staging (static: no heap)
-
-}  // namespace
-
-extern "C" int qext_batch_run_noalloc(const qext_batch_item *items, uint32_t nitems, qext_cuda_stream stream) {
+// Validates the items and fills the descriptor table h (header, per-item
+// descriptors in the given order, tile prefix sums), as both table entry
+// points need it: every item has a plan with GPU kernels, non-null 4-byte
+// aligned pointers (when it has blocks) and a tile that fits the kernel's
+// shared memory; at most QEXT_NOALLOC_MAX_ITEMS items and 2^32 - 1 tiles.
+// order == nullptr keeps the caller's order.
+int fill_table(const qext_batch_item *items, uint32_t nitems, const uint32_t *order, NoallocScratch *h) {
     if (nitems > QEXT_NOALLOC_MAX_ITEMS) return QEXT_E_LIMIT;
     if (nitems && !items) return QEXT_E_INVAL;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return QEXT_E_CUDA;
-    if (dev < 0 || dev >= kNoallocMaxDevices) return QEXT_E_LIMIT;
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    // one-time set-up on this device (the first call, with the device current)
-    if (!g_noalloc_dev[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, qext_noalloc_scratch) != cudaSuccess || !p) return QEXT_E_CUDA;
-        if (cudaFuncSetAttribute(batch_noalloc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) !=
-            cudaSuccess)
-            return QEXT_E_CUDA;
-        g_noalloc_dev[dev] = p;
-    }
-    NoallocScratch *h = reinterpret_cast<NoallocScratch *>(g_noalloc_stage);
     h->counter = 0;
     h->nitems = nitems;
-    for (uint32_t i = 0; i < nitems; ++i)
-        if (!items[i].plan) return QEXT_E_INVAL;
-    // heavier streams first, so their tiles are taken first
-    uint32_t order[QEXT_NOALLOC_MAX_ITEMS];
-    for (uint32_t i = 0; i < nitems; ++i) order[i] = i;
-    std::stable_sort(order, order + nitems,
-                     [&](uint32_t a, uint32_t c) { return items[a].plan->q > items[c].plan->q; });
-    qext_batch_config cfg{4, 1, 3, 0};
+    const qext_batch_config cfg{4, 1, 3, 0};
     uint64_t tiles = 0;
     for (uint32_t k = 0; k < nitems; ++k) {
-        const qext_batch_item &it = items[order[k]];
+        const qext_batch_item &it = items[order ? order[k] : k];
+        if (!it.plan) return QEXT_E_INVAL;
         if (!it.plan->gpu_supported) return QEXT_E_UNSUPPORTED;
         const uintptr_t al = reinterpret_cast<uintptr_t>(it.x) | reinterpret_cast<uintptr_t>(it.y);
         if (it.nblocks && (!it.x || !it.y || !it.out || al % 4 || reinterpret_cast<uintptr_t>(it.out) % 4))
@@ -554,9 +549,7 @@ extern "C" int qext_batch_run_noalloc(const qext_batch_item *items, uint32_t nit
         d.s.wpb = it.plan->n / 32;
         d.s.m = it.plan->m;
         d.s.ntaps = it.plan->ntaps;
-        for (int j = 0; j < 4; ++j) {
-            d.s.taps[j] = it.plan->taps[j];
-        }
+        for (int j = 0; j < 4; ++j) d.s.taps[j] = it.plan->taps[j];
         d.s.set_multipliers();
         d.s.status = qext::device_status_ptr();
         d.q = it.plan->q;
@@ -570,16 +563,59 @@ extern "C" int qext_batch_run_noalloc(const qext_batch_item *items, uint32_t nit
     if (tiles > 0xFFFFFFFFull) return QEXT_E_LIMIT;
     h->tile_prefix[nitems] = tiles;
     h->total_tiles = tiles;
+    return QEXT_OK;
+}
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_dev[kNoallocMaxDevices];                 // device address of the scratch, per device
+unsigned char g_noalloc_stage[sizeof(NoallocScratch)];  // host staging (static: no heap)
+
+}  // namespace
+
+extern "C" int qext_batch_run_noalloc(const qext_batch_item *items, uint32_t nitems, qext_cuda_stream stream) {
+    if (nitems > QEXT_NOALLOC_MAX_ITEMS) return QEXT_E_LIMIT;
+    if (nitems && !items) return QEXT_E_INVAL;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    // The descriptors are copied from a static host buffer that the next call
+    // rewrites; a captured copy would read that buffer at replay time, so a
+    // capturing stream is refused before anything is enqueued.
+    cudaStreamCaptureStatus cap_status = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap_status) != cudaSuccess) return QEXT_E_CUDA;
+    if (cap_status != cudaStreamCaptureStatusNone) return QEXT_E_STATE;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return QEXT_E_CUDA;
+    if (dev < 0 || dev >= kNoallocMaxDevices) return QEXT_E_LIMIT;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    // one-time set-up on this device (the first call, with the device current)
+    if (!g_noalloc_dev[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, qext_noalloc_scratch) != cudaSuccess || !p) return QEXT_E_CUDA;
+        if (cudaFuncSetAttribute(batch_noalloc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) !=
+            cudaSuccess)
+            return QEXT_E_CUDA;
+        g_noalloc_dev[dev] = p;
+    }
+    for (uint32_t i = 0; i < nitems; ++i)
+        if (!items[i].plan) return QEXT_E_INVAL;
+    // heavier streams first, so their tiles are taken first
+    uint32_t order[QEXT_NOALLOC_MAX_ITEMS];
+    for (uint32_t i = 0; i < nitems; ++i) order[i] = i;
+    std::stable_sort(order, order + nitems,
+                     [&](uint32_t a, uint32_t c) { return items[a].plan->q > items[c].plan->q; });
+    NoallocScratch *h = reinterpret_cast<NoallocScratch *>(g_noalloc_stage);
+    const int rc = fill_table(items, nitems, order, h);
+    if (rc != QEXT_OK) return rc;
     // the whole header plus the used part of the item table; the copy from
     // pageable host memory is staged before cudaMemcpyAsync returns
     const size_t bytes = offsetof(NoallocScratch, items) + sizeof(BatchStreamDev) * nitems;
     if (cudaMemcpyAsync(g_noalloc_dev[dev], g_noalloc_stage, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
         return QEXT_E_CUDA;
+    const uint64_t tiles = h->total_tiles;
     if (!tiles) return QEXT_OK;
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return QEXT_E_CUDA;
-    const uint64_t cap = uint64_t(sms) * cfg.ctas_per_sm;
+    const uint64_t cap = uint64_t(sms) * 3;
     const int grid = int(tiles < cap ? tiles : cap);
     batch_noalloc_kernel<<<grid, kThreads, kSmemBytes, st>>>(static_cast<NoallocScratch *>(g_noalloc_dev[dev]));
     return cudaGetLastError() == cudaSuccess ? QEXT_OK : QEXT_E_CUDA;
@@ -598,7 +634,6 @@ size_t batch_table_bytes() { return sizeof(NoallocScratch); }
 
 int batch_launch_tables(const qext_batch_item *items, uint32_t nitems, void *d_table, void *h_stage,
                         qext_cuda_stream stream) {
-    if (nitems > QEXT_NOALLOC_MAX_ITEMS) return QEXT_E_LIMIT;
     static qext::DeviceSlots attr_set;
     const int dev = qext::current_device();
     if (dev < 0 || attr_set.get(dev, [] {
@@ -606,44 +641,18 @@ int batch_launch_tables(const qext_batch_item *items, uint32_t nitems, void *d_t
                                         kSmemBytes) == cudaSuccess ? 1 : 0;
         }) <= 0)
         return QEXT_E_CUDA;
+    if (!d_table || !h_stage) return QEXT_E_INVAL;
     NoallocScratch *h = static_cast<NoallocScratch *>(h_stage);
-    h->counter = 0;
-    h->nitems = nitems;
-    const qext_batch_config cfg{4, 1, 3, 0};
-    uint64_t tiles = 0;
-    for (uint32_t k = 0; k < nitems; ++k) {
-        const qext_batch_item &it = items[k];
-        BatchStreamDev &d = h->items[k];
-        std::memset(&d, 0, sizeof d);
-        d.s.x = it.x;
-        d.s.y = it.y;
-        d.s.out = it.out;
-        d.s.nblocks = it.nblocks;
-        d.s.wpb = it.plan->n / 32;
-        d.s.m = it.plan->m;
-        d.s.ntaps = it.plan->ntaps;
-        for (int j = 0; j < 4; ++j) {
-            d.s.taps[j] = it.plan->taps[j];
-        }
-        d.s.set_multipliers();
-        d.s.status = qext::device_status_ptr();
-        d.q = it.plan->q;
-        d.tma = ((reinterpret_cast<uintptr_t>(it.x) | reinterpret_cast<uintptr_t>(it.y)) % 16) == 0;
-        const uint32_t T = tile_blocks(cfg, d.q, d.s.wpb);
-        if (uint64_t(T) * d.s.wpb * 8 > uint64_t(kSmemBytes)) return QEXT_E_UNSUPPORTED;
-        h->tile_blocks[k] = T;
-        h->tile_prefix[k] = tiles;
-        tiles += (it.nblocks + T - 1) / T;
-    }
-    h->tile_prefix[nitems] = tiles;
-    h->total_tiles = tiles;
+    const int rc = fill_table(items, nitems, nullptr, h);
+    if (rc != QEXT_OK) return rc;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const size_t bytes = offsetof(NoallocScratch, items) + sizeof(BatchStreamDev) * nitems;
     if (cudaMemcpyAsync(d_table, h_stage, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return QEXT_E_CUDA;
+    const uint64_t tiles = h->total_tiles;
     if (!tiles) return QEXT_OK;
     const int sms = qext::sm_count(dev);
     if (sms <= 0) return QEXT_E_CUDA;
-    const uint64_t cap = uint64_t(sms) * cfg.ctas_per_sm;
+    const uint64_t cap = uint64_t(sms) * 3;
     const int grid = int(tiles < cap ? tiles : cap);
     batch_noalloc_kernel<<<grid, kThreads, kSmemBytes, st>>>(static_cast<NoallocScratch *>(d_table));
     return cudaGetLastError() == cudaSuccess ? QEXT_OK : QEXT_E_CUDA;

@@ -107,6 +107,7 @@ def lib():
     L.qext_batch_get_config.argtypes = [vp, P(BatchConfig), P(u32)]
     L.qext_batch_set_config.argtypes = [vp, P(BatchConfig)]
     L.qext_batch_run.argtypes = [vp, vp]
+    L.qext_batch_run_ex.argtypes = [vp, vp, u32]
     L.qext_batch_capture.argtypes = [vp, vp]
     L.qext_batch_launch.argtypes = [vp, vp]
     L.qext_batch_autotune.argtypes = [vp, u32, vp, P(ctypes.c_float)]
@@ -135,7 +136,7 @@ def lib():
                  "qext_pack_samples", "qext_device_status", "qext_stream_create", "qext_stream_destroy",
                  "qext_stream_info", "qext_stream_push", "qext_stream_flush", "qext_stream_save",
                  "qext_stream_restore", "qext_batch_create", "qext_batch_destroy", "qext_batch_get_config",
-                 "qext_batch_set_config", "qext_batch_run", "qext_batch_capture", "qext_batch_launch",
+                 "qext_batch_set_config", "qext_batch_run", "qext_batch_run_ex", "qext_batch_capture", "qext_batch_launch",
                  "qext_batch_autotune", "qext_batch_run_noalloc", "qext_server_create", "qext_server_destroy",
                  "qext_server_add_channel", "qext_server_submit", "qext_server_poll", "qext_server_drain",
                  "qext_server_get_stats", "qext_pipeline_create", "qext_pipeline_info", "qext_pipeline_destroy",
@@ -368,6 +369,10 @@ def qext_batch_set_config(b: Batch, blocks_per_thread_small=4, blocks_per_thread
 
 def qext_batch_run(b: Batch, stream=None) -> None:
     _check(lib().qext_batch_run(b.handle, _stream(stream)), "qext_batch_run")
+
+
+def qext_batch_run_ex(b: Batch, stream=None, flags: int = 0) -> None:
+    _check(lib().qext_batch_run_ex(b.handle, _stream(stream), flags), "qext_batch_run_ex")
 
 
 def qext_batch_capture(b: Batch, stream=None) -> None:

@@ -165,3 +165,31 @@ def test_batched_adc_workload_scaled():
             zz = int(z[0]) | (int(z[1]) << 32 if z.size > 1 else 0)
             assert bits_at(got, l * info["m"], info["m"]) == zz
     b.close()
+
+
+def test_batched_bounded_wait_times_out_and_context_survives():
+    """Failure detection in the batched kernel without a fault: each CTA arms
+    its tile barrier but no bulk copy is issued, so its bounded wait runs out;
+    the kernel records QEXT_E_TIMEOUT and returns, the host reads (and clears)
+    the status, and the next run on the same context is correct."""
+    specs = [(16, 64, 16, 2000, 0), (64, 64, 64, 300, 0), (4, 64, 4, 5000, 0)]
+    items, hosts = make_items(specs, 41)
+    b = qext.qext_batch_create(items)
+    assert qext.qext_device_status() == qext.QEXT_OK
+    qext.qext_batch_run_ex(b, None, qext.QEXT_F_TEST_TIMEOUT)
+    torch.cuda.synchronize()
+    assert qext.qext_device_status() == qext.QEXT_E_TIMEOUT
+    assert qext.qext_device_status() == qext.QEXT_OK          # read clears it
+    qext.qext_batch_run(b)
+    torch.cuda.synchronize()
+    for it, want in zip(items, expected(hosts)):
+        assert (host_words(it[4])[:want.size] == want).all()
+    assert qext.qext_device_status() == qext.QEXT_OK
+    # the test mode needs every stream on the bulk-copy path
+    mis, _ = make_items([(16, 64, 16, 100, 1)], 42)
+    b2 = qext.qext_batch_create(mis)
+    with pytest.raises(qext.QextError) as e:
+        qext.qext_batch_run_ex(b2, None, qext.QEXT_F_TEST_TIMEOUT)
+    assert e.value.code == qext.QEXT_E_INVAL
+    b2.close()
+    b.close()
