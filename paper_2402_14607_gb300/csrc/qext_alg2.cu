@@ -27,6 +27,7 @@
 #include "qext_block.cuh"
 #include "qext_wide.cuh"
 #include "qext_internal.h"
+#include "qext_nvtx.h"
 
 using namespace qxd;
 
@@ -222,6 +223,7 @@ int qext_alg2_extract(const qext_alg2_plan *p, const uint16_t *x, const uint16_t
                       qext_cuda_stream stream) {
     if (!p || nblocks > p->max_blocks) return QEXT_E_INVAL;
     if (nblocks == 0) return QEXT_OK;
+    const qext::NvtxRange range("qext algorithm 2 extract");
     if (!x || !y || !out || reinterpret_cast<uintptr_t>(x) % 2 || reinterpret_cast<uintptr_t>(y) % 2 ||
         reinterpret_cast<uintptr_t>(out) % 2)
         return QEXT_E_INVAL;

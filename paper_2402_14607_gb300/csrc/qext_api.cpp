@@ -4,6 +4,7 @@
 #include <cstdint>
 
 #include "qext_internal.h"
+#include "qext_nvtx.h"
 
 namespace {
 bool aligned(const void *p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
@@ -21,6 +22,7 @@ int qext_extract_ex(const qext_plan *p, const uint32_t *x, const uint32_t *y, ui
     if (nblocks == 0) return QEXT_OK;
     if (!x || !y || !out || !aligned(x, 4) || !aligned(y, 4) || !aligned(out, 4)) return QEXT_E_INVAL;
     if (nblocks > (UINT64_MAX / p->n)) return QEXT_E_INVAL;
+    const qext::NvtxRange range("qext extract");
     if (p->gpu_q80) return qext::launch_extract_q80(p, x, y, nblocks, out, stream);
     return qext::launch_extract(p, x, y, nblocks, out, stream, flags);
 }
@@ -51,6 +53,7 @@ int qext_extract_samples_ex(const qext_plan *p, uint32_t b, const uint16_t *x_sa
     if (nsamples > UINT64_MAX / 16 || nblocks > (nsamples * b) / p->n) return QEXT_E_INVAL;
     if (!x_samples || !y_samples || !out || !aligned(x_samples, 16) || !aligned(y_samples, 16) || !aligned(out, 4))
         return QEXT_E_INVAL;
+    const qext::NvtxRange range("qext ingest+extract (fused)");
     if (p->gpu_q80)  // 16-bit samples are the packed stream (sample s = bits [16s, 16s + 16))
         return qext::launch_extract_q80(p, reinterpret_cast<const uint32_t *>(x_samples),
                                         reinterpret_cast<const uint32_t *>(y_samples), nblocks, out, stream);
@@ -62,6 +65,7 @@ int qext_pack_samples(uint32_t b, const uint16_t *samples, uint64_t nsamples, ui
     if (b < 1 || b > 16) return QEXT_E_INVAL;
     if (nsamples == 0) return QEXT_OK;
     if (!samples || !out || !aligned(samples, 2) || !aligned(out, 4)) return QEXT_E_INVAL;
+    const qext::NvtxRange range("qext ingest (pack)");
     return qext::launch_pack(b, samples, nsamples, out, stream);
 }
 

@@ -27,6 +27,7 @@
 #include "qext_block.cuh"
 #include "qext_wide.cuh"
 #include "qext_internal.h"
+#include "qext_nvtx.h"
 
 using namespace qxd;
 
@@ -370,6 +371,7 @@ int qext_batch_run_ex(qext_batch *b, qext_cuda_stream stream, uint32_t flags) {
         for (const BatchStreamDev &d : b->items)
             if (d.s.nblocks && !d.tma) return QEXT_E_INVAL;
     }
+    const qext::NvtxRange range("qext batch run");
     return enqueue(b, reinterpret_cast<cudaStream_t>(stream), flags);
 }
 
@@ -396,6 +398,7 @@ int qext_batch_capture(qext_batch *b, qext_cuda_stream stream) {
 int qext_batch_launch(qext_batch *b, qext_cuda_stream stream) {
     if (!b) return QEXT_E_INVAL;
     if (!b->graph) return QEXT_E_STATE;
+    const qext::NvtxRange range("qext batch (graph launch)");
     return cudaGraphLaunch(b->graph, reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess ? QEXT_OK : QEXT_E_CUDA;
 }
 

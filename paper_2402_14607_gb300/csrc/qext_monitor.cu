@@ -17,6 +17,7 @@
 
 #include "qext_device.cuh"
 #include "qext_internal.h"
+#include "qext_nvtx.h"
 
 namespace {
 
@@ -82,6 +83,7 @@ int qext_sample_histogram(uint32_t b, const uint16_t *samples, uint64_t nsamples
     if (nsamples == 0) return QEXT_OK;
     if (!samples || !counts || reinterpret_cast<uintptr_t>(samples) % 2 || reinterpret_cast<uintptr_t>(counts) % 8)
         return QEXT_E_INVAL;
+    const qext::NvtxRange range("qext min-entropy histogram");
     static qext::DeviceSlots grid_caps[2];
     const int dev = qext::current_device();
     if (dev < 0) return QEXT_E_CUDA;

@@ -9,6 +9,7 @@
 #include <new>
 
 #include "qext_internal.h"
+#include "qext_nvtx.h"
 
 struct qext_pipeline {
     const qext_plan *plan;
@@ -110,6 +111,7 @@ int qext_pipeline_run(qext_pipeline *pp, const void *x_host, const void *y_host,
     const uint64_t have_bits = pp->b ? count * pp->b : count;
     if (nblocks > have_bits / p->n) return QEXT_E_INVAL;
     if (nblocks == 0) return QEXT_OK;
+    const qext::NvtxRange range("qext pipeline run");
     const uint8_t *hx = static_cast<const uint8_t *>(x_host), *hy = static_cast<const uint8_t *>(y_host);
     const uint64_t nchunks = (nblocks + pp->chunk_blocks - 1) / pp->chunk_blocks;
     for (uint64_t c = 0; c < nchunks; ++c) {
@@ -130,10 +132,13 @@ int qext_pipeline_run(qext_pipeline *pp, const void *x_host, const void *y_host,
         }
         // buffer k is free once chunk c-2's kernel has read it
         if (c >= 2 && cudaStreamWaitEvent(pp->s_in, pp->computed[k], 0) != cudaSuccess) return QEXT_E_CUDA;
-        if (cudaMemcpyAsync(pp->in[k][0], hx + off, bytes, cudaMemcpyHostToDevice, pp->s_in) != cudaSuccess ||
-            cudaMemcpyAsync(pp->in[k][1], hy + off, bytes, cudaMemcpyHostToDevice, pp->s_in) != cudaSuccess ||
-            cudaEventRecord(pp->copied[k], pp->s_in) != cudaSuccess)
-            return QEXT_E_CUDA;
+        {
+            const qext::NvtxRange copy_in("qext copy host->device");
+            if (cudaMemcpyAsync(pp->in[k][0], hx + off, bytes, cudaMemcpyHostToDevice, pp->s_in) != cudaSuccess ||
+                cudaMemcpyAsync(pp->in[k][1], hy + off, bytes, cudaMemcpyHostToDevice, pp->s_in) != cudaSuccess ||
+                cudaEventRecord(pp->copied[k], pp->s_in) != cudaSuccess)
+                return QEXT_E_CUDA;
+        }
         // the output buffer k is free once chunk c-2's output was copied out
         if (cudaStreamWaitEvent(pp->s_comp, pp->copied[k], 0) != cudaSuccess) return QEXT_E_CUDA;
         if (c >= 2 && cudaStreamWaitEvent(pp->s_comp, pp->drained[k], 0) != cudaSuccess) return QEXT_E_CUDA;
@@ -148,6 +153,7 @@ int qext_pipeline_run(qext_pipeline *pp, const void *x_host, const void *y_host,
         if (rc != QEXT_OK) return rc;
         if (cudaEventRecord(pp->computed[k], pp->s_comp) != cudaSuccess) return QEXT_E_CUDA;
         const uint64_t ow = (nb * p->m + 31) / 32;
+        const qext::NvtxRange copy_out("qext copy device->host");
         if (cudaStreamWaitEvent(pp->s_out, pp->computed[k], 0) != cudaSuccess ||
             cudaMemcpyAsync(out_host + b0 * p->m / 32, pp->out[k], ow * 4, cudaMemcpyDeviceToHost, pp->s_out) !=
                 cudaSuccess ||

@@ -40,6 +40,7 @@
 #include <vector>
 
 #include "qext_internal.h"
+#include "qext_nvtx.h"
 
 namespace {
 
@@ -303,6 +304,7 @@ void launch_round(qext_server *S) {
         if (rc != QEXT_OK) r->status = rc;
     }
     if (!items.empty()) {
+        const qext::NvtxRange range("qext serving round (batched launch)");
         const int st = S->next_stage;
         S->next_stage ^= 1;
         cudaEventSynchronize(S->stage_free[st]);  // the staging copy of two rounds ago

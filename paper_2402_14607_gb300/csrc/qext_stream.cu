@@ -24,6 +24,7 @@
 #include "qext_block.cuh"
 #include "qext_wide.cuh"
 #include "qext_internal.h"
+#include "qext_nvtx.h"
 
 using namespace qxd;
 
@@ -216,6 +217,7 @@ int qext_stream_push(qext_stream *s, const uint32_t *x, const uint32_t *y, uint6
     *out_words = 0;
     if (nbits == 0) return QEXT_OK;
     if (!x || !y || !aligned4(x) || !aligned4(y)) return QEXT_E_INVAL;
+    const qext::NvtxRange range("qext stream push");
     const uint64_t t = s->tail_bits, p = s->pending_bits, n = s->n, m = s->m;
     if (nbits > UINT64_MAX - t) return QEXT_E_INVAL;
     const uint64_t V = t + nbits;
