@@ -189,67 +189,104 @@ def run_reference(args):
 # Batched and serving measurements (GPU)
 # ---------------------------------------------------------------------------
 def measure_batched(args, dev):
-    """64 stream pairs (block counts 2^U, U ~ U(12, 20); n over {256, 1024,
-    4096}), uniformly random packed words generated on the device: one
-    autotuned batched launch replayed from a CUDA graph, against the plain
-    single-stream path (one qext_extract per stream) on the same data."""
+    """64 stream pairs of 8- and 12-bit ADC samples (block counts 2^U,
+    U ~ U(12, 20); n over {256, 1024, 4096}; seeded quantised Gaussian noise
+    drawn on the device).  One CUDA graph holds the ingest of every stream
+    (qext_pack_samples, 128 launches) and the batched extraction (memset +
+    ONE persistent kernel, tiles from the autotuner); it is replayed and timed
+    against the plain per-stream path on the same data (one fused
+    qext_extract_samples per stream), and against the batched extraction
+    alone on the packed words (the batch's own graph)."""
     import torch
 
     from paper_2402_14607_gb300 import qext, workloads
     specs = workloads.config_batched()
-    plans, items = {}, []
-    gen = torch.Generator(device=dev)
-    gen.manual_seed(3)
-    total_in = total_out_bits = 0
+    plans, items, raw = {}, [], []
+    total_raw = total_packed = total_out_bits = 0
     for sp in specs:
         key = (sp.n, sp.k, sp.eps)
         if key not in plans:
             plans[key] = qext.qext_plan_create(sp.n, 0, sp.k, sp.eps)
         plan = plans[key]
-        words = sp.nblocks * sp.n // 32
-        x = torch.randint(-2 ** 31, 2 ** 31 - 1, (words,), dtype=torch.int32, device=dev, generator=gen)
-        y = torch.randint(-2 ** 31, 2 ** 31 - 1, (words,), dtype=torch.int32, device=dev, generator=gen)
+        ns = -(-sp.nblocks * sp.n // sp.b)
+        sx = workloads.adc_samples_device(sp.seed_x, ns, sp.b, dev)
+        sy = workloads.adc_samples_device(sp.seed_y, ns, sp.b, dev)
+        words = -(-ns * sp.b // 32)
+        px = torch.empty(words, dtype=torch.int32, device=dev)
+        py = torch.empty(words, dtype=torch.int32, device=dev)
         out = torch.empty(-(-sp.nblocks * plan.info["m"] // 32), dtype=torch.int32, device=dev)
-        items.append((plan, x, y, sp.nblocks, out))
-        total_in += 2 * words * 4
+        items.append((plan, px, py, sp.nblocks, out))
+        raw.append((sp.b, sx, sy, ns))
+        total_raw += 2 * ns * 2
+        total_packed += 2 * sp.nblocks * sp.n // 8
         total_out_bits += sp.nblocks * plan.info["m"]
     stream = torch.cuda.Stream(device=dev)
+    sh = int(stream.cuda_stream)
+
+    def ingest():
+        for (b_, sx, sy, ns), (_, px, py, _, _) in zip(raw, items):
+            qext.qext_pack_samples(b_, sx, ns, px, sh)
+            qext.qext_pack_samples(b_, sy, ns, py, sh)
+
+    ingest()
     b = qext.qext_batch_create(items)
     tuned_ms = qext.qext_batch_autotune(b, 2, stream)
     cfg = qext.qext_batch_get_config(b)
-    qext.qext_batch_capture(b, stream)
     reps = max(3, min(args.steps, 20))
-    for _ in range(2):
-        qext.qext_batch_launch(b, stream)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(reps):
-        qext.qext_batch_launch(b, stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    t_batch = e0.elapsed_time(e1) * 1e-3 / reps
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def timed(fn):
+        fn()
+        fn()
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) * 1e-3 / reps
+
+    # ingest + batched extraction in one graph
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        ingest()
+        qext.qext_batch_run(b, sh)
+
+    def replay():
+        with torch.cuda.stream(stream):
+            graph.replay()
+
+    t_graph = timed(replay)
     ref = [it[4].clone() for it in items]
-    # plain single-stream path on the same streams
-    sh = int(stream.cuda_stream)
-    for plan, x, y, nb, out in items:
-        qext.qext_extract(plan, x, y, nb, out, sh)
-    e0.record(stream)
-    for _ in range(reps):
-        for plan, x, y, nb, out in items:
-            qext.qext_extract(plan, x, y, nb, out, sh)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    t_plain = e0.elapsed_time(e1) * 1e-3 / reps
-    same = all(torch.equal(r, it[4]) for r, it in zip(ref, items))
+    # the batched extraction alone (packed words resident), its own graph
+    qext.qext_batch_capture(b, stream)
+    t_extract = timed(lambda: qext.qext_batch_launch(b, stream))
+    same_extract = all(torch.equal(r, it[4]) for r, it in zip(ref, items))
+    # plain path on the same raw data: one fused ingest + extraction per stream
+
+    def plain():
+        for (b_, sx, sy, ns), (plan, _, _, nb, out) in zip(raw, items):
+            qext.qext_extract_samples(plan, b_, sx, sy, ns, nb, out, sh)
+
+    t_plain = timed(plain)
+    same_plain = all(torch.equal(r, it[4]) for r, it in zip(ref, items))
     b.close()
-    return {"workload": "64 stream pairs, 2^U blocks (U~U(12,20)), n in {256,1024,4096}, random words on device",
-            "streams": len(items), "input_bytes": total_in, "extracted_bits": total_out_bits,
-            "batched_graph_gbps": round(total_out_bits / t_batch / 1e9, 2), "batched_ms": round(t_batch * 1e3, 3),
+    peak = measured_peaks()[0]
+    return {"workload": "64 stream pairs, 2^U blocks (U~U(12,20)), n in {256,1024,4096}, 8- and 12-bit ADC samples "
+                        "(uint16, seeded on the device), ingest + extraction",
+            "streams": len(items), "raw_input_bytes": total_raw, "packed_input_bytes": total_packed,
+            "extracted_bits": total_out_bits,
+            "batched_graph_gbps": round(total_out_bits / t_graph / 1e9, 2), "batched_graph_ms": round(t_graph * 1e3, 3),
+            "graph": "128 qext_pack_samples launches + memset + one persistent batched kernel, one CUDA graph",
             "plain_per_stream_gbps": round(total_out_bits / t_plain / 1e9, 2), "plain_ms": round(t_plain * 1e3, 3),
-            "input_tb_per_s_batched": round(total_in / t_batch / 1e12, 3),
+            "plain": "one qext_extract_samples (fused ingest) per stream, 64 launches",
+            "extraction_only_graph_gbps": round(total_out_bits / t_extract / 1e9, 2),
+            "extraction_only_ms": round(t_extract * 1e3, 3),
+            "extraction_only_hbm_frac": round((total_packed + total_out_bits / 8) / t_extract / 1e9 / peak, 4),
             "autotuned": {k: cfg[k] for k in ("blocks_per_thread_small", "blocks_per_thread_mid", "ctas_per_sm",
                                               "order", "ntiles")}, "autotune_best_ms": round(tuned_ms, 3),
-            "outputs_equal_plain": same, "launches_per_run": 1}
+            "outputs_equal": {"extraction_only": same_extract, "plain_fused_per_stream": same_plain},
+            "kernel_launches_per_graph_run": 2 * len(items) + 1}
 
 
 def measure_paper_params(args, dev):
@@ -321,53 +358,132 @@ def measure_alg2(args, dev):
             "log2_error_bound": round(info["log2_error_bound"], 2)}
 
 
+SUSTAINED_CHUNK = 178956288   # samples: 2^31 - 8192 bits, the largest whole number of 3-block periods in 256 MiB
+
+
 def measure_sustained(args, dev):
-    """The sustained workload's shape: n = 4096 (q = 64) stream pairs pushed
-    through qext_stream_push in 256 MiB chunks (2^31 bits = 2^19 blocks per
-    source), state carried on the device, 16 chunks (4 GiB per source) cycling
-    over two chunk buffers of 12-bit ADC samples (sigma drifting +-5 %) packed
-    on the device by qext_pack_samples (not timed); CUDA events around the 16
-    pushes.  Inputs larger than L2 (512 MiB per push)."""
+    """The sustained workload: two 2^34-bit streams of 12-bit ADC samples
+    (n = 4096, q = 64) whose noise level drifts +-5 % sinusoidally over the
+    stream, fed as RAW samples (uint16 containers) in chunks of 178,956,288
+    samples through qext_stream_push_samples (ingest fused into the
+    extraction, stream state carried across chunks), for
+    --sustained-seconds of wall time.  --sustained-resident chunks per source
+    are generated and kept on the device and cycled (8 = the whole 2^34-bit
+    stream).  Every 8th chunk also goes through the min-entropy monitor
+    (qext_sample_histogram, one source), inside the timed region.  Sampled
+    chunks' outputs are kept and compared with the outputs of the same chunks
+    on later passes (identical, or the run is flagged).  The packed-word push
+    of the same chunk is timed beside it."""
     import numpy as np
     import torch
 
     from paper_2402_14607_gb300 import qext, workloads
-    spec = workloads.config_sustained(total_bits=1 << 32)
+    from paper_2402_14607_gb300.clocks import ClockSampler
+    total_bits = 1 << 34
+    stream_samples = total_bits // 12
+    spec = workloads.config_sustained(total_bits=total_bits)
     plan = qext.qext_plan_create(spec.n, 0, spec.k, spec.eps)
     info = plan.info
-    chunk_bits = 1 << 31
-    bufs = []
-    for c in range(2):
-        nsamp = chunk_bits // 12 + 1
-        sx = workloads.adc_samples(spec.seed_x + 100 * c, nsamp, 12, drift_amp=0.05, drift_period=float(nsamp))
-        sy = workloads.adc_samples(spec.seed_y + 100 * c, nsamp, 12, drift_amp=0.05, drift_period=float(nsamp))
-        px = torch.empty(-(-nsamp * 12 // 32), dtype=torch.int32, device=dev)
-        py = torch.empty_like(px)
-        qext.qext_pack_samples(12, torch.from_numpy(sx.view(np.int16)).to(dev), nsamp, px)
-        qext.qext_pack_samples(12, torch.from_numpy(sy.view(np.int16)).to(dev), nsamp, py)
-        bufs.append((px, py))
-    out_words = chunk_bits // 4096 * info["m"] // 32
-    out = torch.empty(out_words, dtype=torch.int32, device=dev)
+    R = max(1, args.sustained_resident)
+    chunk = SUSTAINED_CHUNK
+    blocks_per_chunk = chunk * 12 // spec.n
+    cap = blocks_per_chunk * info["m"] // 32
+    hx, hy, gx, gy = [], [], [], []
+    for c in range(R):
+        kw = dict(drift_amp=0.05, drift_period=float(stream_samples), start=c * chunk)
+        hx.append(workloads.adc_samples(spec.seed_x + 1000 * c, chunk, 12, **kw))
+        hy.append(workloads.adc_samples(spec.seed_y + 1000 * c, chunk, 12, **kw))
+        gx.append(torch.from_numpy(hx[-1].view(np.int16)).to(dev))
+        gy.append(torch.from_numpy(hy[-1].view(np.int16)).to(dev))
+    outs = [torch.empty(cap, dtype=torch.int32, device=dev) for _ in range(2)]
+    stream = torch.cuda.Stream(device=dev)
+    sh = int(stream.cuda_stream)
     s = qext.qext_stream_create(plan)
-    for c in range(2):  # warm-up pushes
-        qext.qext_stream_push(s, bufs[c][0], bufs[c][1], chunk_bits, out, out_words)
+    for c in range(min(R, 2)):   # warm-up pushes (the stream's state advances; it is one continuous stream)
+        qext.qext_stream_push_samples(s, 12, gx[c], gy[c], chunk, outs[c & 1], cap, sh)
     torch.cuda.synchronize()
-    nchunks = 16
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for c in range(nchunks):
-        qext.qext_stream_push(s, bufs[c % 2][0], bufs[c % 2][1], chunk_bits, out, out_words)
-    e1.record()
+    nmon = 256
+    counts = torch.zeros((nmon, 4096), dtype=torch.int64, device=dev)
+    spot_at = {0, 1, R, R + 1, 4 * R, 4 * R + 1, 64 * R, 64 * R + 1, 4096 * R + 1}
+    spots = {}
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(torch.cuda.current_device(), period_s=0.02 if args.sustained_seconds > 30 else 0.00025)
+    done0 = qext.qext_stream_info(s)["blocks_done"]
+    clocks.start()
+    ev0.record(stream)
+    t_end = time.perf_counter() + args.sustained_seconds
+    i = mon = 0
+    with torch.cuda.stream(stream):
+        while time.perf_counter() < t_end:
+            c = i % R
+            out = outs[i & 1]
+            w = qext.qext_stream_push_samples(s, 12, gx[c], gy[c], chunk, out, cap, sh)
+            if i % 7 == 0 and mon < nmon:
+                counts[mon].zero_()
+                qext.qext_sample_histogram(12, gx[c], chunk, counts[mon], sh)
+                mon += 1
+            if i in spot_at:
+                spots[i] = out[:w].clone()
+            i += 1
+    ev1.record(stream)
     torch.cuda.synchronize()
-    t = e0.elapsed_time(e1) * 1e-3
-    done = qext.qext_stream_info(s)["blocks_done"]
+    clk = clocks.stop()
+    t = ev0.elapsed_time(ev1) * 1e-3
+    blocks = qext.qext_stream_info(s)["blocks_done"] - done0
     s.close()
-    return {"workload": "n = 4096 (q = %d), 16 pushes of 2^31-bit chunks (4 GiB per source), 12-bit ADC with "
-                        "sigma drifting +-5 %%, packed words in HBM, state carried" % info["q"],
-            "chunks": nchunks, "blocks": done, "ms": round(t * 1e3, 3),
-            "extracted_gbps": round(nchunks * (chunk_bits // 4096) * info["m"] / t / 1e9, 2),
-            "input_tbit_per_s": round(2 * nchunks * chunk_bits / t / 1e12, 2),
-            "hbm_frac_of_measured": round(2 * nchunks * chunk_bits / 8 / t / 1e9 / measured_peaks()[0], 4)}
+    assert blocks == i * blocks_per_chunk
+    # clock record binned by SM clock
+    mhz = np.array([x[0] for x in clocks.samples]) if clocks.samples else np.zeros(0)
+    bins = {}
+    for v in mhz:
+        key = int(round(v / 15.0) * 15)
+        bins[key] = bins.get(key, 0) + 1
+    clock_bins = {str(k): round(v / max(1, mhz.size), 4) for k, v in sorted(bins.items())}
+    # min-entropy monitor: plug-in estimate per monitored chunk
+    hmin = [qext.qext_min_entropy_estimate(12, counts[k].cpu().numpy().view(np.uint64)) for k in range(mon)]
+    # spot checks during the run: a chunk pushed again on a later pass over the
+    # resident data must give the identical output (parity of that output with
+    # the oracle is the full-size stream test's business)
+    pairs = [(a_, b_) for a_ in spots for b_ in spots if a_ < b_ and (b_ - a_) % R == 0]
+    same = all(torch.equal(spots[a_], spots[b_]) for a_, b_ in pairs)
+    # the packed-word push of the same chunk (the extraction kernel alone)
+    px = torch.empty(chunk * 12 // 32, dtype=torch.int32, device=dev)
+    py = torch.empty_like(px)
+    qext.qext_pack_samples(12, gx[0], chunk, px, sh)
+    qext.qext_pack_samples(12, gy[0], chunk, py, sh)
+    s2 = qext.qext_stream_create(plan)
+    for _ in range(2):
+        qext.qext_stream_push(s2, px, py, chunk * 12, outs[0], cap, sh)
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for _ in range(16):
+        qext.qext_stream_push(s2, px, py, chunk * 12, outs[0], cap, sh)
+    p1.record(stream)
+    torch.cuda.synchronize()
+    tp = p0.elapsed_time(p1) * 1e-3 / 16
+    s2.close()
+    peak = measured_peaks()[0]
+    uint16_bytes = i * (2 * chunk * 2 + cap * 4)
+    packed_bytes = i * (2 * chunk * 12 // 8 + cap * 4)
+    return {"workload": "two 2^34-bit streams of 12-bit ADC samples (n = 4096, q = %d), sigma drifting +-5 %% over "
+                        "the stream, raw samples (uint16) pushed in chunks of %d samples (2^31 - 8192 bits) through "
+                        "qext_stream_push_samples, ingest fused and timed, state carried; %d chunk(s) per source "
+                        "resident and cycled; min-entropy monitor on every 7th chunk" % (info["q"], chunk, R),
+            "seconds": round(t, 3), "chunks": i, "blocks": blocks,
+            "extracted_gbps": round(blocks * info["m"] / t / 1e9, 2),
+            "input_tbit_per_s": round(2 * i * chunk * 12 / t / 1e12, 2),
+            "hbm_frac_uint16_bytes": round(uint16_bytes / t / 1e9 / peak, 4),
+            "hbm_frac_packed_bytes": round(packed_bytes / t / 1e9 / peak, 4),
+            "clocks": {"sm_mhz_median": clk.get("sm_mhz"), "sm_max_mhz": clk.get("sm_max_mhz"),
+                       "reasons": clk.get("reasons"), "samples": clk.get("samples"), "bins_mhz_fraction": clock_bins},
+            "monitor_h_min_bits": {"chunks": mon, "min": round(min(hmin), 3) if hmin else None,
+                                   "max": round(max(hmin), 3) if hmin else None,
+                                   "first": [round(h, 3) for h in hmin[:8]]},
+            "spot_check": {"pushes_kept": sorted(spots), "pairs_compared": len(pairs),
+                           "repeated_chunks_identical": bool(same)},
+            "packed_push": {"us_per_chunk": round(tp * 1e6, 1),
+                            "extracted_gbps": round(blocks_per_chunk * info["m"] / tp / 1e9, 2),
+                            "hbm_frac": round((2 * chunk * 12 / 8 + cap * 4) / tp / 1e9 / peak, 4)}}
 
 
 def measure_monitor(args, dev):
@@ -746,6 +862,10 @@ def main(argv=None):
                     default=None, help="run only this extra measurement and print it (for kernel profiles)")
     ap.add_argument("--e2e-chunk-blocks", type=int, default=1 << 17)
     ap.add_argument("--serving-requests", type=int, default=1000)
+    ap.add_argument("--sustained-seconds", type=float, default=3.0,
+                    help="wall time of the sustained raw-sample stream (600 for the 10-minute run)")
+    ap.add_argument("--sustained-resident", type=int, default=2,
+                    help="chunks per source generated and cycled on the device (8 = the whole 2^34-bit stream)")
     ap.add_argument("--unfused", action="store_true",
                     help="step = qext_pack_samples x2 (uint16 samples) + qext_extract")
     ap.add_argument("--step", choices=["packed", "uint16"], default="packed",

@@ -266,6 +266,29 @@ int qext_stream_push(qext_stream *s, const uint32_t *x, const uint32_t *y, uint6
                      uint64_t out_capacity_words, uint64_t *out_words, qext_cuda_stream stream);
 
 /*
+ * qext_stream_push_samples -- qext_stream_push for raw ADC samples: appends
+ * nsamples b-bit samples of each source (the low b bits of each uint16,
+ * sample j at the next stream bits [j*b, (j+1)*b), LSB first; Sec. 3's
+ * X_1 ... X_N fed in time order) and extracts every block that becomes
+ * complete, with the same output, counters and state as qext_pack_samples
+ * followed by qext_stream_push of the nsamples*b packed bits.
+ *   b            1 .. 16 (else INVAL);
+ *   x_samples, y_samples  DEVICE pointers to nsamples uint16 each, 2-byte
+ *                aligned.
+ * With no tail or pending bits held, b in {8, 12, 16}, q in {4, 16, 64}
+ * and 16-byte aligned samples, the whole blocks run through the fused
+ * ingest + extraction kernel of qext_extract_samples and only the leftover
+ * bits are packed (into the new tail); otherwise the samples are packed into
+ * the stream's own staging buffers (device memory owned by the stream, grown
+ * on demand: a push that grows them synchronises `stream` first) and pushed
+ * as bits.  out, out_capacity_words, *out_words and the asynchrony are as
+ * for qext_stream_push.  Errors: INVAL, NOSPACE, UNSUPPORTED, CUDA.
+ */
+int qext_stream_push_samples(qext_stream *s, uint32_t b, const uint16_t *x_samples, const uint16_t *y_samples,
+                             uint64_t nsamples, uint32_t *out, uint64_t out_capacity_words, uint64_t *out_words,
+                             qext_cuda_stream stream);
+
+/*
  * qext_stream_flush -- ends the stream: writes the pending output bits (if
  * any) to out[0] (DEVICE, zero above *out_bits) and drops the incomplete
  * block (Algorithm 1 outputs whole blocks only).  Counters keep blocks_done.

@@ -36,6 +36,8 @@ struct qext_stream {
     uint32_t *tail[2][2];   // [buffer][source], wpb + 1 words each (device)
     uint32_t *pending;      // 1 word (device)
     int device;
+    uint32_t *stage[2];     // packed copies of raw-sample pushes on the general path (device, grown on demand)
+    uint64_t stage_words;   // capacity of each, words
 };
 
 namespace qxd {

@@ -114,6 +114,43 @@ __global__ void tail_copy_kernel(const uint32_t *tx, const uint32_t *ty, uint64_
     }
 }
 
+// 32 stream bits starting at bit `bit` of the b-bit samples smp[0 .. ns)
+// (sample j at bits [j*b, (j+1)*b), LSB first; bits past ns*b read as 0)
+__device__ __forceinline__ uint32_t sample_bits32(const uint16_t *smp, uint64_t ns, uint32_t b, uint64_t bit) {
+    const uint32_t mask = b >= 16 ? 0xFFFFu : (1u << b) - 1u;
+    uint32_t w = 0;
+    for (uint64_t j = bit / b; j < ns && j * b < bit + 32; ++j) {
+        const uint32_t v = smp[j] & mask;
+        const int64_t sh = int64_t(j * b) - int64_t(bit);  // position of the sample's bit 0 in w
+        w |= sh >= 0 ? v << sh : v >> -sh;
+    }
+    return w;
+}
+
+// New tail from a raw-sample push with no carried tail: stream bits
+// [from, from + nbits) of the samples into dx, dy (dst_words words, zero
+// above nbits).
+__global__ void tail_from_samples_kernel(const uint16_t *sx, const uint16_t *sy, uint64_t ns, uint32_t b,
+                                         uint64_t from, uint64_t nbits, uint32_t *dx, uint32_t *dy,
+                                         uint32_t dst_words) {
+    for (uint32_t i = threadIdx.x; i < dst_words; i += blockDim.x) {
+        uint32_t a = 0, c = 0;
+        const uint64_t bit = 32ull * i;
+        if (bit < nbits) {
+            a = sample_bits32(sx, ns, b, from + bit);
+            c = sample_bits32(sy, ns, b, from + bit);
+            const uint64_t keep = nbits - bit;
+            if (keep < 32) {
+                const uint32_t mk = (1u << keep) - 1u;
+                a &= mk;
+                c &= mk;
+            }
+        }
+        dx[i] = a;
+        dy[i] = c;
+    }
+}
+
 // pending <- out[word] & low `bits` bits (bits in 1..31)
 __global__ void save_pending_kernel(const uint32_t *out, uint64_t word, uint32_t bits, uint32_t *pending) {
     if (threadIdx.x == 0) *pending = out[word] & ((1u << bits) - 1u);
@@ -199,6 +236,7 @@ int qext_stream_create(const qext_plan *p, qext_stream **out) {
 int qext_stream_destroy(qext_stream *s) {
     if (!s) return QEXT_OK;
     cudaFree(s->tail[0][0]);
+    cudaFree(s->stage[0]);
     delete s;
     return QEXT_OK;
 }
@@ -273,6 +311,69 @@ int qext_stream_push(qext_stream *s, const uint32_t *x, const uint32_t *y, uint6
     if (nt > 0 || t > 0) {
         tail_copy_kernel<<<1, 256, 0, st>>>(s->tail[s->cur][0], s->tail[s->cur][1], t, x, y, chunk_words, B * n, nt,
                                             s->tail[nxt][0], s->tail[nxt][1], dst_words);
+        if (cudaGetLastError() != cudaSuccess) return QEXT_E_CUDA;
+        s->cur = nxt;
+    }
+    s->tail_bits = nt;
+    s->pending_bits = r;
+    s->blocks_done += B;
+    *out_words = total_out >> 5;
+    return QEXT_OK;
+}
+
+int qext_stream_push_samples(qext_stream *s, uint32_t b, const uint16_t *x_samples, const uint16_t *y_samples,
+                             uint64_t nsamples, uint32_t *out, uint64_t out_capacity_words, uint64_t *out_words,
+                             qext_cuda_stream stream) {
+    if (!s || !out_words) return QEXT_E_INVAL;
+    *out_words = 0;
+    if (b < 1 || b > 16) return QEXT_E_INVAL;
+    if (nsamples == 0) return QEXT_OK;
+    if (!x_samples || !y_samples || reinterpret_cast<uintptr_t>(x_samples) % 2 ||
+        reinterpret_cast<uintptr_t>(y_samples) % 2)
+        return QEXT_E_INVAL;
+    if (nsamples > (UINT64_MAX - s->tail_bits) / 16) return QEXT_E_INVAL;
+    const qext::NvtxRange range("qext stream push (raw samples)");
+    const uint64_t t = s->tail_bits, p = s->pending_bits, n = s->n, m = s->m;
+    const uint64_t nbits = nsamples * b;
+    const uint64_t B = (t + nbits) / n;
+    const uint64_t total_out = p + B * m;
+    const uint64_t need = (total_out + 31) / 32;
+    if (need && (!out || !aligned4(out))) return QEXT_E_INVAL;
+    if (out_capacity_words < need) return QEXT_E_NOSPACE;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const uint32_t q = s->plan->q;
+    const bool fused = t == 0 && p == 0 && B > 0 && (b == 8 || b == 12 || b == 16) && (q == 4 || q == 16 || q == 64) &&
+                       reinterpret_cast<uintptr_t>(x_samples) % 16 == 0 && reinterpret_cast<uintptr_t>(y_samples) % 16 == 0;
+    if (!fused) {
+        // general path: pack into the stream's staging buffers, then push the bits
+        const uint64_t words = (nbits + 31) / 32;
+        if (words > s->stage_words) {
+            uint32_t *mem = nullptr;
+            if (cudaStreamSynchronize(st) != cudaSuccess) return QEXT_E_CUDA;  // old buffers may be in use
+            if (cudaMalloc(&mem, 2 * words * sizeof(uint32_t)) != cudaSuccess) return QEXT_E_CUDA;
+            cudaFree(s->stage[0]);
+            s->stage[0] = mem;
+            s->stage[1] = mem + words;
+            s->stage_words = words;
+        }
+        int rc = qext::launch_pack(b, x_samples, nsamples, s->stage[0], stream);
+        if (rc == QEXT_OK) rc = qext::launch_pack(b, y_samples, nsamples, s->stage[1], stream);
+        if (rc != QEXT_OK) return rc;
+        return qext_stream_push(s, s->stage[0], s->stage[1], nbits, out, out_capacity_words, out_words, stream);
+    }
+    // fused path: no carried state, whole blocks straight from the samples
+    int rc = qext::launch_extract_samples(s->plan, b, x_samples, y_samples, nsamples, B, out, stream, 0);
+    if (rc != QEXT_OK) return rc;
+    const uint32_t r = uint32_t(total_out & 31u);
+    if (r) {
+        save_pending_kernel<<<1, 32, 0, st>>>(out, total_out >> 5, r, s->pending);
+        if (cudaGetLastError() != cudaSuccess) return QEXT_E_CUDA;
+    }
+    const uint64_t nt = nbits - B * n;
+    if (nt > 0) {
+        const int nxt = s->cur ^ 1;
+        tail_from_samples_kernel<<<1, 256, 0, st>>>(x_samples, y_samples, nsamples, b, B * n, nt, s->tail[nxt][0],
+                                                    s->tail[nxt][1], s->wpb + 1);
         if (cudaGetLastError() != cudaSuccess) return QEXT_E_CUDA;
         s->cur = nxt;
     }

@@ -98,6 +98,7 @@ def lib():
     L.qext_stream_info.argtypes = [vp, P(u64), P(u64), P(u32)]
     L.qext_stream_push.argtypes = [vp, vp, vp, u64, vp, u64, P(u64), vp]
     L.qext_stream_flush.argtypes = [vp, vp, u64, P(u32), vp]
+    L.qext_stream_push_samples.argtypes = [vp, u32, vp, vp, u64, vp, u64, P(u64), vp]
     L.qext_stream_state_size.argtypes = [vp]
     L.qext_stream_state_size.restype = ctypes.c_size_t
     L.qext_stream_save.argtypes = [vp, vp, ctypes.c_size_t, P(ctypes.c_size_t), vp]
@@ -134,7 +135,7 @@ def lib():
     for name in ["qext_plan_create", "qext_destroy", "qext_plan_info", "qext_alg1_params", "qext_extract",
                  "qext_extract_ex", "qext_extract_samples", "qext_extract_samples_ex",
                  "qext_pack_samples", "qext_device_status", "qext_stream_create", "qext_stream_destroy",
-                 "qext_stream_info", "qext_stream_push", "qext_stream_flush", "qext_stream_save",
+                 "qext_stream_info", "qext_stream_push", "qext_stream_push_samples", "qext_stream_flush", "qext_stream_save",
                  "qext_stream_restore", "qext_batch_create", "qext_batch_destroy", "qext_batch_get_config",
                  "qext_batch_set_config", "qext_batch_run", "qext_batch_run_ex", "qext_batch_capture", "qext_batch_launch",
                  "qext_batch_autotune", "qext_batch_run_noalloc", "qext_server_create", "qext_server_destroy",
@@ -294,6 +295,15 @@ def qext_stream_push(s: Stream, x, y, nbits: int, out, out_capacity_words: int, 
     w = ctypes.c_uint64()
     _check(lib().qext_stream_push(s.handle, _ptr(x), _ptr(y), nbits, _ptr(out), out_capacity_words,
                                   ctypes.byref(w), _stream(stream)), "qext_stream_push")
+    return w.value
+
+
+def qext_stream_push_samples(s: Stream, b: int, x_samples, y_samples, nsamples: int, out, out_capacity_words: int,
+                             stream=None) -> int:
+    w = ctypes.c_uint64()
+    _check(lib().qext_stream_push_samples(s.handle, b, _ptr(x_samples), _ptr(y_samples), nsamples, _ptr(out),
+                                          out_capacity_words, ctypes.byref(w), _stream(stream)),
+           "qext_stream_push_samples")
     return w.value
 
 

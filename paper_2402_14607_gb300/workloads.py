@@ -44,6 +44,25 @@ def adc_samples(seed: int, nsamples: int, b: int, sigma: float = 1.0, offset_amp
     return np.clip(v, 0, (1 << b) - 1).astype(np.uint16)
 
 
+def adc_samples_device(seed: int, nsamples: int, b: int, device, chunk: int = 1 << 25):
+    """Quantised Gaussian ADC samples drawn on the device by torch's seeded
+    generator, for workloads too large to draw on the host: N(0,1) noise
+    clipped at +-4 sigma and quantised to b-bit codes, floor((g + 4)/8 * 2^b),
+    as adc_samples does, with a different random source.  Returns an int16
+    tensor holding the codes (uint16 bit patterns)."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    out = torch.empty(nsamples, dtype=torch.int16, device=device)
+    scale = float(1 << b) / 8.0
+    for a in range(0, nsamples, chunk):
+        k = min(chunk, nsamples - a)
+        g = torch.randn(k, generator=gen, device=device, dtype=torch.float32)
+        v = torch.clamp(torch.floor((g + 4.0) * scale), 0, (1 << b) - 1)
+        out[a:a + k] = v.to(torch.int32).to(torch.int16)
+    return out
+
+
 def random_words(seed: int, nwords: int) -> np.ndarray:
     """Uniformly random uint32 words (full-entropy test input)."""
     rng = np.random.Generator(np.random.PCG64(seed))

@@ -211,3 +211,144 @@ def test_sustained_chunks_fast_path():
         l = int(l)
         z = oracle.extract(64, 64, 64, poly, ox[l * 128:(l + 1) * 128], oy[l * 128:(l + 1) * 128], 1)
         assert bits_at(got, l * 64, 64) == int(z[0]) | (int(z[1]) << 32), "block %d" % l
+
+
+def _push_raw(s, plan, b, sx, sy, a, k, misalign):
+    """Push samples [a, a + k) of each source as a fresh device array (16-byte
+    aligned, or 2-byte aligned with misalign); returns the output words."""
+    info = plan.info
+    st = qext.qext_stream_info(s)
+    newb = (st["tail_bits"] + k * b) // info["n"]
+    cap = (st["pending_bits"] + newb * info["m"] + 31) // 32
+    out = torch.full((cap + 2,), -1, dtype=torch.int32, device="cuda")
+    off = 1 if misalign else 0
+    gx = torch.zeros(k + off + 8, dtype=torch.int16, device="cuda")
+    gy = torch.zeros_like(gx)
+    if k:
+        gx[off:off + k] = torch.from_numpy(sx[a:a + k].view(np.int16)).cuda()
+        gy[off:off + k] = torch.from_numpy(sy[a:a + k].view(np.int16)).cuda()
+    w = qext.qext_stream_push_samples(s, b, gx[off:], gy[off:], k, out, cap)
+    torch.cuda.synchronize()
+    got = host_words(out)
+    assert (got[cap:] == 0xFFFFFFFF).all(), "push wrote past its capacity"
+    return got[:w]
+
+
+def _realigning_count(plan, st, b, limit):
+    """Smallest k <= limit after which the stream holds no tail and no pending bits."""
+    n, m = plan.info["n"], plan.info["m"]
+    for k in range(1, limit + 1):
+        v = st["tail_bits"] + k * b
+        if v % n == 0 and (st["pending_bits"] + (v // n) * m) % 32 == 0:
+            return k
+    return None
+
+
+@pytest.mark.parametrize("q,m,b,seed", [(16, 16, 12, 1), (64, 64, 12, 2), (4, 4, 8, 3), (16, 13, 16, 4),
+                                         (64, 41, 8, 5), (8, 8, 12, 6), (16, 16, 5, 7)])
+def test_raw_sample_pushes_match_oracle(q, m, b, seed):
+    """Raw-sample pushes (qext_stream_push_samples) of random sample counts,
+    some starting on a block boundary with nothing pending (fused path), some
+    not (packed into the stream's staging buffers), mixed with pushes of the
+    packed bits and a checkpoint, give the oracle's one-shot output of the
+    whole stream."""
+    plan = plan_for(q, 64, m)
+    info = plan.info
+    n = info["n"]
+    rng = np.random.Generator(np.random.PCG64(seed))
+    total = 60 * n // b + 3
+    sx = workloads.adc_samples(100 + seed, total, b)
+    sy = workloads.adc_samples(200 + seed, total, b)
+    ox, oy = oracle.pack_samples(b, sx), oracle.pack_samples(b, sy)
+    xi, yi = to_int(ox), to_int(oy)
+    s = qext.qext_stream_create(plan)
+    out_bits, nout, a, step = 0, 0, 0, 0
+    while a < total:
+        st = qext.qext_stream_info(s)
+        kind = step % 5
+        if kind == 0:                      # realign, then a whole-period push (fused where supported)
+            k = _realigning_count(plan, st, b, total - a) or (total - a)
+        elif kind == 3:                    # packed bits of the next samples (qext_stream_push)
+            k = min(int(rng.integers(1, 3 * n // b)), total - a)
+        else:
+            k = min(int(rng.integers(0, 4 * n // b)), total - a)
+        if kind == 3:
+            L = k * b
+            cx, cy = chunk_words(xi, a * b, L), chunk_words(yi, a * b, L)
+            newb = (st["tail_bits"] + L) // n
+            cap = (st["pending_bits"] + newb * info["m"] + 31) // 32
+            out = torch.full((cap + 2,), -1, dtype=torch.int32, device="cuda")
+            w = qext.qext_stream_push(s, cx, cy, L, out, cap)
+            torch.cuda.synchronize()
+            words = host_words(out)[:w]
+        else:
+            words = _push_raw(s, plan, b, sx, sy, a, k, misalign=(kind == 4))
+        out_bits |= to_int(words) << nout
+        nout += 32 * len(words)
+        a += k
+        step += 1
+        if step == 7:
+            state = qext.qext_stream_save(s)
+            s.close()
+            s = qext.qext_stream_restore(plan, state)
+    out = torch.full((2,), -1, dtype=torch.int32, device="cuda")
+    fb = qext.qext_stream_flush(s, out, 1)
+    torch.cuda.synchronize()
+    if fb:
+        out_bits |= int(host_words(out)[0]) << nout
+        nout += fb
+    s.close()
+    want, wbits = oracle_bits(plan, ox, oy, total * b)
+    assert nout == wbits
+    assert out_bits == want
+
+
+def test_raw_sample_full_chunk_with_carried_state():
+    """The sustained workload's chunk at full size: 12-bit samples with drifting
+    sigma, n = 4096.  A small whole-period push (fused path), then 1000 samples
+    that end mid-block, then one full chunk of 178,956,288 samples (2^31 - 8192
+    bits: the largest whole number of 3-block periods within 256 MiB) pushed
+    with that tail carried, then a realigning push; sampled blocks of every
+    part, and the blocks around each boundary, match the oracle."""
+    chunk = 178956288
+    first, mid = 1024, 1000
+    spec = workloads.config_sustained(total_bits=(first + mid + chunk + 4096) * 12)
+    plan = qext.qext_plan_create(spec.n, 0, spec.k, spec.eps)
+    assert (plan.info["q"], plan.info["m"]) == (64, 64)
+    sx, sy = spec.samples("x"), spec.samples("y")
+    gx = torch.from_numpy(sx.view(np.int16)).cuda()
+    gy = torch.from_numpy(sy.view(np.int16)).cuda()
+    s = qext.qext_stream_create(plan)
+    parts = []
+    a = 0
+    for k in (first, mid, chunk):
+        st = qext.qext_stream_info(s)
+        cap = (st["pending_bits"] + (st["tail_bits"] + 12 * k) // 4096 * 64 + 31) // 32
+        out = torch.empty(cap + 1, dtype=torch.int32, device="cuda")
+        w = qext.qext_stream_push_samples(s, 12, gx[a:], gy[a:], k, out, cap)
+        parts.append(out[:w])
+        a += k
+    st = qext.qext_stream_info(s)
+    k = _realigning_count(plan, st, 12, 4096)
+    cap = (st["tail_bits"] + 12 * k) // 4096 * 2
+    out = torch.empty(cap + 1, dtype=torch.int32, device="cuda")
+    parts.append(out[:qext.qext_stream_push_samples(s, 12, gx[a:], gy[a:], k, out, cap)])
+    a += k
+    torch.cuda.synchronize()
+    got = np.concatenate([host_words(p) for p in parts])
+    nb = a * 12 // 4096
+    assert qext.qext_stream_info(s) == dict(blocks_done=nb, tail_bits=0, pending_bits=0)
+    s.close()
+    assert got.size == 2 * nb
+    ox = oracle.pack_samples(12, sx[:a])
+    oy = oracle.pack_samples(12, sy[:a])
+    poly, _ = oracle.select_poly(64)
+    b1 = first * 12 // 4096
+    b2 = (first + mid) * 12 // 4096
+    rng = np.random.Generator(np.random.PCG64(11))
+    sample = np.unique(np.concatenate([rng.integers(0, nb, 300), np.arange(0, 6), np.arange(b1 - 2, b2 + 3),
+                                       np.arange(nb - 6, nb)]))
+    for l in sample:
+        l = int(l)
+        z = oracle.extract(64, 64, 64, poly, ox[l * 128:(l + 1) * 128], oy[l * 128:(l + 1) * 128], 1)
+        assert bits_at(got, l * 64, 64) == int(z[0]) | (int(z[1]) << 32), "block %d" % l
