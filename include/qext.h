@@ -540,10 +540,14 @@ typedef struct qext_alg2_plan qext_alg2_plan;
  * qext_alg2_plan_create -- the first max_blocks blocks of Algorithm 2 for
  * b-bit samples (1 <= b <= 16) of min-entropy rate delta.  q1 and Delta * b
  * must be multiples of 16 (the GPU works on 16-bit units), and
- * q1 + (max_blocks - 1) * Delta * b <= 256 (the largest field built),
- * else UNSUPPORTED.  Holds the per-block polynomials and a device table of
- * them (allocated on the current device).  Caller owns *out.
- * Errors: INVAL, ENTROPY (delta <= 1/2), UNSUPPORTED, PARAM, CUDA.
+ * q1 + (max_blocks - 1) * Delta * b <= 2048 (the largest field built; at
+ * q1 = Delta * b = 16 that is 128 blocks), else UNSUPPORTED.  Finds every
+ * block's field polynomial on the host (the searches of the distinct degrees
+ * run on parallel host threads and are kept for the process: seconds the
+ * first time for fields up to 2048, nothing after that); touches no GPU.
+ * The device tables are made by the first qext_alg2_extract, on the device
+ * then current, which the plan is then bound to.  Caller owns *out.
+ * Errors: INVAL, ENTROPY (delta <= 1/2), UNSUPPORTED, PARAM.
  */
 int qext_alg2_plan_create(double delta, uint32_t b, uint32_t q1, uint32_t Delta, uint32_t max_blocks,
                           qext_alg2_plan **out);
@@ -562,7 +566,11 @@ int qext_alg2_block_info(const qext_alg2_plan *p, uint32_t l, uint32_t *q_l, uin
  *         bits [16u, 16u + 16), LSB first; for b = 16 the samples
  *         themselves), 2-byte aligned, at least in_bit(nblocks) / 16 units;
  *   out   DEVICE pointer to out_bit(nblocks) / 16 units, fully written.
- * One CTA per block.  Asynchronous on stream.  Errors: INVAL, CUDA.
+ * Each block's unit products run as work items over many CTAs of one launch
+ * into the plan's device sums, which a second launch reduces mod P_{q_l}, one
+ * CTA per block.  Asynchronous on stream; calls on one plan that overlap on
+ * the GPU share its sums and race (order them on one stream).  Errors: INVAL,
+ * STATE (a device other than the one the plan's tables live on), CUDA.
  */
 int qext_alg2_extract(const qext_alg2_plan *p, const uint16_t *x, const uint16_t *y, uint32_t nblocks, uint16_t *out,
                       qext_cuda_stream stream);

@@ -86,7 +86,8 @@ def _configure(lib):
     lib.orc_alg1_params.argtypes = [ctypes.c_double, ctypes.c_uint32, ctypes.c_double, ctypes.c_double,
                                     u32p, u32p]
     lib.orc_alg1_params.restype = ctypes.c_int
-    lib.orc_extract_alg2.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, u32p, u32p, u32p]
+    lib.orc_extract_alg2.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, u32p, u32p, u32p,
+                                     ctypes.POINTER(ctypes.c_int)]
     lib.orc_extract_alg2.restype = ctypes.c_int
     lib.orc_alg2_log2_error.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     lib.orc_alg2_log2_error.restype = ctypes.c_double
@@ -186,11 +187,14 @@ def extract(q: int, n_p: int, m: int, poly: int, x: np.ndarray, y: np.ndarray, n
     return out[: (nblocks * m + 31) // 32]
 
 
-def extract_alg2(n_p: int, q1: int, dq: int, nblocks: int, x: np.ndarray, y: np.ndarray) -> np.ndarray:
+def extract_alg2(n_p: int, q1: int, dq: int, nblocks: int, x: np.ndarray, y: np.ndarray,
+                 taps=None) -> np.ndarray:
     """Algorithm 2 (Sec. 3.3) over its first ``nblocks`` blocks: block l has
     q_l = q1 + l*dq (dq = Delta*b) and takes the next q_l*n_p stream bits of
     each packed uint32 stream; returns the concatenated outputs (sum q_l bits)
-    as uint32 words."""
+    as uint32 words.  ``taps``: per block the taps (c, b, a) of P_{q_l} below
+    x^{q_l} (0 past a trinomial's one tap), e.g. as select_poly found them
+    earlier; None makes the oracle search every P_{q_l} itself."""
     lib = _load()
     x = np.ascontiguousarray(x, dtype=np.uint32)
     y = np.ascontiguousarray(y, dtype=np.uint32)
@@ -199,7 +203,14 @@ def extract_alg2(n_p: int, q1: int, dq: int, nblocks: int, x: np.ndarray, y: np.
     if x.size < need or y.size < need:
         raise ValueError("streams shorter than nblocks blocks")
     out = np.zeros(max(1, (sum(qs) + 31) // 32), dtype=np.uint32)
-    if lib.orc_extract_alg2(n_p, q1, dq, nblocks, _u32(x), _u32(y), _u32(out)) != 0:
+    tp = None
+    if taps is not None:
+        t = np.zeros(3 * nblocks, dtype=np.int32)
+        for l in range(nblocks):
+            for i, v in enumerate(list(taps[l])[:3]):
+                t[3 * l + i] = int(v)
+        tp = t.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    if lib.orc_extract_alg2(n_p, q1, dq, nblocks, _u32(x), _u32(y), _u32(out), tp) != 0:
         raise ValueError("bad Algorithm 2 parameters")
     return out
 

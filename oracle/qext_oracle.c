@@ -34,7 +34,7 @@
 #include <omp.h>
 #endif
 
-#define ORC_MAXQ 256                      /* largest field degree supported   */
+#define ORC_MAXQ 2048                     /* largest field degree supported   */
 #define ORC_W ((ORC_MAXQ + 64) / 64 + 1)  /* words of a degree <= MAXQ poly   */
 #define ORC_W2 (2 * ORC_W)                /* words of a product before mod    */
 
@@ -67,6 +67,9 @@ void orc_gf_mul(int q, const uint64_t *poly, const uint64_t *a, const uint64_t *
 {
     uint64_t sh[ORC_W], acc[ORC_W];
     int nw = q / 64 + 1;
+    int pe[ORC_MAXQ + 1], npe = 0;                    /* exponents of P's nonzero terms */
+    for (int d = 0; d <= q; ++d)
+        if (pbit(poly, d)) pe[npe++] = d;
     memset(sh, 0, sizeof sh);
     memset(acc, 0, sizeof acc);
     for (int d = 0; d < q; ++d)
@@ -78,8 +81,7 @@ void orc_gf_mul(int q, const uint64_t *poly, const uint64_t *a, const uint64_t *
         for (int w = nw - 1; w > 0; --w) sh[w] = (sh[w] << 1) | (sh[w - 1] >> 63);
         sh[0] <<= 1;
         if (pbit(sh, q))
-            for (int d = 0; d <= q; ++d)
-                if (pbit(poly, d)) pflip(sh, d);
+            for (int t = 0; t < npe; ++t) pflip(sh, pe[t]);   /* sh -= P */
     }
     int ow = (q + 63) / 64;
     for (int w = 0; w < ow; ++w) out[w] = acc[w];
@@ -89,28 +91,52 @@ void orc_gf_mul(int q, const uint64_t *poly, const uint64_t *a, const uint64_t *
 /* Polynomial arithmetic over F_2 used only by the irreducibility test.      */
 /* ------------------------------------------------------------------------ */
 
-/* r = a mod m (m nonzero); all arrays ORC_W2 words */
+/* r ^= m * x^s (word arrays of ORC_W2 words; the shifted copy must fit) */
+static void pxor_shifted(uint64_t *r, const uint64_t *m, int s)
+{
+    int ws = s >> 6, bs = s & 63;
+    for (int i = ORC_W2 - 1; i >= ws; --i) {
+        uint64_t v = m[i - ws] << bs;
+        if (bs && i - ws - 1 >= 0) v |= m[i - ws - 1] >> (64 - bs);
+        r[i] ^= v;
+    }
+}
+
+/*
+ * r = a mod m (m nonzero); all arrays ORC_W2 words.  Long division from the
+ * top coefficient down: each set coefficient d >= deg m of the running
+ * remainder is cleared by subtracting m * x^(d - deg m).  A sparse m (at most
+ * 8 terms, e.g. a field polynomial) is subtracted term by term, a dense one
+ * as a shifted word copy; both are the same subtraction.
+ */
 static void pmod(const uint64_t *a, const uint64_t *m, uint64_t *r)
 {
     int dm = pdeg(m, ORC_W2);
+    int me[8], nme = 0, sparse = 1;
+    for (int e = 0; e <= dm; ++e)
+        if (pbit(m, e)) {
+            if (nme == 8) { sparse = 0; break; }
+            me[nme++] = e;
+        }
     memcpy(r, a, sizeof(uint64_t) * ORC_W2);
     for (int d = pdeg(r, ORC_W2); d >= dm; --d)
-        if (pbit(r, d))
-            for (int e = 0; e <= dm; ++e)
-                if (pbit(m, e)) pflip(r, d - dm + e);
+        if (pbit(r, d)) {
+            if (sparse)
+                for (int t = 0; t < nme; ++t) pflip(r, d - dm + me[t]);
+            else
+                pxor_shifted(r, m, d - dm);
+        }
 }
 
-/* r = a*b mod m, schoolbook product then remainder */
-static void pmulmod(const uint64_t *a, const uint64_t *b, const uint64_t *m, uint64_t *r)
+/* r = a^2 mod m: over F_2, (sum a_i x^i)^2 = sum a_i x^(2i) */
+static void psqrmod(const uint64_t *a, const uint64_t *m, uint64_t *r)
 {
-    uint64_t prod[ORC_W2];
-    memset(prod, 0, sizeof prod);
-    int da = pdeg(a, ORC_W2), db = pdeg(b, ORC_W2);
+    uint64_t sq[ORC_W2];
+    memset(sq, 0, sizeof sq);
+    int da = pdeg(a, ORC_W2);
     for (int i = 0; i <= da; ++i)
-        if (pbit(a, i))
-            for (int j = 0; j <= db; ++j)
-                if (pbit(b, j)) pflip(prod, i + j);
-    pmod(prod, m, r);
+        if (pbit(a, i)) pset(sq, 2 * i);
+    pmod(sq, m, r);
 }
 
 /* g = gcd(a, b), Euclid */
@@ -135,7 +161,7 @@ static void x_pow_2e(int e, const uint64_t *m, uint64_t *r)
     pset(x, 1);
     pmod(x, m, r);
     for (int i = 0; i < e; ++i) {
-        pmulmod(r, r, m, t);
+        psqrmod(r, m, t);
         memcpy(r, t, sizeof t);
     }
 }
@@ -183,34 +209,56 @@ int orc_is_irreducible(int q, const uint64_t *poly)
  */
 int orc_select_poly(int q, uint64_t *poly, int *taps)
 {
-    uint64_t p[ORC_W];
     int nw = q / 64 + 1;
     taps[0] = taps[1] = taps[2] = 0;
+    if (q < 1 || q > ORC_MAXQ) return 0;
     if (q == 1) {
         memset(poly, 0, sizeof(uint64_t) * nw);
         pset(poly, 1);
         return 2;
     }
+    /* trinomials x^q + x^a + 1 in the order of a; the candidates are tested in
+       parallel and the smallest irreducible one is taken */
+    int best = q;
+#pragma omp parallel for schedule(dynamic, 1) reduction(min:best)
     for (int a = 1; a < q; ++a) {
+        if (a >= best) continue;
+        uint64_t p[ORC_W];
         memset(p, 0, sizeof p);
         pset(p, q); pset(p, a); pset(p, 0);
-        if (orc_is_irreducible(q, p)) {
-            memcpy(poly, p, sizeof(uint64_t) * nw);
-            taps[0] = a;
-            return 3;
+        if (orc_is_irreducible(q, p)) best = a;
+    }
+    if (best < q) {
+        memset(poly, 0, sizeof(uint64_t) * nw);
+        pset(poly, q); pset(poly, best); pset(poly, 0);
+        taps[0] = best;
+        return 3;
+    }
+    /* pentanomials x^q + x^c + x^b + x^a + 1, q > c > b > a >= 1, in the order
+       of c, then b, then a: the candidates with one c are tested together */
+    for (int c = 3; c < q; ++c) {
+        int n = (c - 1) * (c - 2) / 2, first = n;   /* pairs (b, a), b > a >= 1, in order */
+#pragma omp parallel for schedule(dynamic, 1) reduction(min:first)
+        for (int k = 0; k < n; ++k) {
+            if (k >= first) continue;
+            int b = 2, left = k;                    /* the k-th pair in the (b, a) order */
+            while (left >= b - 1) { left -= b - 1; ++b; }
+            int a = 1 + left;
+            uint64_t p[ORC_W];
+            memset(p, 0, sizeof p);
+            pset(p, q); pset(p, c); pset(p, b); pset(p, a); pset(p, 0);
+            if (orc_is_irreducible(q, p)) first = k;
+        }
+        if (first < n) {
+            int b = 2, left = first;
+            while (left >= b - 1) { left -= b - 1; ++b; }
+            int a = 1 + left;
+            memset(poly, 0, sizeof(uint64_t) * nw);
+            pset(poly, q); pset(poly, c); pset(poly, b); pset(poly, a); pset(poly, 0);
+            taps[0] = c; taps[1] = b; taps[2] = a;
+            return 5;
         }
     }
-    for (int c = 3; c < q; ++c)
-        for (int b = 2; b < c; ++b)
-            for (int a = 1; a < b; ++a) {
-                memset(p, 0, sizeof p);
-                pset(p, q); pset(p, c); pset(p, b); pset(p, a); pset(p, 0);
-                if (orc_is_irreducible(q, p)) {
-                    memcpy(poly, p, sizeof(uint64_t) * nw);
-                    taps[0] = c; taps[1] = b; taps[2] = a;
-                    return 5;
-                }
-            }
     return 0;
 }
 
@@ -301,7 +349,8 @@ int orc_extract(int q, int n_p, int m, const uint64_t *poly, const uint32_t *x, 
  * out must hold ceil(sum q_l / 32) words and is fully overwritten.
  * Returns 0, or -1 on bad arguments (some q_l outside 1..ORC_MAXQ).
  */
-int orc_extract_alg2(int n_p, int q1, int dq, int nblocks, const uint32_t *x, const uint32_t *y, uint32_t *out)
+int orc_extract_alg2(int n_p, int q1, int dq, int nblocks, const uint32_t *x, const uint32_t *y, uint32_t *out,
+                     const int *given_taps)
 {
     if (n_p < 1 || q1 < 1 || dq < 0 || nblocks < 0) return -1;
     if ((int64_t)q1 + (int64_t)dq * (nblocks > 0 ? nblocks - 1 : 0) > ORC_MAXQ) return -1;
@@ -314,7 +363,14 @@ int orc_extract_alg2(int n_p, int q1, int dq, int nblocks, const uint32_t *x, co
     for (int l = 0; l < nblocks; ++l) {
         uint64_t poly[ORC_W], z[ORC_W];
         int taps[3];
-        if (!orc_select_poly(ql, poly, taps)) return -1;
+        if (given_taps) {   /* P_{q_l} given as its taps (c, b, a; zero past a trinomial's) */
+            memset(poly, 0, sizeof poly);
+            pset(poly, ql); pset(poly, 0);
+            for (int t = 0; t < 3; ++t)
+                if (given_taps[3 * l + t]) pset(poly, given_taps[3 * l + t]);
+        } else if (!orc_select_poly(ql, poly, taps)) {
+            return -1;
+        }
         int ew = (ql + 63) / 64;
         uint64_t *xs = (uint64_t *)calloc((size_t)n_p * ew, sizeof(uint64_t));
         uint64_t *ys = (uint64_t *)calloc((size_t)n_p * ew, sizeof(uint64_t));

@@ -10,18 +10,28 @@
 // GPU form.  q_1 and Delta b are multiples of 16, so every q_l, every window
 // start (n * sum q_j) and every output offset (sum q_j) is a multiple of 16:
 // the streams and the output are arrays of 16-bit units and an element of
-// block l is k_l = q_l / 16 consecutive units.  One CTA per block: per group of
-// 32 elements, thread (source, u) slices unit u of the 32 elements
-// (slice<16>, elements i and i + 16 in word i: element e in slot e), then
-// the k_l^2 unit products S_u^x (x) S_v^y are spread over the threads, each a
-// 16 x 16 sliced Gram product whose 31 diagonal parities (POPC chain) are
-// XORed into the block's unreduced sum at bit 16 (u + v).  Thread 0 reduces
-// the (2 q_l - 1)-bit sum mod P bit by bit and writes the block's k_l units.
+// block l is k_l = q_l / 16 consecutive units (q_l <= 2048: k_l <= 128).
+// The product Z^(l) = sum_i x_i y_i splits into k_l^2 unit products per
+// element: with S_u = the slices of unit u over a group of 32 elements
+// (slice<16>, elements i and i + 16 in word i: element e in slot e), the
+// unreduced sum is XOR over groups and unit pairs (u, v) of the 31 diagonal
+// parities of the 16 x 16 sliced Gram product S_u^x (x) S_v^y, placed at bit
+// 16 (u + v).  Work items of at most kItemProducts unit pairs of one (block,
+// group) run as CTAs of one launch (alg2_products_kernel): each slices the
+// group's 2 k_l units into shared memory, computes its unit pairs, XORs the
+// parities into a shared sum and that into the block's sum in global memory.
+// A second launch (alg2_reduce_kernel, one CTA per block) reduces each sum mod
+// P_{q_l} word-parallel (the part at and above x^{q_l} folded back by the
+// taps until none is left) and writes the block's k_l output units.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdint>
+#include <mutex>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "qext_block.cuh"
@@ -38,86 +48,147 @@ struct Alg2Block {
     uint32_t taps[4];  // of P_{q_l} below x^{q_l}, descending, ending with 0
     uint64_t in_unit;  // first 16-bit unit of the window: n * sum_{j<l} q_j / 16
     uint64_t out_unit; // first output unit: sum_{j<l} q_j / 16
+    uint64_t zoff;     // first word of the block's unreduced sum (k + 1 words)
+};
+
+// A work item: unit pairs p in [p0, p1) (p = u k + v) of one group of one block.
+struct Alg2Item {
+    uint32_t block;
+    uint32_t group;
+    uint32_t p0, p1;
 };
 
 struct qext_alg2_plan {
     double delta;
     uint32_t b, q1, Delta, n_p, max_blocks;
     std::vector<Alg2Block> blocks;
+    std::vector<Alg2Item> items;
+    std::vector<uint32_t> item_prefix;  // items of blocks < l
+    uint64_t zwords = 0;
+    std::mutex mu;                      // the device tables, made on first use
     Alg2Block *d_blocks = nullptr;
-    int device = 0;
+    Alg2Item *d_items = nullptr;
+    uint32_t *d_z = nullptr;
+    int device = -1;
 };
 
 namespace {
 
 constexpr int kAlg2Threads = 256;
-constexpr uint32_t kMaxUnits = 16;  // q_l <= 256
+constexpr uint32_t kMaxUnits = 128;       // q_l <= 2048
+constexpr uint32_t kItemProducts = 2048;  // unit pairs per work item
 
 __global__ void __launch_bounds__(kAlg2Threads)
-    alg2_kernel(const Alg2Block *__restrict__ table, uint32_t n_p, const uint16_t *__restrict__ x,
-                const uint16_t *__restrict__ y, uint16_t *__restrict__ out) {
-    __shared__ uint32_t S[2][kMaxUnits][16];  // sliced units of the current group
-    __shared__ uint32_t z[kMaxUnits + 1];     // unreduced sum, 2 q_l - 1 bits
-    const Alg2Block blk = table[blockIdx.x];
+    alg2_products_kernel(const Alg2Item *__restrict__ items, const Alg2Block *__restrict__ table, uint32_t n_p,
+                         const uint16_t *__restrict__ x, const uint16_t *__restrict__ y, uint32_t *__restrict__ zg) {
+    __shared__ uint32_t S[2][kMaxUnits][16];  // sliced units of the group
+    __shared__ uint32_t z[kMaxUnits + 1];     // this item's share of the unreduced sum
+    const Alg2Item it = items[blockIdx.x];
+    const Alg2Block blk = table[it.block];
     const uint32_t k = blk.k, tid = threadIdx.x;
-    if (tid <= kMaxUnits) z[tid] = 0;
-    const uint32_t ngroups = (n_p + 31) / 32;
-    for (uint32_t g = 0; g < ngroups; ++g) {
-        __syncthreads();  // the previous group's products are done with S
-        if (tid < 2 * k) {
-            const uint32_t src = tid / k, u = tid % k;
-            const uint16_t *s = (src ? y : x) + blk.in_unit + u;
-            uint32_t w[16];
+    for (uint32_t i = tid; i <= k; i += blockDim.x) z[i] = 0;
+    if (tid < 2 * k) {
+        const uint32_t src = tid / k, u = tid % k;
+        const uint16_t *s = (src ? y : x) + blk.in_unit + u;
+        uint32_t w[16];
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const uint32_t ea = 32 * g + uint32_t(i), eb = ea + 16;
-                const uint32_t a = ea < n_p ? s[uint64_t(ea) * k] : 0u;
-                const uint32_t c = eb < n_p ? s[uint64_t(eb) * k] : 0u;
-                w[i] = a | (c << 16);
-            }
-            slice<16>(w);
-#pragma unroll
-            for (int i = 0; i < 16; ++i) S[src][u][i] = w[i];
+        for (int i = 0; i < 16; ++i) {
+            const uint32_t ea = 32 * it.group + uint32_t(i), eb = ea + 16;
+            const uint32_t a = ea < n_p ? s[uint64_t(ea) * k] : 0u;
+            const uint32_t c = eb < n_p ? s[uint64_t(eb) * k] : 0u;
+            w[i] = a | (c << 16);
         }
+        slice<16>(w);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) S[src][u][i] = w[i];
+    }
+    __syncthreads();
+    for (uint32_t p = it.p0 + tid; p < it.p1; p += blockDim.x) {
+        const uint32_t u = p / k, v = p % k;
+        uint32_t X[16], Y[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            X[i] = S[0][u][i];
+            Y[i] = S[1][v][i];
+        }
+        const uint32_t c = gram16_parities(X, Y);  // diagonal d at bit d (31 bits)
+        const uint32_t off = u + v;                 // in 16-bit units
+        if (off & 1u) {
+            atomicXor(&z[off >> 1], c << 16);
+            atomicXor(&z[(off >> 1) + 1], c >> 16);
+        } else {
+            atomicXor(&z[off >> 1], c);
+        }
+    }
+    __syncthreads();
+    for (uint32_t i = tid; i <= k; i += blockDim.x)
+        if (z[i]) atomicXor(&zg[blk.zoff + i], z[i]);
+}
+
+__global__ void __launch_bounds__(128)
+    alg2_reduce_kernel(const Alg2Block *__restrict__ table, const uint32_t *__restrict__ zg,
+                       uint16_t *__restrict__ out) {
+    __shared__ uint32_t z[kMaxUnits + 2], H[kMaxUnits + 2];
+    const Alg2Block blk = table[blockIdx.x];
+    const uint32_t q = blk.q, nz = blk.k + 1, tid = threadIdx.x;
+    const uint32_t qw = q >> 5, qb = q & 31u, nh = nz - qw;
+    for (uint32_t i = tid; i < nz; i += blockDim.x) z[i] = zg[blk.zoff + i];
+    // fold the part at and above x^q back by P's taps until none is left
+    // (each fold lowers the degree by q - c; bounded for safety)
+    for (int fold = 0; fold < 64; ++fold) {
         __syncthreads();
-        for (uint32_t p = tid; p < k * k; p += blockDim.x) {
-            const uint32_t u = p / k, v = p % k;
-            uint32_t X[16], Y[16];
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                X[i] = S[0][u][i];
-                Y[i] = S[1][v][i];
-            }
-            const uint32_t c = diagonal_chain<16>(X, Y) >> 1;  // diagonal d at bit d
-            const uint32_t off = u + v;                                   // in 16-bit units
-            if (off & 1u) {
-                atomicXor(&z[off >> 1], c << 16);
-                atomicXor(&z[(off >> 1) + 1], c >> 16);
-            } else {
-                atomicXor(&z[off >> 1], c);
-            }
+        bool any = false;
+        for (uint32_t i = tid; i < nh; i += blockDim.x) {
+            uint32_t v = z[qw + i] >> qb;
+            if (qb && qw + i + 1 < nz) v |= z[qw + i + 1] << (32 - qb);
+            H[i] = v;
+            any |= v != 0;
         }
-    }
-    __syncthreads();
-    if (tid == 0) {
-        // reduce mod P = x^q + sum taps: clear bits 2q-2 .. q from the top
-        const uint32_t q = blk.q;
-        for (uint32_t d = 2 * q - 2; d >= q; --d) {
-            if (!((z[d >> 5] >> (d & 31)) & 1u)) continue;
-            z[d >> 5] ^= 1u << (d & 31);
+        if (!__syncthreads_or(any)) break;
+        for (uint32_t i = tid; i < nz; i += blockDim.x) {
+            uint32_t v = z[i];
+            if (i > qw || (i == qw && qb == 0)) v = 0;
+            else if (i == qw) v &= (1u << qb) - 1u;
             for (uint32_t t = 0; t < blk.ntaps; ++t) {
-                const uint32_t e = d - q + blk.taps[t];
-                z[e >> 5] ^= 1u << (e & 31);
+                const uint32_t e = blk.taps[t], ew = e >> 5, eb = e & 31u;
+                if (i >= ew && i - ew < nh) v ^= H[i - ew] << eb;
+                if (eb && i >= ew + 1 && i - ew - 1 < nh) v ^= H[i - ew - 1] >> (32 - eb);
             }
+            z[i] = v;
         }
     }
     __syncthreads();
-    if (tid < k) out[blk.out_unit + tid] = uint16_t(z[tid >> 1] >> (16 * (tid & 1u)));
+    for (uint32_t u = tid; u < blk.k; u += blockDim.x) out[blk.out_unit + u] = uint16_t(z[u >> 1] >> (16 * (u & 1u)));
 }
 
 void release(qext_alg2_plan *p) {
-    if (p->d_blocks) cudaFree(p->d_blocks);
+    cudaFree(p->d_blocks);
+    cudaFree(p->d_items);
+    cudaFree(p->d_z);
     p->d_blocks = nullptr;
+    p->d_items = nullptr;
+    p->d_z = nullptr;
+}
+
+// The device tables (blocks, work items, sums), made on the first extraction
+// on the plan's device.
+int upload(qext_alg2_plan *p) {
+    std::lock_guard<std::mutex> lock(p->mu);
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return QEXT_E_CUDA;
+    if (p->d_blocks) return dev == p->device ? QEXT_OK : QEXT_E_STATE;
+    if (cudaMalloc(&p->d_blocks, sizeof(Alg2Block) * p->blocks.size()) != cudaSuccess ||
+        cudaMalloc(&p->d_items, sizeof(Alg2Item) * p->items.size()) != cudaSuccess ||
+        cudaMalloc(&p->d_z, sizeof(uint32_t) * p->zwords) != cudaSuccess ||
+        cudaMemcpy(p->d_blocks, p->blocks.data(), sizeof(Alg2Block) * p->blocks.size(), cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(p->d_items, p->items.data(), sizeof(Alg2Item) * p->items.size(), cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
+        release(p);
+        return QEXT_E_CUDA;
+    }
+    p->device = dev;
+    return QEXT_OK;
 }
 
 }  // namespace
@@ -144,29 +215,48 @@ int qext_alg2_plan_create(double delta, uint32_t b, uint32_t q1, uint32_t Delta,
     p->n_p = uint32_t(nn);
     p->max_blocks = max_blocks;
     p->blocks.resize(max_blocks);
+    // every block's field polynomial; the searches of distinct degrees run
+    // on parallel host threads (the largest degrees take the longest)
+    std::vector<int> ok(max_blocks, 0);
+    {
+        const unsigned hw = std::thread::hardware_concurrency();
+        const uint32_t nthreads = std::max(1u, std::min(max_blocks, hw ? hw : 4u));
+        std::atomic<uint32_t> next{0};
+        std::vector<std::thread> pool;
+        for (uint32_t t = 0; t < nthreads; ++t)
+            pool.emplace_back([&] {
+                for (uint32_t i; (i = next.fetch_add(1)) < max_blocks;) {
+                    const uint32_t l = max_blocks - 1 - i;  // largest degrees first
+                    Alg2Block &blk = p->blocks[l];
+                    blk.q = uint32_t(q1 + dq * l);
+                    blk.k = blk.q / 16;
+                    for (int j = 0; j < 4; ++j) blk.taps[j] = 0;
+                    ok[l] = qext::field_poly(blk.q, blk.taps, &blk.ntaps) ? 1 : 0;
+                }
+            });
+        for (auto &th : pool) th.join();
+    }
     uint64_t bits = 0, obits = 0;
     for (uint32_t l = 0; l < max_blocks; ++l) {
-        Alg2Block &blk = p->blocks[l];
-        blk.q = uint32_t(q1 + dq * l);
-        blk.k = blk.q / 16;
-        for (int i = 0; i < 4; ++i) blk.taps[i] = 0;
-        if (!qext::field_poly(blk.q, blk.taps, &blk.ntaps)) {
+        if (!ok[l]) {
             delete p;
             return QEXT_E_PARAM;
         }
+        Alg2Block &blk = p->blocks[l];
         blk.in_unit = bits / 16;
         blk.out_unit = obits / 16;
+        blk.zoff = p->zwords;
         bits += uint64_t(blk.q) * p->n_p;
         obits += blk.q;
+        p->zwords += blk.k + 1;
+        // work items: the block's k^2 unit pairs, per group of 32 elements
+        p->item_prefix.push_back(uint32_t(p->items.size()));
+        const uint32_t pairs = blk.k * blk.k, groups = (p->n_p + 31) / 32;
+        for (uint32_t g = 0; g < groups; ++g)
+            for (uint32_t p0 = 0; p0 < pairs; p0 += kItemProducts)
+                p->items.push_back(Alg2Item{l, g, p0, std::min(pairs, p0 + kItemProducts)});
     }
-    if (cudaGetDevice(&p->device) != cudaSuccess ||
-        cudaMalloc(&p->d_blocks, sizeof(Alg2Block) * max_blocks) != cudaSuccess ||
-        cudaMemcpy(p->d_blocks, p->blocks.data(), sizeof(Alg2Block) * max_blocks, cudaMemcpyHostToDevice) !=
-            cudaSuccess) {
-        release(p);
-        delete p;
-        return QEXT_E_CUDA;
-    }
+    p->item_prefix.push_back(uint32_t(p->items.size()));
     *out = p;
     return QEXT_OK;
 }
@@ -227,7 +317,14 @@ int qext_alg2_extract(const qext_alg2_plan *p, const uint16_t *x, const uint16_t
     if (!x || !y || !out || reinterpret_cast<uintptr_t>(x) % 2 || reinterpret_cast<uintptr_t>(y) % 2 ||
         reinterpret_cast<uintptr_t>(out) % 2)
         return QEXT_E_INVAL;
-    alg2_kernel<<<nblocks, kAlg2Threads, 0, reinterpret_cast<cudaStream_t>(stream)>>>(p->d_blocks, p->n_p, x, y, out);
+    const int rc = upload(const_cast<qext_alg2_plan *>(p));
+    if (rc != QEXT_OK) return rc;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const Alg2Block &last = p->blocks[nblocks - 1];
+    if (cudaMemsetAsync(p->d_z, 0, sizeof(uint32_t) * (last.zoff + last.k + 1), st) != cudaSuccess) return QEXT_E_CUDA;
+    alg2_products_kernel<<<p->item_prefix[nblocks], kAlg2Threads, 0, st>>>(p->d_items, p->d_blocks, p->n_p, x, y,
+                                                                          p->d_z);
+    alg2_reduce_kernel<<<nblocks, 128, 0, st>>>(p->d_blocks, p->d_z, out);
     return cudaGetLastError() == cudaSuccess ? QEXT_OK : QEXT_E_CUDA;
 }
 

@@ -4,35 +4,35 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <thread>
+#include <vector>
 
 #include "qext_internal.h"
 
 namespace {
 
-// Polynomials over F_2 of degree < 64*kWords, as little-endian word arrays.
-constexpr int kWords = 9;  // room for products of two degree-256 polynomials
+constexpr int kMaxQ = 2048;  // largest field degree (Algorithm 2's fields up to its 128th block at q_1 = Delta b = 16)
 
-struct BitPoly {
-    uint64_t w[kWords];
-    BitPoly() { std::memset(w, 0, sizeof w); }
+// Polynomials over F_2 as little-endian arrays of 64-bit words; kPW words
+// hold a square (degree <= 2 kMaxQ - 2) before reduction.
+constexpr int kPW = 2 * kMaxQ / 64 + 2;
+
+struct Poly {
+    uint64_t w[kPW];
+    Poly() { std::memset(w, 0, sizeof w); }
     void flip(int d) { w[d >> 6] ^= uint64_t(1) << (d & 63); }
     bool get(int d) const { return (w[d >> 6] >> (d & 63)) & 1u; }
     int degree() const {
-        for (int i = kWords - 1; i >= 0; --i)
+        for (int i = kPW - 1; i >= 0; --i)
             if (w[i]) return i * 64 + 63 - __builtin_clzll(w[i]);
         return -1;
     }
-    bool is_one() const {
-        if (w[0] != 1) return false;
-        for (int i = 1; i < kWords; ++i)
-            if (w[i]) return false;
-        return true;
-    }
-    // this ^= other << s  (s >= 0, result must fit)
-    void xor_shifted(const BitPoly &o, int s) {
-        int ws = s >> 6, bs = s & 63;
-        for (int i = kWords - 1; i >= ws; --i) {
+    // this ^= o * x^s (the shifted copy must fit)
+    void xor_shifted(const Poly &o, int s) {
+        const int ws = s >> 6, bs = s & 63;
+        for (int i = kPW - 1; i >= ws; --i) {
             uint64_t v = o.w[i - ws] << bs;
             if (bs && i - ws - 1 >= 0) v |= o.w[i - ws - 1] >> (64 - bs);
             w[i] ^= v;
@@ -40,66 +40,191 @@ struct BitPoly {
     }
 };
 
-// a mod m by long division from the top coefficient down.
-BitPoly poly_mod(BitPoly a, const BitPoly &m) {
+// A candidate field polynomial P = x^q + sum_t x^e[t] (e[] includes 0).
+struct Sparse {
+    int q;
+    int ne;
+    int e[4];
+    Poly dense() const {
+        Poly p;
+        p.flip(q);
+        for (int t = 0; t < ne; ++t) p.flip(e[t]);
+        return p;
+    }
+};
+
+// Squaring over F_2 spreads bit i to bit 2i: one table lookup per byte.
+struct SpreadTable {
+    uint16_t t[256];
+    SpreadTable() {
+        for (int v = 0; v < 256; ++v) {
+            uint16_t r = 0;
+            for (int i = 0; i < 8; ++i)
+                if (v & (1 << i)) r |= uint16_t(1u << (2 * i));
+            t[v] = r;
+        }
+    }
+};
+const SpreadTable kSpread;
+
+// r = a^2 (a has nw words, r gets 2 nw words; the rest of r is not touched)
+void square_words(const uint64_t *a, int nw, uint64_t *r) {
+    for (int i = 0; i < nw; ++i) {
+        uint64_t lo = 0, hi = 0;
+        for (int k = 0; k < 4; ++k) {
+            lo |= uint64_t(kSpread.t[(a[i] >> (8 * k)) & 0xFF]) << (16 * k);
+            hi |= uint64_t(kSpread.t[(a[i] >> (32 + 8 * k)) & 0xFF]) << (16 * k);
+        }
+        r[2 * i] = lo;
+        r[2 * i + 1] = hi;
+    }
+}
+
+// r mod P in place for a sparse P, by whole-word folds: with H = the part of
+// r at and above x^q, r = (r mod x^q) + H * (P - x^q), repeated until nothing
+// remains at or above x^q.  r has nw words.
+void reduce_sparse(uint64_t *r, int nw, const Sparse &P) {
+    const int q = P.q, qw = q >> 6, qb = q & 63;
+    uint64_t H[kPW];
+    for (;;) {
+        bool any = false;
+        const int hn = nw - qw;
+        for (int i = 0; i < hn; ++i) {
+            uint64_t v = r[qw + i] >> qb;
+            if (qb && qw + i + 1 < nw) v |= r[qw + i + 1] << (64 - qb);
+            H[i] = v;
+            any |= v != 0;
+        }
+        if (!any) return;
+        if (qb) r[qw] &= (uint64_t(1) << qb) - 1;
+        for (int i = (qb ? qw + 1 : qw); i < nw; ++i) r[i] = 0;
+        for (int t = 0; t < P.ne; ++t) {
+            const int s = P.e[t], ws = s >> 6, bs = s & 63;
+            for (int i = hn - 1; i >= 0; --i) {
+                if (!H[i]) continue;
+                const int d = i + ws;
+                if (d < nw) r[d] ^= H[i] << bs;
+                if (bs && d + 1 < nw) r[d + 1] ^= H[i] >> (64 - bs);
+            }
+        }
+    }
+}
+
+// a mod m by long division (dense m), for the gcds of Rabin's test.
+Poly poly_mod(Poly a, const Poly &m) {
     const int dm = m.degree();
     for (int d = a.degree(); d >= dm; d = a.degree()) a.xor_shifted(m, d - dm);
     return a;
 }
 
-// (a * a) mod m: squaring over F_2 spreads bit i to bit 2i.
-BitPoly square_mod(const BitPoly &a, const BitPoly &m) {
-    BitPoly s;
-    for (int d = a.degree(); d >= 0; --d)
-        if (a.get(d)) s.flip(2 * d);
-    return poly_mod(s, m);
-}
-
-BitPoly poly_gcd(BitPoly a, BitPoly b) {
+Poly poly_gcd(Poly a, Poly b) {
     while (b.degree() >= 0) {
-        BitPoly r = poly_mod(a, b);
+        Poly r = poly_mod(a, b);
         a = b;
         b = r;
     }
     return a;
 }
 
-// Ben-Or's test: a degree-q polynomial P is irreducible iff
-// gcd(P, x^(2^i) - x) = 1 for every i = 1 .. floor(q/2).
-bool ben_or_irreducible(const BitPoly &P, int q) {
-    if (P.degree() != q) return false;
+// Small irreducible polynomials f (degrees 2..8, bit masks), found by trial
+// division among themselves, with the powers x^k mod f for k < 2^deg(f) - 1:
+// x^(2^d - 1) = 1 mod f for an irreducible f of degree d other than x, so
+// x^e mod f = x^(e mod (2^d - 1)) mod f.
+struct SmallIrreducibles {
+    static constexpr int kMax = 80;
+    int n = 0;
+    uint32_t f[kMax];
+    uint32_t period[kMax];
+    uint16_t pw[kMax][255];
+    static int deg(uint32_t a) { return a ? 31 - __builtin_clz(a) : -1; }
+    static uint32_t mod_small(uint32_t a, uint32_t m) {
+        const int dm = deg(m);
+        for (int d = deg(a); d >= dm; d = deg(a)) a ^= m << (d - dm);
+        return a;
+    }
+    SmallIrreducibles() {
+        for (uint32_t m = 4; m < 512 && n < kMax; ++m) {      // degrees 2 .. 8
+            bool irr = (m & 1u) && mod_small(m, 3u) != 0;    // no factor x or x + 1
+            for (int i = 0; i < n && irr; ++i)
+                if (mod_small(m, f[i]) == 0) irr = false;
+            if (!irr) continue;
+            f[n] = m;
+            period[n] = (1u << deg(m)) - 1u;
+            uint32_t v = 1;
+            for (uint32_t k = 0; k < period[n]; ++k) {
+                pw[n][k] = uint16_t(v);
+                v = mod_small(v << 1, m);
+            }
+            ++n;
+        }
+    }
+};
+const SmallIrreducibles kSmall;
+
+// A factor of degree <= 8, by trial division: P mod f = sum of x^e mod f
+// over P's terms.  (Candidates have an odd number of terms and a constant
+// term, so neither x nor x + 1 divides them.)
+bool has_small_factor(const Sparse &P) {
+    if (P.q <= 8) return false;
+    for (int i = 0; i < kSmall.n; ++i) {
+        const uint32_t per = kSmall.period[i];
+        uint32_t r = kSmall.pw[i][uint32_t(P.q) % per];
+        for (int t = 0; t < P.ne; ++t) r ^= kSmall.pw[i][uint32_t(P.e[t]) % per];
+        if (r == 0) return true;
+    }
+    return false;
+}
+
+// Rabin's test: P of degree q is irreducible iff x^(2^q) = x mod P and
+// gcd(x^(2^(q/r)) - x, P) = 1 for every prime r dividing q.  The powers
+// x^(2^k) come from q squarings with sparse folds.
+bool rabin_irreducible(const Sparse &P) {
+    const int q = P.q;
     if (q == 1) return true;
-    BitPoly u;  // u = x^(2^i) mod P
-    u.flip(1);
-    for (int i = 1; i <= q / 2; ++i) {
-        u = square_mod(u, P);
-        BitPoly t = u;
-        t.flip(1);  // x^(2^i) - x
-        if (t.degree() < 0) return false;  // P divides x^(2^i) - x with i < q
-        if (!poly_gcd(P, t).is_one()) return false;
+    int primes[16], np = 0, rem = q;
+    for (int r = 2; r <= rem; ++r)
+        if (rem % r == 0) {
+            primes[np++] = r;
+            while (rem % r == 0) rem /= r;
+        }
+    const int nw = q / 64 + 1, sw = 2 * nw;
+    uint64_t u[kPW] = {0}, t[kPW];
+    u[0] = 2;  // x
+    Poly saved[16];
+    for (int k = 1; k <= q; ++k) {
+        std::memset(t, 0, sizeof(uint64_t) * sw);
+        square_words(u, nw, t);
+        reduce_sparse(t, sw, P);
+        std::memcpy(u, t, sizeof(uint64_t) * nw);
+        for (int i = 0; i < np; ++i)
+            if (k == q / primes[i]) std::memcpy(saved[i].w, u, sizeof(uint64_t) * nw);
+    }
+    if (u[0] != 2) return false;
+    for (int i = 1; i < nw; ++i)
+        if (u[i]) return false;
+    const Poly dense = P.dense();
+    for (int i = 0; i < np; ++i) {
+        Poly v = saved[i];
+        v.flip(1);  // x^(2^(q/r)) - x
+        if (v.degree() < 0) return false;
+        if (poly_gcd(dense, v).degree() != 0) return false;
     }
     return true;
 }
 
-BitPoly make_poly(int q, const int *exps, int nexp) {
-    BitPoly p;
-    p.flip(q);
-    for (int i = 0; i < nexp; ++i) p.flip(exps[i]);
-    p.flip(0);
-    return p;
-}
+bool irreducible(const Sparse &P) { return !has_small_factor(P) && rabin_irreducible(P); }
 
 // Minimum-weight irreducible polynomial, first in the order: trinomials
 // x^q + x^a + 1 by a; then pentanomials x^q + x^c + x^b + x^a + 1 by c, b, a.
 // Writes taps (descending, ending with the constant term's exponent 0).
-bool choose_field_poly(int q, uint32_t *taps, uint32_t *ntaps) {
+bool search_field_poly(int q, uint32_t *taps, uint32_t *ntaps) {
     if (q == 1) {  // F_2 itself: P = x, no reduction ever needed
         *ntaps = 0;
         return true;
     }
     for (int a = 1; a < q; ++a) {
-        const int e[1] = {a};
-        if (ben_or_irreducible(make_poly(q, e, 1), q)) {
+        const Sparse P{q, 2, {a, 0, 0, 0}};
+        if (irreducible(P)) {
             taps[0] = uint32_t(a);
             taps[1] = 0;
             *ntaps = 2;
@@ -109,8 +234,8 @@ bool choose_field_poly(int q, uint32_t *taps, uint32_t *ntaps) {
     for (int c = 3; c < q; ++c)
         for (int b = 2; b < c; ++b)
             for (int a = 1; a < b; ++a) {
-                const int e[3] = {c, b, a};
-                if (ben_or_irreducible(make_poly(q, e, 3), q)) {
+                const Sparse P{q, 4, {c, b, a, 0}};
+                if (irreducible(P)) {
                     taps[0] = uint32_t(c);
                     taps[1] = uint32_t(b);
                     taps[2] = uint32_t(a);
@@ -122,13 +247,43 @@ bool choose_field_poly(int q, uint32_t *taps, uint32_t *ntaps) {
     return false;
 }
 
+// The search's result per degree, kept for the process (a search at the
+// largest degrees takes a large fraction of a second).
+struct FieldCache {
+    std::mutex mu;
+    bool known[kMaxQ + 1] = {};
+    uint32_t taps[kMaxQ + 1][4];
+    uint32_t ntaps[kMaxQ + 1];
+};
+FieldCache g_fields;
+
+bool choose_field_poly(int q, uint32_t *taps, uint32_t *ntaps) {
+    if (q < 1 || q > kMaxQ) return false;
+    {
+        std::lock_guard<std::mutex> lock(g_fields.mu);
+        if (g_fields.known[q]) {
+            std::memcpy(taps, g_fields.taps[q], sizeof(uint32_t) * 4);
+            *ntaps = g_fields.ntaps[q];
+            return true;
+        }
+    }
+    uint32_t t[4] = {0, 0, 0, 0}, nt = 0;
+    if (!search_field_poly(q, t, &nt)) return false;
+    std::lock_guard<std::mutex> lock(g_fields.mu);
+    std::memcpy(g_fields.taps[q], t, sizeof t);
+    g_fields.ntaps[q] = nt;
+    g_fields.known[q] = true;
+    std::memcpy(taps, t, sizeof t);
+    *ntaps = nt;
+    return true;
+}
+
 // Theorem 3.1 for an n-bit block with min-entropy k (delta*q*n_p = k):
 // log2 eps_blk = log2 sqrt(3) - 1/4 - (k/4 - n/8) + 2q.
 double theorem31_log2_eps(uint32_t n, double k, uint32_t q) {
     return 0.5 * std::log2(3.0) - 0.25 - (k / 4.0 - double(n) / 8.0) + 2.0 * double(q);
 }
 
-constexpr int kMaxQ = 256;
 
 }  // namespace
 

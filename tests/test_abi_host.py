@@ -150,7 +150,7 @@ def test_alg2_plan_checks_without_gpu():
         qext.qext_alg2_plan_create(0.8, 12, 24, 1, 4)     # q_l not multiples of 16
     assert e.value.code == qext.QEXT_E_UNSUPPORTED
     with pytest.raises(qext.QextError) as e:
-        qext.qext_alg2_plan_create(0.8, 16, 16, 1, 17)    # q_16 = 272 > 256
+        qext.qext_alg2_plan_create(0.8, 16, 16, 1, 129)   # q_128 = 2064 > 2048
     assert e.value.code == qext.QEXT_E_UNSUPPORTED
     with pytest.raises(qext.QextError) as e:
         qext.qext_alg2_plan_create(0.8, 16, 0, 1, 4)

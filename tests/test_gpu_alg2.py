@@ -11,6 +11,7 @@ import torch
 import oracle
 from paper_2402_14607_gb300 import build as qbuild
 from paper_2402_14607_gb300 import qext, workloads
+from tests.conftest import read_golden
 from tests.gpu_util import host_words
 
 pytestmark = pytest.mark.gpu
@@ -63,8 +64,8 @@ def test_alg2_matches_oracle(delta, b, q1, Delta, nb, off):
     assert abs(info["log2_error_bound"] - oracle.alg2_log2_error(n_p, delta, q1, dq, nb)) < 1e-9
 
 
-def test_alg2_up_to_the_largest_field():
-    """q = 16 .. 256 in steps of 48 (the largest field built)."""
+def test_alg2_q_up_to_256_oracle_search():
+    """q = 16 .. 256 in steps of 48, the oracle searching every field itself."""
     p = qext.qext_alg2_plan_create(0.99, 16, 16, 3, 6)
     n_p = p.info["n_p"]
     total_in = n_p * sum(16 + 48 * l for l in range(6))
@@ -76,3 +77,38 @@ def test_alg2_up_to_the_largest_field():
     torch.cuda.synchronize()
     want = oracle.extract_alg2(n_p, 16, 48, 6, x, y).view(np.uint16)[:nout]
     assert (out.cpu().numpy().view(np.uint16) == want).all()
+
+
+def test_alg2_128_blocks_up_to_q_2048():
+    """A stream of real length: the paper's rate (delta = 10.74/16, so n = 71),
+    b = 16, q_1 = 16, Delta = 1: 128 blocks, q_l = 16 .. 2048 (2 x 9,378,816
+    input bits), every output bit against the oracle's Algorithm 2 with the
+    oracle-written field polynomials (tests/golden/alg2_field_polys.txt), run
+    twice on the same plan (the device sums are cleared per call)."""
+    golden = {int(q): tuple(int(t) for t in (c, b, a) if int(t))
+              for q, c, b, a in read_golden("alg2_field_polys.txt")}
+    p = qext.qext_alg2_plan_create(10.74 / 16, 16, 16, 1, 128)
+    n_p = p.info["n_p"]
+    assert n_p == 71
+    end = p.block(128)
+    assert end["in_bit"] == 71 * 16 * 128 * 129 // 2 and end["out_bit"] == 16 * 128 * 129 // 2
+    words = (end["in_bit"] + 31) // 32
+    x = workloads.random_words(91, words)
+    y = workloads.random_words(92, words)
+    nout = end["out_bit"] // 16
+    taps = [golden[16 * (l + 1)] for l in range(128)]
+    want = oracle.extract_alg2(n_p, 16, 16, 128, x, y, taps=taps).view(np.uint16)[:nout]
+    for _ in range(2):
+        out = torch.full((nout + 2,), -1, dtype=torch.int16, device="cuda")
+        qext.qext_alg2_extract(p, units(x), units(y), 128, out)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().view(np.uint16)
+        assert (got[nout:] == 0xFFFF).all(), "wrote past the output"
+        bad = np.nonzero(got[:nout] != want)[0]
+        assert bad.size == 0, "first mismatching output unit %d" % bad[0]
+    # a prefix of the plan's blocks: the first 40 outputs are the same
+    out = torch.full((nout + 2,), -1, dtype=torch.int16, device="cuda")
+    qext.qext_alg2_extract(p, units(x), units(y), 40, out)
+    torch.cuda.synchronize()
+    n40 = p.block(40)["out_bit"] // 16
+    assert (out.cpu().numpy().view(np.uint16)[:n40] == want[:n40]).all()

@@ -85,6 +85,7 @@ def test_theorem33_bound_chain(delta, b, q1, Delta):
 
 
 def test_rejects_fields_past_the_largest():
-    x = np.zeros(100000, np.uint32)
+    assert oracle.max_q() == 2048
+    x = np.zeros(1 << 22, np.uint32)
     with pytest.raises(ValueError):
-        oracle.extract_alg2(25, 16, 16, 20, x, x)   # q_20 = 320 > 256
+        oracle.extract_alg2(25, 2048, 16, 2, x, x)   # q_2 = 2064 > 2048
