@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(kThreads80, 6) extract_q80_kernel(const Q80Arg
                         Y[k] ^= cy[(64 + k) * kThreads80];
                     }
                 }
-                const uint64_t r = gram32_parities_3x16(X, Y);
+                const uint64_t r = gram32_parities(X, Y, s);
                 p11 ^= pr == 0 ? r : 0;
                 p12 ^= pr == 1 ? r : 0;
                 p01 ^= pr == 2 ? r : 0;
