@@ -15,7 +15,8 @@
 // with Pab = (xa + xb)(ya + yb), Paa = xa ya.  Each is accumulated over the
 // block's elements as sliced Gram-diagonal parities, 32 elements per group:
 // the 32-bit parts by a 32 x 32 transpose (element e in slot e) and
-// gram32_parities_3x16, x2 by slice<16> with elements k and k+16 in word k (which
+// gram32_parities (two more Karatsuba levels, parities in byte fields), x2 by
+// slice<16> with elements k and k+16 in word k (which
 // also puts element e in slot e, so x0 + x2 is a slot-wise XOR of slices).
 // Parities are linear, so groups and Karatsuba parts combine after the
 // POPCs; the 159-bit sum is reduced mod P once per block.

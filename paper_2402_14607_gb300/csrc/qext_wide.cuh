@@ -1,6 +1,6 @@
 // Device helpers of the wide fields: q = 64 (elements are word pairs) and
-// the 32 x 32 / 16 x 16 sliced Gram products by Karatsuba levels and POPC
-// diagonal chains that q = 64 and q = 80 share.
+// the 32 x 32 / 16 x 16 sliced Gram products by Karatsuba levels and diagonal
+// parities that q = 64, q = 80 and Algorithm 2 share.
 #pragma once
 
 #include "qext_block.cuh"
@@ -47,28 +47,6 @@ __device__ __forceinline__ uint32_t gram16_parities(uint32_t *X, uint32_t *Y) {
     const uint32_t c = diagonal_chain<8>(X, Y);
     return lop_xor3(a >> 17, b >> 1, lop_xor3(a, b, c) >> 9);
 }
-
-// Parities of the 63 diagonals of a sliced 32 x 32 Gram product, by two
-// Karatsuba levels over the slice index (32 -> 16 + 16 -> 8 + 8) and diagonal
-// chains: nine 8 x 8 products instead of one 32 x 32, combined as three
-// 16 x 16 products (135 diagonal parities; the q = 80 kernel, latency-bound,
-// measured faster with this form than with gram32_parities).  X and Y are
-// overwritten.  Bit d of the result = parity of diagonal d.
-__device__ __forceinline__ uint64_t gram32_parities_3x16(uint32_t (&X)[32], uint32_t (&Y)[32]) {
-    // sums of the halves first (gram16_parities overwrites its operands)
-    uint32_t XS[16], YS[16];
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-        XS[j] = X[j] ^ X[j + 16];
-        YS[j] = Y[j] ^ Y[j + 16];
-    }
-    const uint64_t A = gram16_parities(X, Y);
-    const uint64_t B = gram16_parities(X + 16, Y + 16);
-    const uint64_t C = gram16_parities(XS, YS);
-    const uint64_t M = A ^ B ^ C;
-    return A ^ (M << 16) ^ (B << 32);
-}
-
 
 // Parities of the diagonals D0 .. D1-1 of sum_b t^(S b) (X_b x Y_b), where
 // X_b = X[O0 + OSTEP b .. + 8) and likewise Y_b: diagonal d takes the pairs
