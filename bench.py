@@ -35,7 +35,7 @@ METRIC = "extracted Gbps on 1 GB300 (bit-exact), %HBM roofline; serving p50/p99 
 UNIT = "Gbps"
 L2_BYTES = 126 << 20
 # kernel sources whose hash must match a profile's capture for its traffic figure to be reported
-PACKED16_SOURCES = ["qext_extract_raw.cu", "qext_block.cuh", "qext_device.cuh"]
+PACKED16_SOURCES = ["qext_extract_packed.cu", "qext_block.cuh", "qext_device.cuh"]
 RAW_SOURCES = ["qext_extract_raw.cu", "qext_block.cuh", "qext_device.cuh"]
 
 

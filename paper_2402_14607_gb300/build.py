@@ -16,7 +16,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libqext.so")
-SOURCES = ["qext_plan.cpp", "qext_api.cpp", "qext_extract.cu", "qext_extract_raw.cu", "qext_extract_q80.cu", "qext_fused.cu", "qext_ingest.cu", "qext_stream.cu",
+SOURCES = ["qext_plan.cpp", "qext_api.cpp", "qext_extract.cu", "qext_extract_raw.cu", "qext_extract_packed.cu", "qext_extract_q80.cu", "qext_fused.cu", "qext_ingest.cu", "qext_stream.cu",
            "qext_batch.cu", "qext_server.cu", "qext_pipeline.cu", "qext_alg2.cu", "qext_monitor.cu"]
 HEADERS = [os.path.join(CSRC, "qext_internal.h"), os.path.join(CSRC, "qext_device.cuh"),
            os.path.join(CSRC, "qext_block.cuh"), os.path.join(CSRC, "qext_wide.cuh"),
