@@ -178,6 +178,17 @@ __device__ __forceinline__ void store_warp_wide(const uint32_t (&v)[3], uint64_t
     }
 }
 
+// Truncation of an 80-bit value (three words) to its low m bits.
+__device__ __forceinline__ void truncate80(uint32_t (&v)[3], uint32_t m) {
+    if (m < 64) {
+        v[2] = 0;
+        v[1] = m <= 32 ? 0u : v[1] & uint32_t(mask_m(m - 32));
+        if (m < 32) v[0] &= uint32_t(mask_m(m));
+    } else if (m < 80) {
+        v[2] &= uint32_t(mask_m(m - 64));
+    }
+}
+
 __global__ void __launch_bounds__(kThreads80, 6) extract_q80_kernel(const Q80Args a) {
     // per thread: 80 sliced words of each source, interleaved across threads
     // (word k of thread t at k * kThreads80 + t: conflict-free)
@@ -279,20 +290,244 @@ __global__ void __launch_bounds__(kThreads80, 6) extract_q80_kernel(const Q80Arg
         uint64_t r0;
         uint32_t r1;
         reduce_mod_p80(z0, z1, z2, s, r0, r1);
-        // truncate to m bits
         uint32_t v[3] = {uint32_t(r0), uint32_t(r0 >> 32), r1};
-        if (s.m < 64) {
-            v[2] = 0;
-            v[1] = s.m <= 32 ? 0u : v[1] & uint32_t(mask_m(s.m - 32));
-            if (s.m < 32) v[0] &= uint32_t(mask_m(s.m));
-        } else if (s.m < 80) {
-            v[2] &= uint32_t(mask_m(s.m - 64));
-        }
+        truncate80(v, s.m);
         if (blk >= s.nblocks) v[0] = v[1] = v[2] = 0;
         if (s.m <= 64)
             store_warp(uint64_t(v[0]) | (uint64_t(v[1]) << 32), base, s.nblocks, s.m, s.out);
         else
             store_warp_wide(v, base, s.nblocks, s.m, s.out);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Blocks in lanes (the default for n_p up to the shared-memory limit).  A CTA
+// takes tiles of 32 consecutive blocks; bit b of every sliced word belongs to
+// block b of the tile, so one AND-XOR serves 32 blocks and the Gram sums
+// need no parities: word k of the accumulated product is coefficient k of
+// the 32 blocks' unreduced sums.  An element is split into five 16-bit
+// column groups G_0..G_4 (x = sum_c G_c u^c, u = t^16) and multiplied by
+// the generalised Karatsuba formula over them (Weimerskirch and Paar,
+// "Generalizations of the Karatsuba Algorithm for Efficient
+// Implementations", 2006):
+//     x y = sum_c P_cc u^2c + sum_{c<d} (P_cd + P_cc + P_dd) u^(c+d),
+//     P_cd = (G_c(x) + G_d(x)) (G_c(y) + G_d(y)),
+// fifteen 16 x 16 sliced products, each one Karatsuba level over 8-word
+// halves.  The products are linear in their accumulators, so every thread
+// keeps one product's accumulators across all elements of the tile and the
+// recombination (fifteen products into the 159-bit sum) runs once per tile.
+//
+// Per tile: the 32 blocks of both sources arrive by one bulk copy each (or
+// plain loads for a ragged last tile or unaligned sources); elements are
+// processed in chunks of kChunk80: 5 x 2 x kChunk80 threads slice one column
+// group of one element of one source each (32 halfword rows -> 16 words),
+// then 15 x kChunk80 threads multiply, thread (slot e, product u) taking
+// element e of the chunk.  The next tile's copy is issued once the last
+// chunk is sliced.  At the end of the tile the accumulators are summed over
+// the slots, recombined into the 159 coefficient words, transposed back to
+// one value per block and reduced mod P by warp 0.
+// ---------------------------------------------------------------------------
+constexpr int kThreadsLanes = 128;
+constexpr uint32_t kChunk80 = 8;          // elements per chunk
+constexpr uint32_t kProducts80 = 15;      // P_cd, c <= d < 5
+constexpr uint32_t kVecStride = 20;       // words between column-group vectors (distinct bank groups)
+constexpr uint32_t kSliceStride = 5 * kVecStride;  // words per (element, source)
+constexpr uint32_t kRedWords = (kThreadsLanes / 32) * kProducts80 * 31;  // per-warp partial products
+constexpr uint32_t kWorkWords =           // slices, or (aliased) the tile's recombination buffers
+    (2 * kChunk80 * kSliceStride > kRedWords + 160 + 160) ? 2 * kChunk80 * kSliceStride : kRedWords + 160 + 160;
+
+// Products 0..4 are P_cc, 5..14 the pairs c < d in lexicographic order.
+__host__ __device__ constexpr uint32_t product_lo(uint32_t u) {
+    return u < 5 ? u : u < 9 ? 0 : u < 12 ? 1 : u < 14 ? 2 : 3;
+}
+__host__ __device__ constexpr uint32_t product_hi(uint32_t u) {
+    return u < 5 ? u : u < 9 ? u - 4 : u < 12 ? u - 7 : u < 14 ? u - 9 : 4;
+}
+
+struct LanesArgs {
+    StreamArgs s;
+    uint32_t n_p;
+    uint32_t in_words;    // words of one source per tile (= n)
+    uint32_t y_offset;    // words from the x tile to the y tile in shared memory
+    int bulk;             // sources 16-byte aligned: whole tiles arrive by bulk copy
+    uint64_t src_words;   // readable words of each source, ceil(nblocks n / 32)
+};
+
+__global__ void __launch_bounds__(kThreadsLanes, 4) extract_q80_lanes_kernel(const LanesArgs a) {
+    extern __shared__ __align__(16) uint32_t smem80[];
+    __shared__ __align__(8) uint64_t bar;
+    const StreamArgs &s = a.s;
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    uint32_t *const tin = smem80;                                  // x tile, then y tile
+    uint32_t *const work = smem80 + a.y_offset + a.in_words;       // slices / recombination
+    const uint64_t ntiles = (s.nblocks + 31) / 32;
+    const uint32_t n = a.in_words, hw_row = n / 16;                // halfwords per block row
+    auto full_tile = [&](uint64_t t) { return a.bulk && 32 * (t + 1) <= s.nblocks; };
+    auto issue = [&](uint64_t t) {
+        mbar_expect_tx(&bar, 8u * n);
+        tma_load_1d(tin, s.x + t * n, 4u * n, &bar);
+        tma_load_1d(tin + a.y_offset, s.y + t * n, 4u * n, &bar);
+    };
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    pdl_prologue();
+    uint64_t t = blockIdx.x;
+    if (tid == 0 && t < ntiles && full_tile(t)) issue(t);
+    const uint32_t u = tid & 15u, slot = tid >> 4;
+    const uint32_t ca = product_lo(u < kProducts80 ? u : 0), cb = product_hi(u < kProducts80 ? u : 0);
+    const uint32_t pmask = ca == cb ? 0u : ~0u;
+    for (uint32_t phase = 0; t < ntiles; t += gridDim.x) {
+        if (full_tile(t)) {
+            const bool ok = mbar_wait_bounded(&bar, phase & 1u);
+            ++phase;
+            if (__syncthreads_or(!ok)) {
+                if (tid == 0) {
+                    record_status(s.status, QEXT_E_TIMEOUT);
+                    mbar_wait_bounded(&bar, (phase - 1) & 1u);  // let the copies in flight land
+                }
+                return;
+            }
+        } else {
+            // ragged last tile or unaligned sources: plain loads, zeros past the streams
+            for (uint32_t i = tid; i < n; i += kThreadsLanes) {
+                const uint64_t w = t * n + i;
+                tin[i] = w < a.src_words ? s.x[w] : 0u;
+                tin[a.y_offset + i] = w < a.src_words ? s.y[w] : 0u;
+            }
+            __syncthreads();
+        }
+        uint32_t D[23], C[15];
+#pragma unroll
+        for (int k = 0; k < 23; ++k) D[k] = 0;
+#pragma unroll
+        for (int k = 0; k < 15; ++k) C[k] = 0;
+        for (uint32_t c0 = 0; c0 < a.n_p; c0 += kChunk80) {
+            // slicing: job (element e, source src, column group g)
+            if (tid < 10 * kChunk80) {
+                const uint32_t e = tid / 10, src = (tid / 5) & 1u, g = tid % 5;
+                if (c0 + e < a.n_p) {
+                    const uint16_t *const rows =
+                        reinterpret_cast<const uint16_t *>(tin + src * a.y_offset) + 5 * (c0 + e) + g;
+                    uint32_t W[16];
+#pragma unroll
+                    for (int k = 0; k < 16; ++k)
+                        W[k] = __byte_perm(rows[k * hw_row], rows[(k + 16) * hw_row], 0x5410);
+                    slice<16>(W);  // word j: bit j of the group, row b in bit b
+                    uint32_t *const dst = work + (2 * e + src) * kSliceStride + kVecStride * g;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        *reinterpret_cast<uint4 *>(dst + 4 * k) = make_uint4(W[4 * k], W[4 * k + 1], W[4 * k + 2], W[4 * k + 3]);
+                }
+            }
+            __syncthreads();
+            if (c0 + kChunk80 >= a.n_p && tid == 0 && t + gridDim.x < ntiles && full_tile(t + gridDim.x))
+                issue(t + gridDim.x);  // every row of this tile is sliced: the tile buffer is free
+            if (u < kProducts80 && c0 + slot < a.n_p) {
+                const uint32_t *const ex = work + 2 * slot * kSliceStride, *const ey = ex + kSliceStride;
+                uint32_t X[16], Y[16];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const uint4 xa = lds4(ex + kVecStride * ca + 4 * k), xb = lds4(ex + kVecStride * cb + 4 * k);
+                    const uint4 ya = lds4(ey + kVecStride * ca + 4 * k), yb = lds4(ey + kVecStride * cb + 4 * k);
+                    X[4 * k] = lop_and_xor(xb.x, pmask, xa.x);
+                    X[4 * k + 1] = lop_and_xor(xb.y, pmask, xa.y);
+                    X[4 * k + 2] = lop_and_xor(xb.z, pmask, xa.z);
+                    X[4 * k + 3] = lop_and_xor(xb.w, pmask, xa.w);
+                    Y[4 * k] = lop_and_xor(yb.x, pmask, ya.x);
+                    Y[4 * k + 1] = lop_and_xor(yb.y, pmask, ya.y);
+                    Y[4 * k + 2] = lop_and_xor(yb.z, pmask, ya.z);
+                    Y[4 * k + 3] = lop_and_xor(yb.w, pmask, ya.w);
+                }
+                // D += X_L Y_L + t^8 X_H Y_H,  C += (X_L + X_H)(Y_L + Y_H)
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+#pragma unroll
+                    for (int l = 0; l < 8; ++l) {
+                        D[j + l] = lop_and_xor(X[j], Y[l], D[j + l]);
+                        D[j + l + 8] = lop_and_xor(X[8 + j], Y[8 + l], D[j + l + 8]);
+                    }
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    X[j] ^= X[8 + j];
+                    Y[j] ^= Y[8 + j];
+                }
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+#pragma unroll
+                    for (int l = 0; l < 8; ++l) C[j + l] = lop_and_xor(X[j], Y[l], C[j + l]);
+            }
+            __syncthreads();
+        }
+        // the product's 31 coefficient words: R = D (1 + t^8) + t^8 C, summed
+        // over the slots (two per warp by a shuffle, then over the warps)
+        uint32_t *const red = work, *const zw = work + kRedWords, *const ow = zw + 160;
+        {
+            uint32_t R[31];
+#pragma unroll
+            for (int k = 0; k < 31; ++k) {
+                uint32_t r = k < 23 ? D[k] : 0u;
+                if (k >= 8) r ^= D[k - 8] ^ (k - 8 < 15 ? C[k - 8] : 0u);
+                R[k] = r ^ __shfl_xor_sync(0xffffffffu, r, 16);
+            }
+            if (lane < kProducts80) {
+#pragma unroll
+                for (int k = 0; k < 31; ++k) red[(warp * kProducts80 + lane) * 31 + k] = R[k];
+            }
+        }
+        __syncthreads();
+        for (uint32_t i = tid; i < kProducts80 * 31; i += kThreadsLanes) {
+            uint32_t r = red[i];
+#pragma unroll
+            for (uint32_t w = 1; w < kThreadsLanes / 32; ++w) r ^= red[w * kProducts80 * 31 + i];
+            red[i] = r;
+        }
+        __syncthreads();
+        // z_k: P_cc at u^2c and at u^(c+d) for every d != c; P_cd (c < d) at u^(c+d)
+        for (uint32_t k = tid; k < 160; k += kThreadsLanes) {
+            uint32_t z = 0;
+#pragma unroll
+            for (uint32_t p = 0; p < kProducts80; ++p) {
+                const uint32_t c = product_lo(p), d = product_hi(p);
+#pragma unroll
+                for (uint32_t e = 0; e < 5; ++e) {
+                    // offsets: for P_cc, 32c (e == c) and 16(c + e) (e != c); for P_cd, 16(c + d) once (e == 0)
+                    const uint32_t off = c == d ? 16 * (c + e) : 16 * (c + d);
+                    if ((c == d || e == 0) && k - off < 31u) z ^= red[p * 31 + (k - off)];
+                }
+            }
+            zw[k] = z;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            if (lane < 5) {
+                uint32_t W[32];
+#pragma unroll
+                for (int e = 0; e < 32; ++e) W[e] = zw[32 * lane + e];
+                slice<32>(W);  // word b: coefficients 32 lane .. 32 lane + 31 of block b
+#pragma unroll
+                for (int b = 0; b < 32; ++b) ow[lane * 32 + b] = W[b];
+            }
+            __syncwarp();
+            const uint64_t z0 = ow[lane] | (uint64_t(ow[32 + lane]) << 32);
+            const uint64_t z1 = ow[64 + lane] | (uint64_t(ow[96 + lane]) << 32);
+            const uint64_t z2 = ow[128 + lane];
+            uint64_t r0;
+            uint32_t r1;
+            reduce_mod_p80(z0, z1, z2, s, r0, r1);
+            uint32_t v[3] = {uint32_t(r0), uint32_t(r0 >> 32), r1};
+            truncate80(v, s.m);
+            const uint64_t base = 32 * t;
+            if (base + lane >= s.nblocks) v[0] = v[1] = v[2] = 0;
+            if (s.m <= 64)
+                store_warp(uint64_t(v[0]) | (uint64_t(v[1]) << 32), base, s.nblocks, s.m, s.out);
+            else
+                store_warp_wide(v, base, s.nblocks, s.m, s.out);
+        }
+        // the next tile's first slicing overwrites the buffers warp 0 reads:
+        // the barrier after its copy (or its loads) orders them
     }
 }
 
@@ -304,36 +539,68 @@ int launch_extract_q80(const qext_plan *p, const uint32_t *x, const uint32_t *y,
                        qext_cuda_stream stream) {
     if (p->q != 80) return QEXT_E_UNSUPPORTED;
     if (nblocks == 0) return QEXT_OK;
-    static DeviceSlots grid_caps;
+    static DeviceSlots grid_caps, smem_optin, attr_set;
     const int dev = current_device();
     if (dev < 0) return QEXT_E_CUDA;
-    const int grid_cap = grid_caps.get(dev, [dev] {
+    const int sms = sm_count(dev);
+    if (sms <= 0) return QEXT_E_CUDA;
+    const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    StreamArgs s;
+    s.x = x;
+    s.y = y;
+    s.out = out;
+    s.nblocks = nblocks;
+    s.wpb = 0;  // blocks need not be whole words
+    s.m = p->m;
+    s.ntaps = p->ntaps;
+    for (int i = 0; i < 4; ++i) s.taps[i] = p->taps[i];
+    s.set_multipliers();
+    s.status = device_status_ptr();
+
+    // blocks in lanes while two tiles of 32 blocks and the work buffers fit
+    const int optin = smem_optin.get(dev, [dev] {
+        int v = 0;
+        return cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess ? v : 0;
+    });
+    if (optin <= 0) return QEXT_E_CUDA;
+    const uint64_t n = 80ull * p->n_p;
+    const uint64_t lanes_smem = (2 * n + 4 + kWorkWords) * 4;
+    if (lanes_smem + 1024 <= uint64_t(optin)) {
+        if (attr_set.get(dev, [optin] {
+                return cudaFuncSetAttribute(extract_q80_lanes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            optin - 1024) == cudaSuccess ? 1 : 0;
+            }) <= 0)
+            return QEXT_E_CUDA;
         int occ = 0;
-        const int sms = sm_count(dev);
-        if (sms <= 0 || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, extract_q80_kernel, kThreads80, 0) !=
-                            cudaSuccess)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, extract_q80_lanes_kernel, kThreadsLanes,
+                                                          size_t(lanes_smem)) != cudaSuccess)
+            return QEXT_E_CUDA;
+        LanesArgs a;
+        a.s = s;
+        a.n_p = p->n_p;
+        a.in_words = uint32_t(n);
+        a.y_offset = uint32_t(n) + 4;  // 16 bytes between the tiles: the slicing reads spread over the banks
+        a.bulk = (reinterpret_cast<uintptr_t>(x) % 16 == 0 && reinterpret_cast<uintptr_t>(y) % 16 == 0) ? 1 : 0;
+        a.src_words = (nblocks * n + 31) / 32;
+        const uint64_t ntiles = (nblocks + 31) / 32, cap = uint64_t(sms) * uint64_t(occ > 0 ? occ : 1);
+        const int grid = int(ntiles < cap ? ntiles : cap);
+        return launch_pdl(extract_q80_lanes_kernel, grid, kThreadsLanes, size_t(lanes_smem), st, a);
+    }
+
+    const int grid_cap = grid_caps.get(dev, [sms] {
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, extract_q80_kernel, kThreads80, 0) != cudaSuccess)
             return 0;
         return sms * (occ > 0 ? occ : 1);
     });
     if (grid_cap <= 0) return QEXT_E_CUDA;
     Q80Args a;
-    a.s.x = x;
-    a.s.y = y;
-    a.s.out = out;
-    a.s.nblocks = nblocks;
-    a.s.wpb = 0;  // blocks need not be whole words
-    a.s.m = p->m;
-    a.s.ntaps = p->ntaps;
-    for (int i = 0; i < 4; ++i) {
-        a.s.taps[i] = p->taps[i];
-    }
-    a.s.set_multipliers();
-    a.s.status = device_status_ptr();
+    a.s = s;
     a.n_p = p->n_p;
     a.zero = 0;
     const uint64_t ctas = (nblocks + kThreads80 - 1) / kThreads80;
     const int grid = int(ctas < uint64_t(grid_cap) ? ctas : uint64_t(grid_cap));
-    return launch_pdl(extract_q80_kernel, grid, kThreads80, 0, reinterpret_cast<cudaStream_t>(stream), a);
+    return launch_pdl(extract_q80_kernel, grid, kThreads80, 0, st, a);
 }
 
 }  // namespace qext

@@ -42,13 +42,16 @@ def run(plan, nblocks, seed, off=0):
     assert (got[:nout] == want).all(), (info, nblocks)
 
 
-@pytest.mark.parametrize("nblocks,off", [(1, 0), (2, 1), (31, 0), (33, 3), (97, 1), (1000, 0)])
+@pytest.mark.parametrize("nblocks,off", [(1, 0), (2, 1), (31, 0), (32, 0), (33, 3), (97, 0), (97, 1), (1000, 0)])
 def test_paper_parameters_match_oracle(nblocks, off):
     run(paper_plan(), nblocks, 100 + nblocks, off)
 
 
-@pytest.mark.parametrize("n_p,m", [(25, 0), (32, 0), (33, 64), (40, 71), (64, 33), (71, 16), (96, 7), (71, 79)])
+@pytest.mark.parametrize("n_p,m", [(25, 0), (32, 0), (33, 64), (40, 71), (64, 33), (71, 16), (96, 7), (71, 79),
+                                   (340, 0), (400, 50)])
 def test_other_shapes_and_truncations(n_p, m):
+    """n_p = 340: the largest tiles of 32 blocks (one CTA per SM); n_p = 400:
+    too large for them, one block per thread."""
     run(plan_for(80, n_p, m), 301, 7 * n_p + m)
 
 
