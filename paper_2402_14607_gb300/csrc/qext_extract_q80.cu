@@ -344,29 +344,53 @@ __host__ __device__ constexpr uint32_t product_hi(uint32_t u) {
     return u < 5 ? u : u < 9 ? u - 4 : u < 12 ? u - 7 : u < 14 ? u - 9 : 4;
 }
 
+// Products placed at u^m in x y (m = 0 .. 8): P_cd with c < d, c + d = m, and
+// P_cc with 0 <= m - c <= 4 (at u^2c, and at u^(c+e) for every e != c).
+__constant__ uint8_t kAtOffset[9][7] = {{0},          {0, 1, 5},          {0, 1, 2, 6},    {0, 1, 2, 3, 7, 9},
+                                        {0, 1, 2, 3, 4, 8, 10}, {1, 2, 3, 4, 11, 12}, {2, 3, 4, 13}, {3, 4, 14},
+                                        {4}};
+__constant__ uint8_t kAtOffsetLen[9] = {1, 3, 4, 6, 7, 6, 4, 3, 1};
+
+// 32 x 32 bit transpose across a warp: lane e holds row e on entry, column
+// e on return (bit b of lane e's result = bit e of lane b's row), by five
+// exchange stages between lanes G apart.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t w, uint32_t lane) {
+    constexpr uint32_t kLow[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        const uint32_t G = 16u >> i, M = kLow[i];
+        const uint32_t v = __shfl_xor_sync(0xffffffffu, w, int(G));
+        w = (lane & G) ? lop_select(v >> G, w, M) : lop_select(w, v << G, M);
+    }
+    return w;
+}
+
 struct LanesArgs {
     StreamArgs s;
     uint32_t n_p;
-    uint32_t in_words;    // words of one source per tile (= n)
-    uint32_t y_offset;    // words from the x tile to the y tile in shared memory
     int bulk;             // sources 16-byte aligned: whole tiles arrive by bulk copy
     uint64_t src_words;   // readable words of each source, ceil(nblocks n / 32)
 };
 
+// NP > 0: n_p fixed at compile time (the row strides of the slicing become
+// immediate offsets); NP = 0: any n_p.
+template <uint32_t NP>
 __global__ void __launch_bounds__(kThreadsLanes, 4) extract_q80_lanes_kernel(const LanesArgs a) {
     extern __shared__ __align__(16) uint32_t smem80[];
     __shared__ __align__(8) uint64_t bar;
     const StreamArgs &s = a.s;
     const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
-    uint32_t *const tin = smem80;                                  // x tile, then y tile
-    uint32_t *const work = smem80 + a.y_offset + a.in_words;       // slices / recombination
+    const uint32_t n_p = NP ? NP : a.n_p, n = 80 * n_p, hw_row = 5 * n_p;  // hw_row: halfwords per block row
+    // y tile 16 bytes past the x tile (the slicing reads spread over the banks)
+    const uint32_t y_off = n + 4;
+    uint32_t *const tin = smem80;               // x tile, then y tile
+    uint32_t *const work = smem80 + y_off + n;  // slices / recombination
     const uint64_t ntiles = (s.nblocks + 31) / 32;
-    const uint32_t n = a.in_words, hw_row = n / 16;                // halfwords per block row
     auto full_tile = [&](uint64_t t) { return a.bulk && 32 * (t + 1) <= s.nblocks; };
     auto issue = [&](uint64_t t) {
         mbar_expect_tx(&bar, 8u * n);
         tma_load_1d(tin, s.x + t * n, 4u * n, &bar);
-        tma_load_1d(tin + a.y_offset, s.y + t * n, 4u * n, &bar);
+        tma_load_1d(tin + y_off, s.y + t * n, 4u * n, &bar);
     };
     if (tid == 0) {
         mbar_init(&bar, 1);
@@ -395,7 +419,7 @@ __global__ void __launch_bounds__(kThreadsLanes, 4) extract_q80_lanes_kernel(con
             for (uint32_t i = tid; i < n; i += kThreadsLanes) {
                 const uint64_t w = t * n + i;
                 tin[i] = w < a.src_words ? s.x[w] : 0u;
-                tin[a.y_offset + i] = w < a.src_words ? s.y[w] : 0u;
+                tin[y_off + i] = w < a.src_words ? s.y[w] : 0u;
             }
             __syncthreads();
         }
@@ -404,13 +428,13 @@ __global__ void __launch_bounds__(kThreadsLanes, 4) extract_q80_lanes_kernel(con
         for (int k = 0; k < 23; ++k) D[k] = 0;
 #pragma unroll
         for (int k = 0; k < 15; ++k) C[k] = 0;
-        for (uint32_t c0 = 0; c0 < a.n_p; c0 += kChunk80) {
+        for (uint32_t c0 = 0; c0 < n_p; c0 += kChunk80) {
             // slicing: job (element e, source src, column group g)
             if (tid < 10 * kChunk80) {
                 const uint32_t e = tid / 10, src = (tid / 5) & 1u, g = tid % 5;
-                if (c0 + e < a.n_p) {
+                if (c0 + e < n_p) {
                     const uint16_t *const rows =
-                        reinterpret_cast<const uint16_t *>(tin + src * a.y_offset) + 5 * (c0 + e) + g;
+                        reinterpret_cast<const uint16_t *>(tin + src * y_off) + 5 * (c0 + e) + g;
                     uint32_t W[16];
 #pragma unroll
                     for (int k = 0; k < 16; ++k)
@@ -423,9 +447,9 @@ __global__ void __launch_bounds__(kThreadsLanes, 4) extract_q80_lanes_kernel(con
                 }
             }
             __syncthreads();
-            if (c0 + kChunk80 >= a.n_p && tid == 0 && t + gridDim.x < ntiles && full_tile(t + gridDim.x))
+            if (c0 + kChunk80 >= n_p && tid == 0 && t + gridDim.x < ntiles && full_tile(t + gridDim.x))
                 issue(t + gridDim.x);  // every row of this tile is sliced: the tile buffer is free
-            if (u < kProducts80 && c0 + slot < a.n_p) {
+            if (u < kProducts80 && c0 + slot < n_p) {
                 const uint32_t *const ex = work + 2 * slot * kSliceStride, *const ey = ex + kSliceStride;
                 uint32_t X[16], Y[16];
 #pragma unroll
@@ -485,32 +509,26 @@ __global__ void __launch_bounds__(kThreadsLanes, 4) extract_q80_lanes_kernel(con
             red[i] = r;
         }
         __syncthreads();
-        // z_k: P_cc at u^2c and at u^(c+d) for every d != c; P_cd (c < d) at u^(c+d)
+        // z_k: the products placed at u^m for the (at most two) m with
+        // 16m <= k < 16m + 31
         for (uint32_t k = tid; k < 160; k += kThreadsLanes) {
             uint32_t z = 0;
 #pragma unroll
-            for (uint32_t p = 0; p < kProducts80; ++p) {
-                const uint32_t c = product_lo(p), d = product_hi(p);
-#pragma unroll
-                for (uint32_t e = 0; e < 5; ++e) {
-                    // offsets: for P_cc, 32c (e == c) and 16(c + e) (e != c); for P_cd, 16(c + d) once (e == 0)
-                    const uint32_t off = c == d ? 16 * (c + e) : 16 * (c + d);
-                    if ((c == d || e == 0) && k - off < 31u) z ^= red[p * 31 + (k - off)];
+            for (uint32_t mm = 0; mm < 2; ++mm) {
+                const uint32_t m = (k >> 4) - mm, idx = k - 16 * m;  // m = -1 wraps past 8
+                if (m <= 8 && idx < 31) {
+                    const uint32_t len = kAtOffsetLen[m];
+                    for (uint32_t j = 0; j < len; ++j) z ^= red[kAtOffset[m][j] * 31 + idx];
                 }
             }
             zw[k] = z;
         }
         __syncthreads();
+        // back to one value per block: words 32g .. 32g + 31 of z transposed
+        // by warp g (warp 0 also takes g = 4)
+        for (uint32_t g = warp; g < 5; g += kThreadsLanes / 32) ow[32 * g + lane] = warp_transpose32(zw[32 * g + lane], lane);
+        __syncthreads();
         if (warp == 0) {
-            if (lane < 5) {
-                uint32_t W[32];
-#pragma unroll
-                for (int e = 0; e < 32; ++e) W[e] = zw[32 * lane + e];
-                slice<32>(W);  // word b: coefficients 32 lane .. 32 lane + 31 of block b
-#pragma unroll
-                for (int b = 0; b < 32; ++b) ow[lane * 32 + b] = W[b];
-            }
-            __syncwarp();
             const uint64_t z0 = ow[lane] | (uint64_t(ow[32 + lane]) << 32);
             const uint64_t z1 = ow[64 + lane] | (uint64_t(ow[96 + lane]) << 32);
             const uint64_t z2 = ow[128 + lane];
@@ -539,7 +557,7 @@ int launch_extract_q80(const qext_plan *p, const uint32_t *x, const uint32_t *y,
                        qext_cuda_stream stream) {
     if (p->q != 80) return QEXT_E_UNSUPPORTED;
     if (nblocks == 0) return QEXT_OK;
-    static DeviceSlots grid_caps, smem_optin, attr_set;
+    static DeviceSlots grid_caps, smem_optin, attr_set[2];
     const int dev = current_device();
     if (dev < 0) return QEXT_E_CUDA;
     const int sms = sm_count(dev);
@@ -566,25 +584,26 @@ int launch_extract_q80(const qext_plan *p, const uint32_t *x, const uint32_t *y,
     const uint64_t n = 80ull * p->n_p;
     const uint64_t lanes_smem = (2 * n + 4 + kWorkWords) * 4;
     if (lanes_smem + 1024 <= uint64_t(optin)) {
-        if (attr_set.get(dev, [optin] {
-                return cudaFuncSetAttribute(extract_q80_lanes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            optin - 1024) == cudaSuccess ? 1 : 0;
+        // the paper's n_p = 71 with compile-time row strides, any other n_p at run time
+        const bool fixed = p->n_p == 71;
+        void (*const kernel)(const LanesArgs) = fixed ? extract_q80_lanes_kernel<71> : extract_q80_lanes_kernel<0>;
+        if (attr_set[fixed].get(dev, [optin, kernel] {
+                return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - 1024) ==
+                               cudaSuccess ? 1 : 0;
             }) <= 0)
             return QEXT_E_CUDA;
         int occ = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, extract_q80_lanes_kernel, kThreadsLanes,
-                                                          size_t(lanes_smem)) != cudaSuccess)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kThreadsLanes, size_t(lanes_smem)) !=
+            cudaSuccess)
             return QEXT_E_CUDA;
         LanesArgs a;
         a.s = s;
         a.n_p = p->n_p;
-        a.in_words = uint32_t(n);
-        a.y_offset = uint32_t(n) + 4;  // 16 bytes between the tiles: the slicing reads spread over the banks
         a.bulk = (reinterpret_cast<uintptr_t>(x) % 16 == 0 && reinterpret_cast<uintptr_t>(y) % 16 == 0) ? 1 : 0;
         a.src_words = (nblocks * n + 31) / 32;
         const uint64_t ntiles = (nblocks + 31) / 32, cap = uint64_t(sms) * uint64_t(occ > 0 ? occ : 1);
         const int grid = int(ntiles < cap ? ntiles : cap);
-        return launch_pdl(extract_q80_lanes_kernel, grid, kThreadsLanes, size_t(lanes_smem), st, a);
+        return launch_pdl(kernel, grid, kThreadsLanes, size_t(lanes_smem), st, a);
     }
 
     const int grid_cap = grid_caps.get(dev, [sms] {
