@@ -781,18 +781,24 @@ def run_gpu(args):
     te = max_over_ranks(time.perf_counter() - t0, world)
     e2e_ok = bool((h_out.numpy().view(np.uint32) == gpu_out).all())
     # the host link: one step's input copied host -> device alone (pinned,
-    # the same bytes), the bound of the end-to-end number
+    # the same bytes, in the pipeline's chunks), the bound of the end-to-end
+    # number
     d_x = torch.empty_like(h_x, device=dev)
     d_y = torch.empty_like(h_y, device=dev)
+    hb_x, hb_y, db_x, db_y = (t.view(torch.uint8) for t in (h_x, h_y, d_x, d_y))
+    cbits = qext.qext_pipeline_info(pp)["chunk_blocks"] * spec.n  # stream bits per chunk and source
+    cb = cbits // 8 if not pb else cbits // pb * 2                # bytes per chunk and source
     link = []
-    for _ in range(3):
+    for rep in range(7):
         c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         c0.record()
-        d_x.copy_(h_x, non_blocking=True)
-        d_y.copy_(h_y, non_blocking=True)
+        for off in range(0, hb_x.numel(), cb):
+            db_x[off:off + cb].copy_(hb_x[off:off + cb], non_blocking=True)
+            db_y[off:off + cb].copy_(hb_y[off:off + cb], non_blocking=True)
         c1.record()
         torch.cuda.synchronize()
-        link.append(c0.elapsed_time(c1) * 1e-3)
+        if rep >= 2:
+            link.append(c0.elapsed_time(c1) * 1e-3)
     link_gbs = h2d / statistics.median(link) / 1e9
     del d_x, d_y
     link_bound = bits_per_step / (h2d / (link_gbs * 1e9)) / 1e9
