@@ -526,7 +526,8 @@ def measure_monitor(args, dev):
     return {"workload": "qext_sample_histogram, 12-bit samples: one 2^31-bit chunk (358 MB); drift: 8 chunks of "
                         "2^24 samples, sigma(t) = 1 + 0.05 sin(2 pi t / T)",
             "us": round(t * 1e6, 2), "gb_per_s": round(2 * n / t / 1e9, 1),
-            "hbm_frac_of_measured": round(2 * n / t / 1e9 / measured_peaks()[0], 4),
+            "hbm_frac": round(2 * n / t / 1e9 / measured_peaks()[0], 4),
+            "hbm_peak_source": measured_peaks()[1],
             "h_min_per_chunk_bits": est, "h_min_analytic_sigma1_bits": round(workloads.adc_min_entropy(12), 3)}
 
 
