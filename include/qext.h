@@ -345,6 +345,33 @@ typedef struct qext_batch qext_batch; /* opaque, host-owned, holds device memory
 int qext_batch_create(const qext_batch_item *items, uint32_t nitems, qext_batch **out);
 int qext_batch_destroy(qext_batch *b);
 
+/* One stream pair of raw ADC samples in a batch: the ingest of
+ * qext_extract_samples (Sec. 3: sample s at stream bits [s*b, (s+1)*b), the
+ * low b bits of each uint16) runs inside the batched kernel, which packs each
+ * tile from the samples straight into shared memory; the packed stream never
+ * reaches device memory. */
+typedef struct qext_batch_samples_item {
+    const qext_plan *plan;     /* q <= 64 with a GPU kernel (gpu_supported == 1); must outlive the batch */
+    uint32_t b;                /* bits per sample: 8, 12 or 16 */
+    const uint16_t *x_samples; /* DEVICE, nsamples uint16, 16-byte aligned */
+    const uint16_t *y_samples; /* DEVICE, same layout as x_samples */
+    uint64_t nsamples;         /* samples per source; nblocks * n <= nsamples * b */
+    uint64_t nblocks;          /* whole blocks of this stream */
+    uint32_t *out;             /* DEVICE, ceil(nblocks*m/32) words, fully written */
+} qext_batch_samples_item;
+
+/*
+ * qext_batch_create_samples -- qext_batch_create for streams of raw samples
+ * (same tiles, configuration, run, capture, launch and autotune; outputs
+ * equal to qext_extract_samples per stream).  The items' arguments are
+ * checked before the device is touched.  Errors: INVAL (null or misaligned
+ * pointers, nblocks * n > nsamples * b), UNSUPPORTED (b not 8, 12 or 16, a
+ * plan without a GPU kernel, or blocks over 8192 bits), CUDA.
+ * qext_batch_run_ex with QEXT_F_TEST_TIMEOUT returns INVAL for such a batch
+ * (its tiles take no bulk copy).
+ */
+int qext_batch_create_samples(const qext_batch_samples_item *items, uint32_t nitems, qext_batch **out);
+
 /* Current configuration and tile count (either pointer may be NULL). */
 int qext_batch_get_config(const qext_batch *b, qext_batch_config *cfg, uint32_t *ntiles);
 /* Rebuilds the tile table for cfg (drops a captured graph).  Errors: INVAL. */

@@ -14,6 +14,11 @@
 // Tile shape (blocks per thread for q = 4 and q = 16) and CTAs per SM are the
 // tunables; qext_batch_autotune times the candidates on the batch itself.
 // qext_batch_capture records memset + kernel into a CUDA graph.
+//
+// Streams of raw b-bit samples (qext_batch_create_samples) are packed by the
+// CTA from global memory straight into the tile buffer (the fused ingest of
+// qext_extract_samples), so a batch of ADC streams is one launch with no
+// packed copy in device memory.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -40,6 +45,11 @@ struct BatchStreamDev {
     StreamArgs s;
     uint32_t q;
     uint32_t tma;  // x, y 16-byte aligned
+    // raw samples (b = 8, 12 or 16; b = 0: packed words in s.x, s.y)
+    const uint16_t *sx;
+    const uint16_t *sy;
+    uint64_t nsamples;
+    uint32_t b;
 };
 
 struct BatchTileDev {
@@ -128,8 +138,19 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(const BatchStreamDev *_
         const StreamArgs &s = it.s;
         const uint32_t words = tl.nb * s.wpb;
         uint32_t *xs = smem, *ys = smem + words;
-        bool ok;
-        load_tile(s, tl.first, tl.nb, it.tma, xs, ys, &bar, uses, ok, max_polls, no_copy);
+        bool ok = true;
+        if (it.b) {
+            // fused ingest: the tile's samples packed from global memory into the buffer
+            const uint64_t w0 = tl.first * s.wpb;
+            if (it.b == 8)
+                pack_tile<8>(it.sx, it.sy, it.nsamples, w0, words, xs, ys, tid, kThreads);
+            else if (it.b == 12)
+                pack_tile<12>(it.sx, it.sy, it.nsamples, w0, words, xs, ys, tid, kThreads);
+            else
+                pack_tile<16>(it.sx, it.sy, it.nsamples, w0, words, xs, ys, tid, kThreads);
+        } else {
+            load_tile(s, tl.first, tl.nb, it.tma, xs, ys, &bar, uses, ok, max_polls, no_copy);
+        }
         if (!__syncthreads_and(ok)) {
             if (tid == 0) {
                 record_status(s.status, QEXT_E_TIMEOUT);
@@ -212,7 +233,7 @@ int build_tiles(qext_batch *b) {
             h.t.item = i;
             h.t.first = f;
             h.t.nb = uint32_t(std::min<uint64_t>(T, it.s.nblocks - f));
-            h.cost = h.t.nb * block_cost(it.q, it.s.wpb);
+            h.cost = h.t.nb * block_cost(it.q, it.s.wpb) * (it.b ? 1.25 : 1.0);  // the ingest adds ~a quarter
             tiles.push_back(h);
         }
     }
@@ -254,11 +275,26 @@ void drop_graph(qext_batch *b) {
 
 }  // namespace
 
-extern "C" {
+namespace {
 
-int qext_batch_create(const qext_batch_item *items, uint32_t nitems, qext_batch **out) {
-    if (!out || (nitems && !items)) return QEXT_E_INVAL;
-    *out = nullptr;
+// The device descriptor of one stream (pointers filled by the caller).
+BatchStreamDev stream_dev(const qext_plan *plan, uint64_t nblocks, uint32_t *out) {
+    BatchStreamDev d;
+    std::memset(&d, 0, sizeof d);
+    d.s.out = out;
+    d.s.nblocks = nblocks;
+    d.s.wpb = plan->n / 32;
+    d.s.m = plan->m;
+    d.s.ntaps = plan->ntaps;
+    for (int k = 0; k < 4; ++k) d.s.taps[k] = plan->taps[k];
+    d.s.set_multipliers();
+    d.s.status = qext::device_status_ptr();
+    d.q = plan->q;
+    return d;
+}
+
+// Device tables and tiles for validated descriptors.
+int create_batch(const std::vector<BatchStreamDev> &devs, qext_batch **out) {
     static qext::DeviceSlots attr_set;
     const int dev = qext::current_device();
     if (dev < 0 || attr_set.get(dev, [] {
@@ -273,51 +309,12 @@ int qext_batch_create(const qext_batch_item *items, uint32_t nitems, qext_batch 
     b->cfg.ctas_per_sm = 3;
     b->cfg.order = 0;
     b->sms = qext::sm_count(dev);
-    if (b->sms <= 0) {
-        delete b;
-        return QEXT_E_CUDA;
-    }
-    for (uint32_t i = 0; i < nitems; ++i) {
-        const qext_batch_item &it = items[i];
-        if (!it.plan) {
-            qext_batch_destroy(b);
-            return QEXT_E_INVAL;
-        }
-        if (!it.plan->gpu_supported) {
-            qext_batch_destroy(b);
-            return QEXT_E_UNSUPPORTED;
-        }
-        const uintptr_t al = reinterpret_cast<uintptr_t>(it.x) | reinterpret_cast<uintptr_t>(it.y);
-        if (it.nblocks && (!it.x || !it.y || !it.out || al % 4 || reinterpret_cast<uintptr_t>(it.out) % 4)) {
-            qext_batch_destroy(b);
-            return QEXT_E_INVAL;
-        }
-        BatchStreamDev d;
-        std::memset(&d, 0, sizeof d);
-        d.s.x = it.x;
-        d.s.y = it.y;
-        d.s.out = it.out;
-        d.s.nblocks = it.nblocks;
-        d.s.wpb = it.plan->n / 32;
-        d.s.m = it.plan->m;
-        d.s.ntaps = it.plan->ntaps;
-        for (int k = 0; k < 4; ++k) {
-            d.s.taps[k] = it.plan->taps[k];
-        }
-        d.s.set_multipliers();
-        d.s.status = qext::device_status_ptr();
-        d.q = it.plan->q;
-        d.tma = al % 16 == 0;
-        b->items.push_back(d);
-    }
-    if (cudaMalloc(&b->d_counter, sizeof(*b->d_counter)) != cudaSuccess ||
-        (nitems && cudaMalloc(&b->d_items, sizeof(BatchStreamDev) * nitems) != cudaSuccess)) {
-        qext_batch_destroy(b);
-        return QEXT_E_CUDA;
-    }
-    if (nitems &&
-        cudaMemcpy(b->d_items, b->items.data(), sizeof(BatchStreamDev) * nitems, cudaMemcpyHostToDevice) !=
-            cudaSuccess) {
+    b->items = devs;
+    const size_t nitems = devs.size();
+    if (b->sms <= 0 || cudaMalloc(&b->d_counter, sizeof(*b->d_counter)) != cudaSuccess ||
+        (nitems && cudaMalloc(&b->d_items, sizeof(BatchStreamDev) * nitems) != cudaSuccess) ||
+        (nitems && cudaMemcpy(b->d_items, b->items.data(), sizeof(BatchStreamDev) * nitems,
+                              cudaMemcpyHostToDevice) != cudaSuccess)) {
         qext_batch_destroy(b);
         return QEXT_E_CUDA;
     }
@@ -328,6 +325,56 @@ int qext_batch_create(const qext_batch_item *items, uint32_t nitems, qext_batch 
     }
     *out = b;
     return QEXT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int qext_batch_create(const qext_batch_item *items, uint32_t nitems, qext_batch **out) {
+    if (!out || (nitems && !items)) return QEXT_E_INVAL;
+    *out = nullptr;
+    std::vector<BatchStreamDev> devs;
+    devs.reserve(nitems);
+    for (uint32_t i = 0; i < nitems; ++i) {
+        const qext_batch_item &it = items[i];
+        if (!it.plan) return QEXT_E_INVAL;
+        if (!it.plan->gpu_supported) return QEXT_E_UNSUPPORTED;
+        const uintptr_t al = reinterpret_cast<uintptr_t>(it.x) | reinterpret_cast<uintptr_t>(it.y);
+        if (it.nblocks && (!it.x || !it.y || !it.out || al % 4 || reinterpret_cast<uintptr_t>(it.out) % 4))
+            return QEXT_E_INVAL;
+        BatchStreamDev d = stream_dev(it.plan, it.nblocks, it.out);
+        d.s.x = it.x;
+        d.s.y = it.y;
+        d.tma = al % 16 == 0;
+        devs.push_back(d);
+    }
+    return create_batch(devs, out);
+}
+
+int qext_batch_create_samples(const qext_batch_samples_item *items, uint32_t nitems, qext_batch **out) {
+    if (!out || (nitems && !items)) return QEXT_E_INVAL;
+    *out = nullptr;
+    std::vector<BatchStreamDev> devs;
+    devs.reserve(nitems);
+    for (uint32_t i = 0; i < nitems; ++i) {
+        const qext_batch_samples_item &it = items[i];
+        if (!it.plan) return QEXT_E_INVAL;
+        if (it.b != 8 && it.b != 12 && it.b != 16) return QEXT_E_UNSUPPORTED;
+        if (!it.plan->gpu_supported) return QEXT_E_UNSUPPORTED;
+        const uintptr_t al = reinterpret_cast<uintptr_t>(it.x_samples) | reinterpret_cast<uintptr_t>(it.y_samples);
+        if (it.nblocks && (!it.x_samples || !it.y_samples || !it.out || al % 16 ||
+                           reinterpret_cast<uintptr_t>(it.out) % 4))
+            return QEXT_E_INVAL;
+        if (it.nsamples > UINT64_MAX / 16 || it.nblocks > (it.nsamples * it.b) / it.plan->n) return QEXT_E_INVAL;
+        BatchStreamDev d = stream_dev(it.plan, it.nblocks, it.out);
+        d.sx = it.x_samples;
+        d.sy = it.y_samples;
+        d.nsamples = it.nsamples;
+        d.b = it.b;
+        devs.push_back(d);
+    }
+    return create_batch(devs, out);
 }
 
 int qext_batch_destroy(qext_batch *b) {
@@ -367,9 +414,9 @@ int qext_batch_run_ex(qext_batch *b, qext_cuda_stream stream, uint32_t flags) {
     if (!b) return QEXT_E_INVAL;
     if (flags & ~uint32_t(QEXT_F_TEST_TIMEOUT)) return QEXT_E_INVAL;
     if (flags) {
-        // the test needs every tile on the bulk-copy path
+        // the test needs every tile on the bulk-copy path (sample tiles take none)
         for (const BatchStreamDev &d : b->items)
-            if (d.s.nblocks && !d.tma) return QEXT_E_INVAL;
+            if (d.s.nblocks && (!d.tma || d.b)) return QEXT_E_INVAL;
     }
     const qext::NvtxRange range("qext batch run");
     return enqueue(b, reinterpret_cast<cudaStream_t>(stream), flags);

@@ -43,6 +43,12 @@ class BatchItem(ctypes.Structure):
                 ("nblocks", ctypes.c_uint64), ("out", ctypes.c_void_p)]
 
 
+class BatchSamplesItem(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("b", ctypes.c_uint32), ("x_samples", ctypes.c_void_p),
+                ("y_samples", ctypes.c_void_p), ("nsamples", ctypes.c_uint64), ("nblocks", ctypes.c_uint64),
+                ("out", ctypes.c_void_p)]
+
+
 class BatchConfig(ctypes.Structure):
     _fields_ = [("blocks_per_thread_small", ctypes.c_uint32), ("blocks_per_thread_mid", ctypes.c_uint32),
                 ("ctas_per_sm", ctypes.c_uint32), ("order", ctypes.c_uint32)]
@@ -104,6 +110,7 @@ def lib():
     L.qext_stream_save.argtypes = [vp, vp, ctypes.c_size_t, P(ctypes.c_size_t), vp]
     L.qext_stream_restore.argtypes = [vp, vp, ctypes.c_size_t, P(vp), vp]
     L.qext_batch_create.argtypes = [vp, u32, P(vp)]
+    L.qext_batch_create_samples.argtypes = [vp, u32, P(vp)]
     L.qext_batch_destroy.argtypes = [vp]
     L.qext_batch_get_config.argtypes = [vp, P(BatchConfig), P(u32)]
     L.qext_batch_set_config.argtypes = [vp, P(BatchConfig)]
@@ -136,7 +143,7 @@ def lib():
                  "qext_extract_ex", "qext_extract_samples", "qext_extract_samples_ex",
                  "qext_pack_samples", "qext_device_status", "qext_stream_create", "qext_stream_destroy",
                  "qext_stream_info", "qext_stream_push", "qext_stream_push_samples", "qext_stream_flush", "qext_stream_save",
-                 "qext_stream_restore", "qext_batch_create", "qext_batch_destroy", "qext_batch_get_config",
+                 "qext_stream_restore", "qext_batch_create", "qext_batch_create_samples", "qext_batch_destroy", "qext_batch_get_config",
                  "qext_batch_set_config", "qext_batch_run", "qext_batch_run_ex", "qext_batch_capture", "qext_batch_launch",
                  "qext_batch_autotune", "qext_batch_run_noalloc", "qext_server_create", "qext_server_destroy",
                  "qext_server_add_channel", "qext_server_submit", "qext_server_poll", "qext_server_drain",
@@ -356,6 +363,16 @@ def qext_batch_create(items) -> Batch:
         arr[i] = BatchItem(plan.handle, _ptr(x), _ptr(y), nb, _ptr(out))
     h = ctypes.c_void_p()
     _check(lib().qext_batch_create(arr, len(items), ctypes.byref(h)), "qext_batch_create")
+    return Batch(h.value, [it for it in items])
+
+
+def qext_batch_create_samples(items) -> Batch:
+    """items: sequence of (plan, b, x_samples, y_samples, nsamples, nblocks, out)."""
+    arr = (BatchSamplesItem * max(1, len(items)))()
+    for i, (plan, b, sx, sy, ns, nb, out) in enumerate(items):
+        arr[i] = BatchSamplesItem(plan.handle, b, _ptr(sx), _ptr(sy), ns, nb, _ptr(out))
+    h = ctypes.c_void_p()
+    _check(lib().qext_batch_create_samples(arr, len(items), ctypes.byref(h)), "qext_batch_create_samples")
     return Batch(h.value, [it for it in items])
 
 

@@ -183,6 +183,24 @@ def test_samples_argument_checks_without_gpu():
     assert e.value.code == qext.QEXT_E_INVAL    # the q = 80 kernel takes no flags
 
 
+def test_batch_samples_argument_checks_without_gpu():
+    """qext_batch_create_samples checks every item before any device work."""
+    p = qext.qext_plan_create(1024, 0, 867, 2.0 ** -50)   # q = 16, n = 1024
+    p80 = qext.qext_plan_create(5680, 80, 0.67125 * 5680, 2.0 ** -30)
+    cases = [
+        ((p, 10, 16, 16, 1000, 1, 16), qext.QEXT_E_UNSUPPORTED),   # b not 8 / 12 / 16
+        ((p80, 16, 16, 16, 1000, 1, 16), qext.QEXT_E_UNSUPPORTED),  # q = 80: no batched kernel
+        ((p, 12, 16, 16, 85, 1, 16), qext.QEXT_E_INVAL),            # 85 samples < one 1024-bit block
+        ((p, 12, 0, 16, 1000, 1, 16), qext.QEXT_E_INVAL),           # null x
+        ((p, 12, 16, 8, 1000, 1, 16), qext.QEXT_E_INVAL),           # y not 16-byte aligned
+        ((p, 12, 16, 16, 1000, 1, 2), qext.QEXT_E_INVAL),           # out not 4-byte aligned
+    ]
+    for item, code in cases:
+        with pytest.raises(qext.QextError) as e:
+            qext.qext_batch_create_samples([item])
+        assert e.value.code == code, item
+
+
 def test_monitor_host_side_without_gpu():
     """The histogram entry checks its arguments before any device work; the
     plug-in min-entropy is host code and agrees with the oracle's."""

@@ -167,6 +167,64 @@ def test_batched_adc_workload_scaled():
     b.close()
 
 
+@pytest.mark.parametrize("seed", [21, 22])
+def test_batched_raw_samples_match_oracle(seed):
+    """qext_batch_create_samples: streams of raw 8-, 12- and 16-bit samples
+    (garbage above the low b bits of each uint16), q in {1 .. 64}, ragged
+    block counts and spare samples, one launch with the ingest inside; every
+    output bit against the oracle on the packed streams, and equal to
+    qext_extract_samples / the packed-word batch on the same data."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    specs = [(16, 64, 16, 1000, 12), (4, 64, 4, 3000, 8), (64, 64, 64, 300, 12), (64, 64, 50, 129, 8),
+             (16, 64, 13, 257, 16), (8, 64, 8, 129, 12), (1, 64, 1, 700, 8), (32, 64, 32, 65, 12),
+             (64, 64, 64, 1, 16), (16, 64, 16, 0, 12), (4, 72, 4, 600, 12), (64, 40, 64, 100, 12)]
+    items, hosts, packed = [], [], []
+    for q, n_p, m, nb, b in specs:
+        plan = plan_for(q, n_p, m)
+        n = q * n_p
+        ns = -(-nb * n // b) + int(rng.integers(0, 20))
+        raw_x = rng.integers(0, 1 << 16, ns, dtype=np.uint16)
+        raw_y = rng.integers(0, 1 << 16, ns, dtype=np.uint16)
+        sx = torch.from_numpy(raw_x.view(np.int16)).cuda()
+        sy = torch.from_numpy(raw_y.view(np.int16)).cuda()
+        nout = -(-nb * plan.info["m"] // 32)
+        out = torch.full((nout + 2,), -1, dtype=torch.int32, device="cuda")
+        items.append((plan, b, sx, sy, ns, nb, out))
+        words = nb * n // 32
+        hosts.append((plan, oracle.pack_samples(b, raw_x)[:words], oracle.pack_samples(b, raw_y)[:words], nb, nout))
+        px = torch.empty(max(1, -(-ns * b // 32)), dtype=torch.int32, device="cuda")
+        py = torch.empty_like(px)
+        if ns:
+            qext.qext_pack_samples(b, sx, ns, px)
+            qext.qext_pack_samples(b, sy, ns, py)
+        packed.append((plan, px, py, nb, torch.full((nout + 2,), -1, dtype=torch.int32, device="cuda")))
+    bs = qext.qext_batch_create_samples(items)
+    qext.qext_batch_run(bs)
+    wants = expected(hosts)
+    check([(it[0], None, None, it[5], it[6]) for it in items], hosts, wants)
+    bp = qext.qext_batch_create(packed)
+    qext.qext_batch_run(bp)
+    torch.cuda.synchronize()
+    for it, pk in zip(items, packed):
+        assert torch.equal(it[6], pk[4])
+    # graph replay and every configuration give the same bits
+    s = torch.cuda.Stream()
+    for cfg in [(1, 1, 1, 1), (2, 2, 2, 0), (4, 4, 3, 0)]:
+        qext.qext_batch_set_config(bs, *cfg)
+        for it in items:
+            it[6].fill_(-1)
+        qext.qext_batch_capture(bs, s)
+        qext.qext_batch_launch(bs, s)
+        s.synchronize()
+        check([(it[0], None, None, it[5], it[6]) for it in items], hosts, wants)
+    # the test mode of failure detection needs bulk-copied tiles
+    with pytest.raises(qext.QextError) as e:
+        qext.qext_batch_run_ex(bs, None, qext.QEXT_F_TEST_TIMEOUT)
+    assert e.value.code == qext.QEXT_E_INVAL
+    bs.close()
+    bp.close()
+
+
 def test_batched_bounded_wait_times_out_and_context_survives():
     """Failure detection in the batched kernel without a fault: each CTA arms
     its tile barrier but no bulk copy is issued, so its bounded wait runs out;

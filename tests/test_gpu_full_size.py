@@ -161,9 +161,11 @@ def _block_from_samples(plan, n, b, samples, l):
 
 def test_batched_adc_full_size_sampled():
     """The batched workload as the benchmark runs it: 64 stream pairs of 8- and
-    12-bit ADC samples drawn on the device, one CUDA graph holding every
-    stream's ingest and the single batched extraction launch; sampled blocks
-    of every stream (and its first and last) match the oracle."""
+    12-bit ADC samples drawn on the device, the raw-sample batch (ingest inside
+    the one batched launch) autotuned and replayed from its CUDA graph; sampled
+    blocks of every stream (and its first and last) match the oracle, and the
+    two-pass graph (every stream's ingest, then the packed-word batch) gives
+    the same outputs."""
     specs = workloads.config_batched()
     plans, items, raw = {}, [], []
     for sp in specs:
@@ -182,23 +184,13 @@ def test_batched_adc_full_size_sampled():
         raw.append((sp.b, sx, sy, ns))
     stream = torch.cuda.Stream()
     sh = int(stream.cuda_stream)
-
-    def ingest():
-        for (b_, sx, sy, ns), (_, px, py, _, _) in zip(raw, items):
-            qext.qext_pack_samples(b_, sx, ns, px, sh)
-            qext.qext_pack_samples(b_, sy, ns, py, sh)
-
-    ingest()
-    b = qext.qext_batch_create(items)
-    qext.qext_batch_autotune(b, 1, stream)
+    bs = qext.qext_batch_create_samples([(plan, b_, sx, sy, ns, nb, out)
+                                         for (b_, sx, sy, ns), (plan, _, _, nb, out) in zip(raw, items)])
+    qext.qext_batch_autotune(bs, 1, stream)
     for it in items:
         it[4].fill_(-1)
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph, stream=stream):
-        ingest()
-        qext.qext_batch_run(b, sh)
-    with torch.cuda.stream(stream):
-        graph.replay()
+    qext.qext_batch_capture(bs, stream)
+    qext.qext_batch_launch(bs, stream)
     stream.synchronize()
     rng = np.random.Generator(np.random.PCG64(19))
     for (plan, _, _, nb, out), (b_, sx, sy, ns), sp in zip(items, raw, specs):
@@ -210,4 +202,24 @@ def test_batched_adc_full_size_sampled():
             xw = _block_from_samples(plan, sp.n, b_, sx, l)
             yw = _block_from_samples(plan, sp.n, b_, sy, l)
             assert bits_at(got, l * m, m) == block_value(plan, xw, yw), (sp.n, b_, nb, l)
+    fused = [it[4].clone() for it in items]
+
+    def ingest():
+        for (b_, sx, sy, ns), (_, px, py, _, _) in zip(raw, items):
+            qext.qext_pack_samples(b_, sx, ns, px, sh)
+            qext.qext_pack_samples(b_, sy, ns, py, sh)
+
+    ingest()
+    b = qext.qext_batch_create(items)
+    for it in items:
+        it[4].fill_(-1)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        ingest()
+        qext.qext_batch_run(b, sh)
+    with torch.cuda.stream(stream):
+        graph.replay()
+    stream.synchronize()
+    assert all(torch.equal(f, it[4]) for f, it in zip(fused, items))
     b.close()
+    bs.close()
