@@ -139,10 +139,15 @@ def cpu_baseline(spec, sx, sy, gpu_out_words, sample_blocks):
     if gpu_out_words is not None:
         nw = out.size
         match = bool((gpu_out_words[:nw] == out).all()) if sample_blocks * m % 32 == 0 else None
+    # one core, on the first sixteenth of the sample
+    one = max(32, sample_blocks // 16)
+    _, dt1, _ = run_oracle_sample(spec, ox, oy, one, 1)
     return {
         "value": round(sample_blocks * m / dt / 1e9, 6), "unit": UNIT, "cores": threads, "kind": "oracle",
         "sample": "first %d block pairs of the same workload (extraction from the packed words), %.1f s" %
                   (sample_blocks, dt),
+        "single_thread_value": round(one * m / dt1 / 1e9, 6),
+        "single_thread_sample": "first %d block pairs, %.1f s" % (one, dt1),
         "matches_gpu_output": match,
     }
 
