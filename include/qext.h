@@ -409,7 +409,7 @@ int qext_batch_autotune(qext_batch *b, uint32_t reps, qext_cuda_stream stream, f
  * appliance or server whose admission control counts every byte), and code
  * in a latency-critical loop where cudaMalloc / cudaFree would synchronise
  * the device.  Nothing is allocated: the descriptors and the tile counter live
- * in one static device array of the library (about 100 KB, present on every
+ * in one static device array of the library (about 200 KB, present on every
  * device that loads the library until the process exits).  The paper has no
  * counterpart; this is a calling convention, not part of the method.
  *   items, nitems  as for qext_batch_create; at most QEXT_NOALLOC_MAX_ITEMS

@@ -508,7 +508,9 @@ struct NoallocScratch {
 };
 
 // Scratch of the allocation-free entry point: one per device, held until the
-// process exits, shared by every call (see qext_batch_run_noalloc).
+// process exits, shared by every call (see qext_batch_run_noalloc).  The size
+// quoted in the header (about 200 KB) is kept by this bound.
+static_assert(sizeof(NoallocScratch) <= 200 * 1024, "the documented static scratch size");
 static __device__ __align__(256) unsigned char qext_noalloc_scratch[sizeof(NoallocScratch)];
 
 __global__ void __launch_bounds__(kThreads) batch_noalloc_kernel(NoallocScratch *sc) {
