@@ -423,11 +423,7 @@ __global__ void __launch_bounds__(kThreadsLanes, 4) extract_q80_lanes_kernel(con
             }
             __syncthreads();
         }
-        uint32_t D[23], C[15];
-#pragma unroll
-        for (int k = 0; k < 23; ++k) D[k] = 0;
-#pragma unroll
-        for (int k = 0; k < 15; ++k) C[k] = 0;
+        Acc16K2 acc;  // this thread's product, over every element of the tile
         for (uint32_t c0 = 0; c0 < n_p; c0 += kChunk80) {
             // slicing: job (element e, source src, column group g)
             if (tid < 10 * kChunk80) {
@@ -465,31 +461,22 @@ __global__ void __launch_bounds__(kThreadsLanes, 4) extract_q80_lanes_kernel(con
                     Y[4 * k + 2] = lop_and_xor(yb.z, pmask, ya.z);
                     Y[4 * k + 3] = lop_and_xor(yb.w, pmask, ya.w);
                 }
-                // D += X_L Y_L + t^8 X_H Y_H,  C += (X_L + X_H)(Y_L + Y_H)
-#pragma unroll
-                for (int j = 0; j < 8; ++j)
-#pragma unroll
-                    for (int l = 0; l < 8; ++l) {
-                        D[j + l] = lop_and_xor(X[j], Y[l], D[j + l]);
-                        D[j + l + 8] = lop_and_xor(X[8 + j], Y[8 + l], D[j + l + 8]);
-                    }
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    X[j] ^= X[8 + j];
-                    Y[j] ^= Y[8 + j];
-                }
-#pragma unroll
-                for (int j = 0; j < 8; ++j)
-#pragma unroll
-                    for (int l = 0; l < 8; ++l) C[j + l] = lop_and_xor(X[j], Y[l], C[j + l]);
+                acc.add(X, Y);  // two Karatsuba levels (8 + 8, then 4 + 4), word accumulators
             }
             __syncthreads();
         }
-        // the product's 31 coefficient words: R = D (1 + t^8) + t^8 C, summed
-        // over the slots (two per warp by a shuffle, then over the warps)
+        // the product's 31 coefficient words: R = D (1 + t^8) + t^8 C with
+        // D = F (1 + t^4) + t^4 G and C = E (1 + t^4) + t^4 M (Acc16K2's parts),
+        // summed over the slots (two per warp by a shuffle, then over the warps)
         uint32_t *const red = work, *const zw = work + kRedWords, *const ow = zw + 160;
         {
-            uint32_t R[31];
+            uint32_t D[23], C[15], R[31];
+#pragma unroll
+            for (int k = 0; k < 23; ++k)
+                D[k] = (k < 19 ? acc.F[k] : 0u) ^ (k >= 4 ? acc.F[k - 4] ^ (k - 4 < 15 ? acc.G[k - 4] : 0u) : 0u);
+#pragma unroll
+            for (int k = 0; k < 15; ++k)
+                C[k] = (k < 11 ? acc.E[k] : 0u) ^ (k >= 4 ? acc.E[k - 4] ^ (k - 4 < 7 ? acc.M[k - 4] : 0u) : 0u);
 #pragma unroll
             for (int k = 0; k < 31; ++k) {
                 uint32_t r = k < 23 ? D[k] : 0u;
