@@ -312,8 +312,8 @@ __global__ void __launch_bounds__(kThreads80, 6) extract_q80_kernel(const Q80Arg
 // Implementations", 2006):
 //     x y = sum_c P_cc u^2c + sum_{c<d} (P_cd + P_cc + P_dd) u^(c+d),
 //     P_cd = (G_c(x) + G_d(x)) (G_c(y) + G_d(y)),
-// fifteen 16 x 16 sliced products, each one Karatsuba level over 8-word
-// halves.  The products are linear in their accumulators, so every thread
+// fifteen 16 x 16 sliced products, each by two Karatsuba levels (8-word,
+// then 4-word halves: the accumulators of Acc16K2).  The products are linear in their accumulators, so every thread
 // keeps one product's accumulators across all elements of the tile and the
 // recombination (fifteen products into the 159-bit sum) runs once per tile.
 //
