@@ -11,24 +11,34 @@
 // start (n * sum q_j) and every output offset (sum q_j) is a multiple of 16:
 // the streams and the output are arrays of 16-bit units and an element of
 // block l is k_l = q_l / 16 consecutive units (q_l <= 2048: k_l <= 128).
-// The product Z^(l) = sum_i x_i y_i splits into k_l^2 unit products per
-// element: with S_u = the slices of unit u over a group of 32 elements
-// (slice<16>, elements i and i + 16 in word i: element e in slot e), the
-// unreduced sum is XOR over groups and unit pairs (u, v) of the 31 diagonal
-// parities of the 16 x 16 sliced Gram product S_u^x (x) S_v^y, placed at bit
-// 16 (u + v).  Work items of at most kItemProducts unit pairs of one (block,
-// group) run as CTAs of one launch (alg2_products_kernel): each slices the
-// group's 2 k_l units into shared memory, computes its unit pairs, XORs the
-// parities into a shared sum and that into the block's sum in global memory.
-// A second launch (alg2_reduce_kernel, one CTA per block) reduces each sum mod
-// P_{q_l} word-parallel (the part at and above x^{q_l} folded back by the
-// taps until none is left) and writes the block's k_l output units.
+// The product Z^(l) = sum_i x_i y_i is taken unit by unit: with S_u = the
+// slices of unit u over a group of 32 elements (slice<16>, elements i and
+// i + 16 in word i: element e in slot e), each element is x = sum_u X_u w^u
+// (w = t^16) and the generalised Karatsuba formula (Weimerskirch and Paar,
+// 2006) gives
+//     x y = sum_u P_uu w^2u + sum_{u<v} (P_uv + P_uu + P_vv) w^(u+v),
+//     P_uv = (X_u + X_v)(Y_u + Y_v),
+// k_l (k_l + 1) / 2 unit products instead of k_l^2.  Each is a 16 x 16 sliced
+// Gram product whose 31 diagonal parities (parities are linear: XORed over
+// groups) are placed at bit 16 (u + v) of the block's unreduced sum, P_uv for
+// u < v directly; P_uu lands at every offset o = u + w, w < k_l, so the P_uu
+// are collected in a per-block array D and placed by the second launch as
+// window XORs, W_o = XOR of D_u over max(0, o - k_l + 1) <= u <= min(o, k_l - 1)
+// (prefix XORs).  Work items of at most kItemProducts unit products of one
+// (block, group) run as CTAs of one launch (alg2_products_kernel): each slices
+// the group's 2 k_l units into shared memory, computes its products, XORs the
+// parities into shared sums and those into the block's arrays in global
+// memory.  A second launch (alg2_reduce_kernel, one CTA per block) adds the
+// P_uu windows, reduces the sum mod P_{q_l} word-parallel (the part at and
+// above x^{q_l} folded back by the taps until none is left) and writes the
+// block's k_l output units.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdint>
+#include <cstring>
 #include <mutex>
 #include <new>
 #include <thread>
@@ -48,10 +58,11 @@ struct Alg2Block {
     uint32_t taps[4];  // of P_{q_l} below x^{q_l}, descending, ending with 0
     uint64_t in_unit;  // first 16-bit unit of the window: n * sum_{j<l} q_j / 16
     uint64_t out_unit; // first output unit: sum_{j<l} q_j / 16
-    uint64_t zoff;     // first word of the block's unreduced sum (k + 1 words)
+    uint64_t zoff;     // first word of the block's unreduced sum (k + 1 words), then D (k words)
 };
 
-// A work item: unit pairs p in [p0, p1) (p = u k + v) of one group of one block.
+// A work item: unit products p in [p0, p1) of one group of one block (p
+// counts the pairs u <= v row by row: row u holds v = u .. k - 1).
 struct Alg2Item {
     uint32_t block;
     uint32_t group;
@@ -76,17 +87,23 @@ namespace {
 
 constexpr int kAlg2Threads = 256;
 constexpr uint32_t kMaxUnits = 128;       // q_l <= 2048
-constexpr uint32_t kItemProducts = 2048;  // unit pairs per work item
+constexpr uint32_t kItemProducts = 1024;  // unit products per work item
+constexpr uint32_t kRow = 20;             // words per sliced unit in shared memory
 
 __global__ void __launch_bounds__(kAlg2Threads)
     alg2_products_kernel(const Alg2Item *__restrict__ items, const Alg2Block *__restrict__ table, uint32_t n_p,
-                         const uint16_t *__restrict__ x, const uint16_t *__restrict__ y, uint32_t *__restrict__ zg) {
-    __shared__ uint32_t S[2][kMaxUnits][16];  // sliced units of the group
+                         const uint16_t *__restrict__ x, const uint16_t *__restrict__ y, uint32_t *__restrict__ zg,
+                         const StreamArgs pm) {  // pm: the parity-assembly multipliers only
+    // sliced units of the group; rows of 20 words, so that a quarter-warp's
+    // 16-byte reads of consecutive rows fall on distinct bank groups
+    __shared__ __align__(16) uint32_t S[2][kMaxUnits][kRow];
     __shared__ uint32_t z[kMaxUnits + 1];     // this item's share of the unreduced sum
+    __shared__ uint32_t d[kMaxUnits];         // and of the P_uu parities
     const Alg2Item it = items[blockIdx.x];
     const Alg2Block blk = table[it.block];
     const uint32_t k = blk.k, tid = threadIdx.x;
     for (uint32_t i = tid; i <= k; i += blockDim.x) z[i] = 0;
+    for (uint32_t i = tid; i < k; i += blockDim.x) d[i] = 0;
     if (tid < 2 * k) {
         const uint32_t src = tid / k, u = tid % k;
         const uint16_t *s = (src ? y : x) + blk.in_unit + u;
@@ -100,19 +117,39 @@ __global__ void __launch_bounds__(kAlg2Threads)
         }
         slice<16>(w);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) S[src][u][i] = w[i];
+        for (int c = 0; c < 4; ++c)
+            *reinterpret_cast<uint4 *>(&S[src][u][4 * c]) = make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
     }
     __syncthreads();
     for (uint32_t p = it.p0 + tid; p < it.p1; p += blockDim.x) {
-        const uint32_t u = p / k, v = p % k;
+        // row u starts at R(u) = u k - u (u - 1) / 2
+        const float b2 = float(2 * k + 1);
+        uint32_t u = uint32_t((b2 - sqrtf(b2 * b2 - 8.0f * float(p))) * 0.5f);
+        auto row = [k](uint32_t r) { return r * k - r * (r - 1) / 2; };
+        while (u > 0 && row(u) > p) --u;
+        while (u + 1 < k && row(u + 1) <= p) ++u;
+        const uint32_t v = u + (p - row(u));
+        const uint32_t mask = u == v ? 0u : ~0u;
         uint32_t X[16], Y[16];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            X[i] = S[0][u][i];
-            Y[i] = S[1][v][i];
+        for (int c = 0; c < 4; ++c) {
+            const uint4 xu = lds4(&S[0][u][4 * c]), xv = lds4(&S[0][v][4 * c]);
+            const uint4 yu = lds4(&S[1][u][4 * c]), yv = lds4(&S[1][v][4 * c]);
+            X[4 * c] = lop_and_xor(xv.x, mask, xu.x);
+            X[4 * c + 1] = lop_and_xor(xv.y, mask, xu.y);
+            X[4 * c + 2] = lop_and_xor(xv.z, mask, xu.z);
+            X[4 * c + 3] = lop_and_xor(xv.w, mask, xu.w);
+            Y[4 * c] = lop_and_xor(yv.x, mask, yu.x);
+            Y[4 * c + 1] = lop_and_xor(yv.y, mask, yu.y);
+            Y[4 * c + 2] = lop_and_xor(yv.z, mask, yu.z);
+            Y[4 * c + 3] = lop_and_xor(yv.w, mask, yu.w);
         }
-        const uint32_t c = gram16_parities(X, Y);  // diagonal d at bit d (31 bits)
-        const uint32_t off = u + v;                 // in 16-bit units
+        const uint32_t c = gram16_parities(X, Y, pm);  // diagonal d at bit d (31 bits)
+        if (u == v) {
+            atomicXor(&d[u], c);
+            continue;
+        }
+        const uint32_t off = u + v;  // in 16-bit units
         if (off & 1u) {
             atomicXor(&z[off >> 1], c << 16);
             atomicXor(&z[(off >> 1) + 1], c >> 16);
@@ -123,6 +160,16 @@ __global__ void __launch_bounds__(kAlg2Threads)
     __syncthreads();
     for (uint32_t i = tid; i <= k; i += blockDim.x)
         if (z[i]) atomicXor(&zg[blk.zoff + i], z[i]);
+    for (uint32_t i = tid; i < k; i += blockDim.x)
+        if (d[i]) atomicXor(&zg[blk.zoff + k + 1 + i], d[i]);
+}
+
+// W_o = XOR of D_u over max(0, o - k + 1) <= u <= min(o, k - 1), from the
+// prefix XORs H[u] = D_0 ^ ... ^ D_{u-1}; 0 past the last offset 2k - 2.
+__device__ __forceinline__ uint32_t puu_window(const uint32_t *H, uint32_t k, uint32_t o) {
+    if (o > 2 * k - 2) return 0u;
+    const uint32_t lo = o + 1 > k ? o + 1 - k : 0u, hi = o < k - 1 ? o : k - 1;
+    return H[hi + 1] ^ H[lo];
 }
 
 __global__ void __launch_bounds__(128)
@@ -130,9 +177,24 @@ __global__ void __launch_bounds__(128)
                        uint16_t *__restrict__ out) {
     __shared__ uint32_t z[kMaxUnits + 2], H[kMaxUnits + 2];
     const Alg2Block blk = table[blockIdx.x];
-    const uint32_t q = blk.q, nz = blk.k + 1, tid = threadIdx.x;
+    const uint32_t q = blk.q, k = blk.k, nz = k + 1, tid = threadIdx.x;
     const uint32_t qw = q >> 5, qb = q & 31u, nh = nz - qw;
-    for (uint32_t i = tid; i < nz; i += blockDim.x) z[i] = zg[blk.zoff + i];
+    // prefix XORs of the P_uu parities: H[u] = D_0 ^ ... ^ D_{u-1}
+    for (uint32_t u = tid; u < k; u += blockDim.x) z[u] = zg[blk.zoff + nz + u];
+    __syncthreads();
+    if (tid == 0) {
+        uint32_t acc = 0;
+        for (uint32_t u = 0; u < k; ++u) {
+            H[u] = acc;
+            acc ^= z[u];
+        }
+        H[k] = acc;
+    }
+    __syncthreads();
+    // word i of the sum: W_o (31 bits at bit 16 o) for o = 2i - 1, 2i, 2i + 1
+    for (uint32_t i = tid; i < nz; i += blockDim.x)
+        z[i] = zg[blk.zoff + i] ^ puu_window(H, k, 2 * i) ^ (i ? puu_window(H, k, 2 * i - 1) >> 16 : 0u) ^
+               (puu_window(H, k, 2 * i + 1) << 16);
     // fold the part at and above x^q back by P's taps until none is left
     // (each fold lowers the degree by q - c; bounded for safety)
     for (int fold = 0; fold < 64; ++fold) {
@@ -149,7 +211,9 @@ __global__ void __launch_bounds__(128)
             uint32_t v = z[i];
             if (i > qw || (i == qw && qb == 0)) v = 0;
             else if (i == qw) v &= (1u << qb) - 1u;
-            for (uint32_t t = 0; t < blk.ntaps; ++t) {
+#pragma unroll
+            for (uint32_t t = 0; t < 4; ++t) {
+                if (t >= blk.ntaps) break;
                 const uint32_t e = blk.taps[t], ew = e >> 5, eb = e & 31u;
                 if (i >= ew && i - ew < nh) v ^= H[i - ew] << eb;
                 if (eb && i >= ew + 1 && i - ew - 1 < nh) v ^= H[i - ew - 1] >> (32 - eb);
@@ -248,10 +312,10 @@ int qext_alg2_plan_create(double delta, uint32_t b, uint32_t q1, uint32_t Delta,
         blk.zoff = p->zwords;
         bits += uint64_t(blk.q) * p->n_p;
         obits += blk.q;
-        p->zwords += blk.k + 1;
-        // work items: the block's k^2 unit pairs, per group of 32 elements
+        p->zwords += 2 * blk.k + 1;
+        // work items: the block's k (k + 1) / 2 unit products, per group of 32 elements
         p->item_prefix.push_back(uint32_t(p->items.size()));
-        const uint32_t pairs = blk.k * blk.k, groups = (p->n_p + 31) / 32;
+        const uint32_t pairs = blk.k * (blk.k + 1) / 2, groups = (p->n_p + 31) / 32;
         for (uint32_t g = 0; g < groups; ++g)
             for (uint32_t p0 = 0; p0 < pairs; p0 += kItemProducts)
                 p->items.push_back(Alg2Item{l, g, p0, std::min(pairs, p0 + kItemProducts)});
@@ -321,9 +385,13 @@ int qext_alg2_extract(const qext_alg2_plan *p, const uint16_t *x, const uint16_t
     if (rc != QEXT_OK) return rc;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const Alg2Block &last = p->blocks[nblocks - 1];
-    if (cudaMemsetAsync(p->d_z, 0, sizeof(uint32_t) * (last.zoff + last.k + 1), st) != cudaSuccess) return QEXT_E_CUDA;
+    if (cudaMemsetAsync(p->d_z, 0, sizeof(uint32_t) * (last.zoff + 2 * last.k + 1), st) != cudaSuccess)
+        return QEXT_E_CUDA;
+    StreamArgs pm;
+    std::memset(&pm, 0, sizeof pm);
+    pm.set_multipliers();
     alg2_products_kernel<<<p->item_prefix[nblocks], kAlg2Threads, 0, st>>>(p->d_items, p->d_blocks, p->n_p, x, y,
-                                                                          p->d_z);
+                                                                          p->d_z, pm);
     alg2_reduce_kernel<<<nblocks, 128, 0, st>>>(p->d_blocks, p->d_z, out);
     return cudaGetLastError() == cudaSuccess ? QEXT_OK : QEXT_E_CUDA;
 }

@@ -33,21 +33,6 @@ __device__ __forceinline__ uint32_t diagonal_chain(const uint32_t *X, const uint
     return c;
 }
 
-// Parities of the 31 diagonals of a sliced 16 x 16 Gram product by one
-// Karatsuba level (8 + 8): bit d of the result = parity of diagonal d.  X and
-// Y are overwritten (their low halves become the halves' sums).
-__device__ __forceinline__ uint32_t gram16_parities(uint32_t *X, uint32_t *Y) {
-    const uint32_t a = diagonal_chain<8>(X, Y);  // 15 parities in bits 17..31
-    const uint32_t b = diagonal_chain<8>(X + 8, Y + 8);
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        X[j] ^= X[j + 8];
-        Y[j] ^= Y[j + 8];
-    }
-    const uint32_t c = diagonal_chain<8>(X, Y);
-    return lop_xor3(a >> 17, b >> 1, lop_xor3(a, b, c) >> 9);
-}
-
 // Parities of the diagonals D0 .. D1-1 of sum_b t^(S b) (X_b x Y_b), where
 // X_b = X[O0 + OSTEP b .. + 8) and likewise Y_b: diagonal d takes the pairs
 // j + l = d - S b of block b.  One live accumulator per diagonal; bit d - D0
@@ -79,6 +64,22 @@ __device__ __forceinline__ uint32_t block_parities(const uint32_t *X, const uint
         }
     }
     return r;
+}
+
+// Parities of the 31 diagonals of a sliced 16 x 16 Gram product by one
+// Karatsuba level (8 + 8): with D = A + t^8 B (the halves' products, 23
+// diagonals, one shared chain per diagonal) and C = (X_L + X_H)(Y_L + Y_H)
+// (15), the product is D (1 + t^8) + t^8 C.  Bit d of the result = parity of
+// diagonal d.  X and Y are overwritten (their low halves become the sums).
+__device__ __forceinline__ uint32_t gram16_parities(uint32_t *X, uint32_t *Y, const StreamArgs &s) {
+    const uint32_t d = block_parities<2, 0, 8, 8, 0, 23>(X, Y, s);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        X[j] ^= X[8 + j];
+        Y[j] ^= Y[8 + j];
+    }
+    const uint32_t c = block_parities<1, 0, 0, 0, 0, 15>(X, Y, s);
+    return d ^ (d << 8) ^ (c << 8);
 }
 
 // Parities of the 63 diagonals of a sliced 32 x 32 Gram product by two
