@@ -150,7 +150,8 @@ int qext_extract(const qext_plan *p, const uint32_t *x, const uint32_t *y, uint6
                                    wait after a few polls, records QEXT_E_TIMEOUT (qext_device_status) and
                                    returns; outputs are not written.  Needs 16-byte aligned x, y and a
                                    staged tile (else INVAL).  Alone it tests the default kernel of the
-                                   plan (the per-warp kernel for q = 16 with n_p = 64); with
+                                   plan (the per-warp kernel for q = 16 with n_p = 64; for q = 80,
+                                   the blocks-in-lanes kernel, with nblocks a multiple of 32); with
                                    QEXT_F_CTA_TILES, the CTA-tile kernel.  qext_extract_samples_ex
                                    accepts it for its per-warp kernel (q = 4, 16 with n_p = 64) only. */
 #define QEXT_F_ALL 0x1Fu
@@ -160,9 +161,9 @@ int qext_extract(const qext_plan *p, const uint32_t *x, const uint32_t *y, uint6
  * default path chosen by qext_extract).  Same arguments, ownership and errors;
  * INVAL also for unknown flag bits.  The output is identical for every flag
  * combination.  The default path for q = 16 with n_p = 64 and 16-byte
- * aligned x, y is the per-warp copy pipeline of qext_extract_samples_ex (its
- * 16-bit samples are the packed stream); any flag, including
- * QEXT_F_CTA_TILES (below), selects the CTA-tile kernel instead.
+ * aligned x, y is a per-warp copy pipeline over sub-tiles of 32 blocks; any
+ * flag but QEXT_F_TEST_TIMEOUT, including QEXT_F_CTA_TILES (below), selects
+ * the CTA-tile kernel instead.  q = 80 plans take QEXT_F_TEST_TIMEOUT only.
  */
 int qext_extract_ex(const qext_plan *p, const uint32_t *x, const uint32_t *y, uint64_t nblocks, uint32_t *out,
                     qext_cuda_stream stream, uint32_t flags);

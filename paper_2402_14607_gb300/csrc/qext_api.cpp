@@ -18,12 +18,13 @@ int qext_extract_ex(const qext_plan *p, const uint32_t *x, const uint32_t *y, ui
     if (flags & ~uint32_t(QEXT_F_ALL | QEXT_F_CTA_TILES)) return QEXT_E_INVAL;
     if ((flags & QEXT_F_TILE32) && (flags & QEXT_F_TILE64)) return QEXT_E_INVAL;
     if (!p->gpu_supported && !p->gpu_q80) return QEXT_E_UNSUPPORTED;
-    if (p->gpu_q80 && flags) return QEXT_E_INVAL;  // one kernel, no launch options
+    // q = 80: no launch options; QEXT_F_TEST_TIMEOUT tests the lanes kernel's bounded wait
+    if (p->gpu_q80 && (flags & ~uint32_t(QEXT_F_TEST_TIMEOUT))) return QEXT_E_INVAL;
     if (nblocks == 0) return QEXT_OK;
     if (!x || !y || !out || !aligned(x, 4) || !aligned(y, 4) || !aligned(out, 4)) return QEXT_E_INVAL;
     if (nblocks > (UINT64_MAX / p->n)) return QEXT_E_INVAL;
     const qext::NvtxRange range("qext extract");
-    if (p->gpu_q80) return qext::launch_extract_q80(p, x, y, nblocks, out, stream);
+    if (p->gpu_q80) return qext::launch_extract_q80(p, x, y, nblocks, out, stream, flags);
     return qext::launch_extract(p, x, y, nblocks, out, stream, flags);
 }
 

@@ -370,6 +370,8 @@ struct LanesArgs {
     uint32_t n_p;
     int bulk;             // sources 16-byte aligned: whole tiles arrive by bulk copy
     uint64_t src_words;   // readable words of each source, ceil(nblocks n / 32)
+    uint32_t max_polls;   // bound of every mbarrier wait
+    int no_copy;          // test of failure detection: barrier armed, no copy issued
 };
 
 // NP > 0: n_p fixed at compile time (the row strides of the slicing become
@@ -389,6 +391,7 @@ __global__ void __launch_bounds__(kThreadsLanes, 4) extract_q80_lanes_kernel(con
     auto full_tile = [&](uint64_t t) { return a.bulk && 32 * (t + 1) <= s.nblocks; };
     auto issue = [&](uint64_t t) {
         mbar_expect_tx(&bar, 8u * n);
+        if (a.no_copy) return;  // the completion never comes: the wait must give up
         tma_load_1d(tin, s.x + t * n, 4u * n, &bar);
         tma_load_1d(tin + y_off, s.y + t * n, 4u * n, &bar);
     };
@@ -405,12 +408,12 @@ __global__ void __launch_bounds__(kThreadsLanes, 4) extract_q80_lanes_kernel(con
     const uint32_t pmask = ca == cb ? 0u : ~0u;
     for (uint32_t phase = 0; t < ntiles; t += gridDim.x) {
         if (full_tile(t)) {
-            const bool ok = mbar_wait_bounded(&bar, phase & 1u);
+            const bool ok = mbar_wait_bounded(&bar, phase & 1u, a.max_polls);
             ++phase;
             if (__syncthreads_or(!ok)) {
                 if (tid == 0) {
                     record_status(s.status, QEXT_E_TIMEOUT);
-                    mbar_wait_bounded(&bar, (phase - 1) & 1u);  // let the copies in flight land
+                    if (!a.no_copy) mbar_wait_bounded(&bar, (phase - 1) & 1u, a.max_polls);  // let the copies land
                 }
                 return;
             }
@@ -541,8 +544,9 @@ __global__ void __launch_bounds__(kThreadsLanes, 4) extract_q80_lanes_kernel(con
 namespace qext {
 
 int launch_extract_q80(const qext_plan *p, const uint32_t *x, const uint32_t *y, uint64_t nblocks, uint32_t *out,
-                       qext_cuda_stream stream) {
+                       qext_cuda_stream stream, uint32_t flags) {
     if (p->q != 80) return QEXT_E_UNSUPPORTED;
+    if (flags & ~uint32_t(QEXT_F_TEST_TIMEOUT)) return QEXT_E_INVAL;
     if (nblocks == 0) return QEXT_OK;
     static DeviceSlots grid_caps, smem_optin, attr_set[2];
     const int dev = current_device();
@@ -588,11 +592,16 @@ int launch_extract_q80(const qext_plan *p, const uint32_t *x, const uint32_t *y,
         a.n_p = p->n_p;
         a.bulk = (reinterpret_cast<uintptr_t>(x) % 16 == 0 && reinterpret_cast<uintptr_t>(y) % 16 == 0) ? 1 : 0;
         a.src_words = (nblocks * n + 31) / 32;
+        a.no_copy = (flags & QEXT_F_TEST_TIMEOUT) ? 1 : 0;
+        a.max_polls = a.no_copy ? 256u : kMaxPolls;
+        // the test needs every tile on the bulk-copy path
+        if (a.no_copy && (!a.bulk || nblocks % 32)) return QEXT_E_INVAL;
         const uint64_t ntiles = (nblocks + 31) / 32, cap = uint64_t(sms) * uint64_t(occ > 0 ? occ : 1);
         const int grid = int(ntiles < cap ? ntiles : cap);
         return launch_pdl(kernel, grid, kThreadsLanes, size_t(lanes_smem), st, a);
     }
 
+    if (flags) return QEXT_E_INVAL;  // one block per thread: no bulk copies to time out
     const int grid_cap = grid_caps.get(dev, [sms] {
         int occ = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, extract_q80_kernel, kThreads80, 0) != cudaSuccess)

@@ -122,7 +122,8 @@ int launch_raw_samples(uint32_t q, uint32_t b, const qxd::StreamArgs &s, const u
 int launch_extract_packed16(const qxd::StreamArgs &s, qext_cuda_stream stream, uint32_t flags);
 // q = 80 blocks (any n_p), packed words.
 int launch_extract_q80(const qext_plan *p, const uint32_t *x, const uint32_t *y, uint64_t nblocks, uint32_t *out,
-                       qext_cuda_stream stream);
+                       qext_cuda_stream stream,
+                       uint32_t flags = 0);
 int launch_pack(uint32_t b, const uint16_t *samples, uint64_t nsamples, uint32_t *out, qext_cuda_stream stream);
 int read_device_status(int *status);
 // Device address of the status word of the current device (null if the

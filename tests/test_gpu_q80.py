@@ -130,3 +130,34 @@ def test_paper_workload_full_size_sampled():
     got = host_words(out)
     assert got[-1] == 0xFFFFFFFF, "wrote past the output"
     check_sampled(plan, oracle.pack_samples(16, sx), oracle.pack_samples(16, sy), got[:-1], nb, 5)
+
+
+def test_bounded_wait_times_out_and_context_survives():
+    """Failure detection in the blocks-in-lanes kernel without a fault: with
+    QEXT_F_TEST_TIMEOUT every CTA arms its tile barrier but issues no bulk
+    copy, so its bounded wait runs out; the kernel records QEXT_E_TIMEOUT and
+    returns, the host reads (and clears) the status, and the next launch on
+    the same context is bit-exact.  The mode needs bulk-copied tiles only."""
+    plan = paper_plan()
+    nblocks = 32 * 40
+    words = nblocks * 5680 // 32
+    x = workloads.random_words(71, words)
+    y = workloads.random_words(72, words)
+    tx, ty = dev_words(x), dev_words(y)
+    out = torch.full((nblocks * 80 // 32,), -1, dtype=torch.int32, device="cuda")
+    assert qext.qext_device_status() == qext.QEXT_OK
+    qext.qext_extract_ex(plan, tx, ty, nblocks, out, None, qext.QEXT_F_TEST_TIMEOUT)
+    torch.cuda.synchronize()
+    assert qext.qext_device_status() == qext.QEXT_E_TIMEOUT
+    assert qext.qext_device_status() == qext.QEXT_OK          # read clears it
+    qext.qext_extract(plan, tx, ty, nblocks, out)
+    torch.cuda.synchronize()
+    assert (host_words(out) == oracle_extract(plan, x, y, nblocks)).all()
+    assert qext.qext_device_status() == qext.QEXT_OK
+    for args, flags in [((tx, ty, nblocks - 1), qext.QEXT_F_TEST_TIMEOUT),        # a ragged last tile
+                        ((dev_words(x, offset_words=1), dev_words(y, offset_words=1), nblocks),
+                         qext.QEXT_F_TEST_TIMEOUT),                              # no bulk copies
+                        ((tx, ty, nblocks), qext.QEXT_F_DIRECT)]:               # no launch options
+        with pytest.raises(qext.QextError) as e:
+            qext.qext_extract_ex(plan, *args, out, None, flags)
+        assert e.value.code == qext.QEXT_E_INVAL
