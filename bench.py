@@ -206,7 +206,7 @@ def measure_batched(args, dev):
     import torch
 
     from paper_2402_14607_gb300 import qext, workloads
-    specs = workloads.config_batched()
+    specs = workloads.config_batched(hi=args.batched_max_log2_blocks)
     plans, items, raw = {}, [], []
     total_raw = total_packed = total_out_bits = 0
     for sp in specs:
@@ -288,8 +288,8 @@ def measure_batched(args, dev):
     bs.close()
     b.close()
     peak = measured_peaks()[0]
-    return {"workload": "64 stream pairs, 2^U blocks (U~U(12,20)), n in {256,1024,4096}, 8- and 12-bit ADC samples "
-                        "(uint16, seeded on the device), ingest + extraction",
+    return {"workload": "64 stream pairs, 2^U blocks (U~U(12,%d)), n in {256,1024,4096}, 8- and 12-bit ADC samples "
+                        "(uint16, seeded on the device), ingest + extraction" % args.batched_max_log2_blocks,
             "streams": len(items), "raw_input_bytes": total_raw, "packed_input_bytes": total_packed,
             "extracted_bits": total_out_bits,
             "batched_graph_gbps": round(total_out_bits / t_graph / 1e9, 2), "batched_graph_ms": round(t_graph * 1e3, 3),
@@ -892,6 +892,9 @@ def main(argv=None):
     ap.add_argument("--ref-sample-blocks", type=int, default=1 << 15)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched and serving measurements")
+    ap.add_argument("--batched-max-log2-blocks", type=int, default=20,
+                    help="upper end of the batched streams' log2 block counts (20: the workload; smaller for "
+                         "profiling captures)")
     ap.add_argument("--only", choices=["batched", "serving", "paper_params", "alg2", "sustained", "monitor"],
                     default=None, help="run only this extra measurement and print it (for kernel profiles)")
     ap.add_argument("--e2e-chunk-blocks", type=int, default=1 << 17)
