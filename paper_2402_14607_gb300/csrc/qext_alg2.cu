@@ -179,16 +179,30 @@ __global__ void __launch_bounds__(128)
     const Alg2Block blk = table[blockIdx.x];
     const uint32_t q = blk.q, k = blk.k, nz = k + 1, tid = threadIdx.x;
     const uint32_t qw = q >> 5, qb = q & 31u, nh = nz - qw;
-    // prefix XORs of the P_uu parities: H[u] = D_0 ^ ... ^ D_{u-1}
-    for (uint32_t u = tid; u < k; u += blockDim.x) z[u] = zg[blk.zoff + nz + u];
-    __syncthreads();
-    if (tid == 0) {
-        uint32_t acc = 0;
-        for (uint32_t u = 0; u < k; ++u) {
-            H[u] = acc;
-            acc ^= z[u];
+    // prefix XORs of the P_uu parities, H[u] = D_0 ^ ... ^ D_{u-1}: warp 0,
+    // lane j holding D_{4j} .. D_{4j+3} (k <= 128), an XOR scan across lanes
+    if (tid < 32) {
+        uint32_t d[4], run = 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const uint32_t u = 4 * tid + uint32_t(i);
+            d[i] = u < k ? zg[blk.zoff + nz + u] : 0u;
+            run ^= d[i];
         }
-        H[k] = acc;
+        uint32_t incl = run;  // inclusive scan of the lanes' XORs
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (tid >= uint32_t(o)) incl ^= v;
+        }
+        uint32_t acc = incl ^ run;  // XOR of the lanes before this one
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const uint32_t u = 4 * tid + uint32_t(i);
+            if (u <= k) H[u] = acc;
+            acc ^= d[i];
+        }
+        if (tid == 31 && k == kMaxUnits) H[kMaxUnits] = acc;  // the whole XOR
     }
     __syncthreads();
     // word i of the sum: W_o (31 bits at bit 16 o) for o = 2i - 1, 2i, 2i + 1
