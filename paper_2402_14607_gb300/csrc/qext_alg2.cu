@@ -99,6 +99,7 @@ __global__ void __launch_bounds__(kAlg2Threads)
     __shared__ __align__(16) uint32_t S[2][kMaxUnits][kRow];
     __shared__ uint32_t z[kMaxUnits + 1];     // this item's share of the unreduced sum
     __shared__ uint32_t d[kMaxUnits];         // and of the P_uu parities
+    pdl_prologue();
     const Alg2Item it = items[blockIdx.x];
     const Alg2Block blk = table[it.block];
     const uint32_t k = blk.k, tid = threadIdx.x;
@@ -176,6 +177,7 @@ __global__ void __launch_bounds__(128)
     alg2_reduce_kernel(const Alg2Block *__restrict__ table, const uint32_t *__restrict__ zg,
                        uint16_t *__restrict__ out) {
     __shared__ uint32_t z[kMaxUnits + 2], H[kMaxUnits + 2];
+    pdl_prologue();  // the products launch has completed past this point
     const Alg2Block blk = table[blockIdx.x];
     const uint32_t q = blk.q, k = blk.k, nz = k + 1, tid = threadIdx.x;
     const uint32_t qw = q >> 5, qb = q & 31u, nh = nz - qw;
@@ -404,10 +406,14 @@ int qext_alg2_extract(const qext_alg2_plan *p, const uint16_t *x, const uint16_t
     StreamArgs pm;
     std::memset(&pm, 0, sizeof pm);
     pm.set_multipliers();
-    alg2_products_kernel<<<p->item_prefix[nblocks], kAlg2Threads, 0, st>>>(p->d_items, p->d_blocks, p->n_p, x, y,
-                                                                          p->d_z, pm);
-    alg2_reduce_kernel<<<nblocks, 128, 0, st>>>(p->d_blocks, p->d_z, out);
-    return cudaGetLastError() == cudaSuccess ? QEXT_OK : QEXT_E_CUDA;
+    const Alg2Item *const items = p->d_items;
+    const Alg2Block *const table = p->d_blocks;
+    uint32_t *const z = p->d_z;
+    const uint32_t n_p = p->n_p;
+    const int rp = qext::launch_pdl(alg2_products_kernel, int(p->item_prefix[nblocks]), kAlg2Threads, 0, st, items,
+                                    table, n_p, x, y, z, pm);
+    if (rp != QEXT_OK) return rp;
+    return qext::launch_pdl(alg2_reduce_kernel, int(nblocks), 128, 0, st, table, static_cast<const uint32_t *>(z), out);
 }
 
 int qext_alg2_destroy(qext_alg2_plan *p) {
