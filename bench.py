@@ -32,6 +32,8 @@ if ROOT not in sys.path:
 import numpy as np  # noqa: E402
 
 METRIC = "extracted Gbps on 1 GB300 (bit-exact), %HBM roofline; serving p50/p99 ms"
+DATA = "synthetic (seeded quantised-Gaussian 12-bit ADC samples, numpy PCG64)"
+DEFAULT_STEP = "qext_extract (packed 12-bit samples, one kernel)"
 UNIT = "Gbps"
 L2_BYTES = 126 << 20
 # kernel sources whose hash must match a profile's capture for its traffic figure to be reported
@@ -164,6 +166,9 @@ def run_reference(args):
     sx = workloads.adc_samples(spec.seed_x, ns, spec.b, offset_amp=spec.offset_amp)   # prefix of the stream
     sy = workloads.adc_samples(spec.seed_y, ns, spec.b, offset_amp=spec.offset_amp)
     threads = os.cpu_count() or 1
+    import oracle
+    op = oracle.plan(spec.n, 0, spec.k, spec.eps)
+    info = {"q": op["q"], "n_p": op["n_p"], "m": op["m"], "log2_eps_block": op["log2_eps"]}
     ox, oy = oracle_packed(spec, sx, sy, sample)
     for _ in range(args.warmup):
         run_oracle_sample(spec, ox, oy, 1, threads)
@@ -178,12 +183,13 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total / args.steps * 1e3, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-        "data": "synthetic (seeded quantised-Gaussian ADC samples)",
-        "config": {"workload": "large single stream (n=1024, 12-bit ADC samples packed to bits), each step a "
-                               "bounded sample of %d block pairs" % sample, "n": spec.n, "nblocks_per_step": sample,
-                   "b": spec.b},
+        "data": DATA,
+        # the same workload and step as the default run of this file; the
+        # oracle's steps are bounded samples of it (cpu_baseline.sample)
+        "config": dict(workload_config(spec, info, world), step=DEFAULT_STEP),
         "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": "%d block pairs per step (extraction from the packed words)" % sample},
+                         "sample": "each step the first %d of the workload's %d block pairs (extraction from the "
+                                   "packed words)" % (sample, spec.nblocks)},
         "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -865,11 +871,11 @@ def run_gpu(args):
             "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(t / args.steps * 1e3, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-            "data": "synthetic (seeded quantised-Gaussian 12-bit ADC samples, numpy PCG64)",
+            "data": DATA,
             "config": dict(workload_config(spec, info, world), step=(
                 "qext_pack_samples(x), qext_pack_samples(y), qext_extract (from uint16 samples)" if args.unfused
                 else "qext_extract_samples (uint16 samples, ingest fused into the extraction kernel)"
-                if args.step == "uint16" else "qext_extract (packed 12-bit samples, one kernel)")),
+                if args.step == "uint16" else DEFAULT_STEP)),
             "input_gbps": round(input_gbps, 2),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "uint16_step": uint16_step,
             "clocks": {k: clk.get(k) for k in ("sm_mhz", "sm_max_mhz", "reasons", "samples", "source")},
